@@ -1,0 +1,401 @@
+"""Benchmark: MLUPS and fraction of the HBM roofline of the MRT-LB hot path.
+
+Workload (default): 2D D2Q9, periodic 4096^2, nu = 0.02, eps = 0.2048,
+theta0 = 2 + sin(2 pi x) sin(2 pi y) (the 2D sine family), FP64 and FP32
+shifted storage.  One benchmark step is one pass of the whole hot path:
+lb_set_theta0 (initialisation), S fused pull-stream + collide sweeps,
+lb_macros (theta, grad theta, u), lb_sum_theta and lb_reduce (error norms
+against the closed-form solution at t = S dt).  MLUPS = nodes * S / time.
+
+The state (2 x 1.2 GB for FP64) is larger than L2 (129 MB), so there is no
+L2 flush between steps.  Times come from CUDA events on the solver's
+stream.  ``e2e`` repeats the step through the public API from pinned host
+buffers (inputs copied in, theta and u copied out, inside the timed
+region).  ``--impl reference`` times the FP64 CPU oracle instead.
+
+Multi-GPU: the path is one periodic grid per GPU; ranks run independent
+replicas (weak scaling, no collective on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2309_02825_gb300 import workloads as W  # noqa: E402
+
+METRIC = "MLUPS and % of HBM BW vs L2 err to exact: FP64 vs FP32-shifted; adjoint step cost"
+UNIT = "MLUPS"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32s"])
+    p.add_argument("--N", type=int, default=4096)
+    p.add_argument("--sweeps", type=int, default=100, help="sweeps per benchmark step")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-variant", action="store_true", help="skip the other precision's sub-result")
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        return {"hbm_gbs": float(pk["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def profile_traffic(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary for this kernel,
+    valid only while the kernel source is unchanged (same sha)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2309_02825_gb300", "csrc", "lb_kernels.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        path = os.path.join(ROOT, "profiles", "traffic.txt")
+        for line in open(path):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kernel_key and parts[1] == sha:
+                return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier_max(t, world):
+    if world == 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    v = torch.tensor([t], dtype=torch.float64, device="cuda")
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return float(v.item())
+
+
+# ---------------------------------------------------------------------------
+# Our implementation.
+# ---------------------------------------------------------------------------
+
+def run_ours(args, precision, world, rank, local, peaks, with_e2e, label_main):
+    import torch
+    from paper_2309_02825_gb300 import lb
+
+    torch.cuda.set_device(local)
+    case = W.sine_2d(args.N)
+    S = args.sweeps
+    N, d = case.N, case.d
+    T = S * case.dt
+    th0_h = case.problem.theta(N, case.dx)
+    g0_h = np.ascontiguousarray(case.problem.grad(N, case.dx))
+    ex_t_h = case.problem.theta(N, case.dx, T)
+    ex_u_h = np.ascontiguousarray(case.problem.u(N, case.dx, T))
+    th0 = torch.from_numpy(th0_h).cuda()
+    g0 = torch.from_numpy(g0_h).cuda()
+    ex_t = torch.from_numpy(ex_t_h).cuda()
+    ex_u = torch.from_numpy(ex_u_h).cuda()
+
+    stream = torch.cuda.Stream()
+    theta_ref = 2.0 if precision == "fp32s" else 0.0
+    s = lb.Solver(d, N, case.nu, case.dx, case.dt, precision=precision, theta_ref=theta_ref, stream=stream)
+    th = torch.empty(tuple(reversed(N)), dtype=torch.float64, device="cuda")
+    gr = torch.empty((d,) + tuple(reversed(N)), dtype=torch.float64, device="cuda")
+    u = torch.empty_like(gr)
+
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    out = {}
+
+    def one_step(i=None):
+        s.set_theta0(th0, g0)
+        if i is not None:
+            ev_s[i].record(stream)
+        s.step(S)
+        if i is not None:
+            ev_e[i].record(stream)
+        s.macros(th, gr, u)
+        out["total"] = s.sum_theta()
+        out["norms"] = s.reduce(th, u, ex_t, ex_u)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local) if label_main else None
+    if clocks:
+        clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        t_start.record(stream)
+        for i in range(args.steps):
+            one_step(i)
+        t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    elapsed = barrier_max(elapsed, world)
+    sweep_ms = sum(a.elapsed_time(b) for a, b in zip(ev_s, ev_e)) / (args.steps * S)
+
+    nodes = case.nodes
+    lups = nodes * S * args.steps * world
+    value = lups / elapsed / 1e6
+    q = 9
+    elem = 8 if precision == "fp64" else 4
+    bytes_lu = 2 * q * elem
+    achieved = bytes_lu * nodes / (sweep_ms / 1e3) / 1e9
+    norms = out["norms"]
+    res = {
+        "value": value,
+        "ms_per_step": elapsed / args.steps * 1e3,
+        "sweep_ms": sweep_ms,
+        "bytes_per_lu": bytes_lu,
+        "roofline": {
+            "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"],
+            "traffic": profile_traffic("sweep_d2q9_%s_%d" % (precision, args.N)),
+            "kernel": "sweep_kernel<D2Q9,%s>" % ("double" if precision == "fp64" else "float"),
+            "algorithmic_bytes_per_launch": bytes_lu * nodes,
+            "peak_source": peaks["source"],
+        },
+        "error": {"t": T, "theta_rmse": norms["theta"]["rmse"],
+                  "u_rmse": math.sqrt(sum(norms["u%d" % a]["rmse"] ** 2 for a in range(d)) / d),
+                  "u_linf": max(norms["u%d" % a]["linf"] for a in range(d)),
+                  "u_rel_l2": math.sqrt(sum(norms["u%d" % a]["rel_l2"] ** 2 for a in range(d)) / d),
+                  "sum_theta_drift": abs(out["total"] - float(th0_h.sum())) / float(th0_h.sum())},
+        "clocks": clk,
+        "gpu_launches": args.steps * (S + 6),
+    }
+
+    if with_e2e:
+        res["e2e"] = run_e2e(args, s, case, th0_h, g0_h, ex_t_h, ex_u_h, stream, world)
+    s.close()
+    return res
+
+
+def run_e2e(args, s, case, th0_h, g0_h, ex_t_h, ex_u_h, stream, world):
+    """Same step through the public API with pinned host buffers: H2D of
+    theta0, grad theta0 and the exact fields, the hot path, D2H of theta and
+    u and the norms (host)."""
+    import torch
+    S = args.sweeps
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_in = [pin(th0_h), pin(g0_h), pin(ex_t_h), pin(ex_u_h)]
+    d_in = [torch.empty_like(h, device="cuda") for h in h_in]
+    shape = tuple(reversed(case.N))
+    th = torch.empty(shape, dtype=torch.float64, device="cuda")
+    u = torch.empty((case.d,) + shape, dtype=torch.float64, device="cuda")
+    h_out = [torch.empty(th.shape, dtype=torch.float64).pin_memory(),
+             torch.empty(u.shape, dtype=torch.float64).pin_memory()]
+
+    def one():
+        for h, dv in zip(h_in, d_in):
+            dv.copy_(h, non_blocking=True)
+        s.set_theta0(d_in[0], d_in[1])
+        s.step(S)
+        s.macros(th, None, u)
+        s.reduce(th, u, d_in[2], d_in[3])
+        h_out[0].copy_(th, non_blocking=True)
+        h_out[1].copy_(u, non_blocking=True)
+        stream.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.warmup)):
+            one()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            one()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+    el = barrier_max(el, world)
+    h2d = sum(h.numel() * h.element_size() for h in h_in)
+    d2h = sum(h.numel() * h.element_size() for h in h_out)
+    return {"value": case.nodes * S * args.steps * world / el / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+# ---------------------------------------------------------------------------
+# The oracle (CPU baseline / reference arm).
+# ---------------------------------------------------------------------------
+
+def time_oracle(N, sweeps):
+    import oracle as O
+    case = W.sine_2d(N)
+    m = O.Model(case.d, case.N, case.nu, case.dx, case.dt)
+    f = m.initialize(case.problem.theta(case.N, case.dx), case.problem.grad(case.N, case.dx))
+    t0 = time.perf_counter()
+    f = m.run(f, sweeps)
+    el = time.perf_counter() - t0
+    return case.nodes * sweeps / el / 1e6, el
+
+
+def cpu_baseline(args):
+    sweeps = 2
+    v, el = time_oracle(args.N, sweeps)
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d sweeps of the %d^2 D2Q9 FP64 oracle (%.1f s, single thread)" % (sweeps, args.N, el)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        time_oracle(args.N, 1)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, _ = time_oracle(args.N, 1)
+        vals.append(v)
+    el = time.perf_counter() - t0
+    value = args.N * args.N * args.steps / el / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "2D D2Q9 periodic %d^2 sine, nu=0.02, eps=0.2048; reference step = 1 oracle sweep"
+                   % args.N, "precision": "fp64", "l2_flush": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "1 sweep of %d^2 per step" % args.N},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    peaks = load_peaks()
+    main_res = run_ours(args, args.precision, world, rank, local, peaks, not args.no_e2e, True)
+    other = "fp32s" if args.precision == "fp64" else "fp64"
+    variant = None
+    if not args.no_variant:
+        v = run_ours(args, other, world, rank, local, peaks, False, False)
+        variant = {"precision": other, "value": v["value"], "unit": UNIT, "roofline": v["roofline"],
+                   "error": v["error"], "sweep_ms": v["sweep_ms"]}
+    base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        base = cpu_baseline(args)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": main_res["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": main_res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": "2D D2Q9 periodic %d^2 sine, nu=0.02, eps=0.2048; step = init + %d fused "
+                       "sweeps + recovery + sum theta + error norms" % (args.N, args.sweeps),
+                       "precision": args.precision, "sweeps_per_step": args.sweeps,
+                       "l2_flush": "inputs larger than L2 (state %.1f GB)" % (
+                           2 * 9 * (8 if args.precision == "fp64" else 4) * args.N ** 2 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": main_res["roofline"],
+            "cpu_baseline": base,
+            "e2e": main_res.get("e2e"),
+            "gpu_launches": main_res["gpu_launches"] * world,
+            "clocks": main_res["clocks"],
+            "error": main_res["error"],
+            "sweep_ms": main_res["sweep_ms"],
+        }
+        if variant:
+            line["variant"] = variant
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,184 @@
+/*
+ * lb.h - C ABI of the GB300 Cole-Hopf fourth-order MRT-LB solver.
+ *
+ * Method: Chen, Liu, Chai & Shi, "A Cole-Hopf transformation based
+ * fourth-order multiple-relaxation-time lattice Boltzmann model for the
+ * coupled Burgers' equations" (arXiv:2309.02825).  The coupled Burgers'
+ * velocity u is recovered through the Cole-Hopf map u = -2 nu grad(theta) /
+ * theta (Eq. (transf)) from theta solving d(theta)/dt = nu lap(theta)
+ * (Eq. (eq-theta)), which is advanced by the MRT-LB scheme of Sec. III.A on
+ * the DdQ(1+2d^2) lattice (d = 1, 2, 3: D1Q3, D2Q9, D3Q19).
+ *
+ * Conventions for every call:
+ *  - Every call returns an lb_status; nothing aborts or throws across the
+ *    ABI.  lb_last_error() gives a message for the last failure.
+ *  - Grids are periodic with sizes N[0..d-1] (N[0] along x, the fastest
+ *    axis); nodes sit at x_a = j*dx, j = 0..N[a]-1.
+ *  - Field arguments are caller-owned DEVICE pointers to contiguous IEEE
+ *    double arrays: a scalar field has N[0]*...*N[d-1] entries with x
+ *    fastest; a vector field is d such arrays back to back (component a =
+ *    axis a first).  The library never frees or retains them past the call.
+ *  - The context owns its device state (two distribution buffers and a
+ *    small reduction scratch area); they are freed by lb_destroy.
+ *  - Work is enqueued on the CUDA stream given to lb_create, in call order.
+ *    Calls whose output lands in host memory (lb_set_theta0's positivity
+ *    check, lb_sum_theta, lb_reduce) synchronise that stream before they
+ *    return; the others are asynchronous.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+    LB_OK = 0,
+    LB_EINVAL = 1,   /* an argument is out of range or a pointer is NULL */
+    LB_ENOMEM = 2,   /* a device allocation failed */
+    LB_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    LB_ESTATE = 4,   /* called out of order (e.g. lb_step before lb_set_theta0) */
+    LB_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+    LB_ENONPOS = 6   /* theta <= 0 or non-finite where Cole-Hopf needs theta > 0 */
+} lb_status;
+
+typedef enum {
+    LB_FP64 = 0,         /* distributions stored and updated in IEEE double */
+    LB_FP32_SHIFTED = 1  /* stored and updated in float as f - w*theta_ref */
+} lb_precision;
+
+/*
+ * Relaxation set (Sec. III.A, Theorem 2).  With paper_set != 0 the fields
+ * s1, s2x, s22, w1, wd are ignored and taken from Eq. (Bur-Sol) with
+ * eps = nu*dt/dx^2:
+ *   s1 = 2/(6 eps + 1), s2x = 24 eps/(6 eps + 1)^2  (s_2 for d = 1, s_21 for
+ *   d > 1), s22 = 4/(6 eps + 3), w1 = 1/6 - (d-1) eps/3, wd = eps/6
+ *   (w1 = 1/6 and no wd for d = 1).
+ * Otherwise they are used as given (each rate must lie in (0, 2), Sec. III.A);
+ * w0 = 1 - 2d w1 - 2d(d-1) wd (Eq. (d1-3-weight)).  Weights need not be
+ * positive.  theta_ref is the reference value of LB_FP32_SHIFTED storage
+ * (typically the mean of theta0); it is ignored for LB_FP64.
+ */
+typedef struct {
+    int paper_set;
+    double s1, s2x, s22, w1, wd;
+    double theta_ref;
+} lb_relax;
+
+/*
+ * Create a solver context.
+ *   d        1, 2 or 3.
+ *   N        host array of d sizes, each >= 1 (a size of 1 makes that axis
+ *            trivially periodic); N[0] <= 2^24, product <= 2^31.
+ *   nu, dx, dt  viscosity, lattice spacing, time step (all > 0, finite);
+ *            c = dx/dt is the lattice speed.
+ *   rs       relaxation set (NULL = paper set, theta_ref = 0).
+ *   precision  LB_FP64 or LB_FP32_SHIFTED.
+ *   stream   a cudaStream_t (NULL = the legacy default stream).
+ *   out      receives the context; set to NULL on failure.
+ * Allocates 2*q*pitch*N[1]*N[2] distribution values on the current device.
+ * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA.
+ */
+lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt,
+                    const lb_relax *rs, int precision, void *stream, lb_ctx **out);
+
+/* Release the context and its device memory (after synchronising its stream). NULL is a no-op. */
+lb_status lb_destroy(lb_ctx *ctx);
+
+/*
+ * Parameters in use, written to out[0..13] (host):
+ *   eps, c, cs2 (= c_s^2, Eq. (conseved-moment)), s1, s2x, s22, w0, w1, wd,
+ *   nu, dx, dt, q, theta_ref.
+ */
+lb_status lb_get_params(const lb_ctx *ctx, double *out);
+
+/*
+ * Initialise the distributions from theta0 (Sec. IV: the first two terms of
+ * Eq. (f-feq-o5)):  f_i(x, 0) = w_i theta0 - dt [M^-1 S^-1 M Dbar (w theta0)]_i
+ * with Dbar = diag(c_i . grad).
+ *   theta0       device, scalar field, every value finite and > 0.
+ *   grad_theta0  device, vector field (d*nodes) holding grad theta0, or NULL
+ *                to use a fourth-order central difference of theta0.
+ * Resets the step counter to 0.  Synchronises the stream.
+ * Errors: LB_EINVAL (NULL theta0), LB_ENONPOS (theta0 <= 0 or non-finite
+ * somewhere, or a non-finite gradient; the state is then left uninitialised),
+ * LB_ECUDA.
+ */
+lb_status lb_set_theta0(lb_ctx *ctx, const double *theta0, const double *grad_theta0);
+
+/*
+ * Advance nsteps >= 0 time steps of Eq. (distribution-f): at every node the
+ * pre-collision f is pulled from the neighbours (streaming), relaxed in
+ * moment space (m* = m - S (m - m^eq), m^eq = M w theta) and stored.
+ * Asynchronous.  Errors: LB_EINVAL (nsteps < 0), LB_ESTATE (no
+ * lb_set_theta0 yet), LB_ECUDA.
+ */
+lb_status lb_step(lb_ctx *ctx, int64_t nsteps);
+
+/* Number of steps taken since the last lb_set_theta0 (host, no sync). */
+lb_status lb_get_step(const lb_ctx *ctx, int64_t *nsteps);
+
+/*
+ * Macroscopic recovery at the current time from the pre-collision f
+ * (Sec. III.C):
+ *   theta = sum_k f_k,
+ *   grad theta = -s1 sum_k c_k f^ne_k / (dt c_s^2)   (Eq. (nabla-theta)),
+ *   u_a = (2 - s1) sum_k c_ka f^ne_k / sum_k f_k     (Eq. (ui-compute)).
+ * All three are computed in FP64 (also for LB_FP32_SHIFTED).  Any output
+ * pointer may be NULL to skip it.  Device outputs: theta (nodes), grad_theta
+ * and u (d*nodes).  Asynchronous; a node with theta <= 0 or non-finite is
+ * recorded and reported by the next lb_reduce as LB_ENONPOS.
+ * Errors: LB_ESTATE, LB_ECUDA.
+ */
+lb_status lb_macros(lb_ctx *ctx, double *theta, double *grad_theta, double *u);
+
+/*
+ * Conserved total sum_x theta(x) = sum over nodes and populations of f,
+ * accumulated in FP64 (exactly conserved up to rounding on a periodic grid).
+ * out: host, 1 value.  Synchronises the stream.  Errors: LB_ESTATE, LB_ECUDA.
+ */
+lb_status lb_sum_theta(lb_ctx *ctx, double *out);
+
+/*
+ * Error norms of the recovered fields against reference fields (Sec. IV,
+ * RMSE per variable).  Device inputs: theta and exact_theta (nodes), u and
+ * exact_u (d*nodes; both NULL to skip the velocity).  Host output out, with
+ * V = 1 + d variables (theta, u_1, ..., u_d) and for variable v:
+ *   out[3v+0] = RMSE   = sqrt(sum (psi - psi*)^2 / nodes)
+ *   out[3v+1] = Linf   = max |psi - psi*|
+ *   out[3v+2] = rel L2 = sqrt(sum (psi - psi*)^2 / sum psi*^2)
+ * and out[3V] = sum theta.  FP64 with a deterministic two-level reduction
+ * (warp shuffles, then a fixed-order pass over per-block partials held in
+ * the context's scratch area).  Synchronises the stream.
+ * Errors: LB_EINVAL, LB_ENONPOS (a previous lb_macros saw theta <= 0), LB_ECUDA.
+ */
+lb_status lb_reduce(lb_ctx *ctx, const double *theta, const double *u,
+                    const double *exact_theta, const double *exact_u, double *out);
+
+/*
+ * Copy the raw distribution state to/from a caller buffer (checkpointing).
+ * The state is q arrays in the context's padded layout (lb_state_layout):
+ * value (i, x, y, z) sits at element i*slab + (z*N[1] + y)*pitch + x.
+ * Values are stored after collision and before streaming: the pre-collision
+ * distribution at the current step n is f_i(x, n) = state_i(x - e_i)
+ * (periodic).  For LB_FP32_SHIFTED the stored value is f - w_i*theta_ref.
+ * Padding entries (x >= N[0]) are ignored.  buf is a device pointer of
+ * q*slab*elem_bytes bytes.  lb_load_state sets the step counter to `step`.
+ */
+lb_status lb_state_layout(const lb_ctx *ctx, int64_t *pitch, int64_t *slab, int64_t *elem_bytes);
+lb_status lb_save_state(lb_ctx *ctx, void *buf);
+lb_status lb_load_state(lb_ctx *ctx, const void *buf, int64_t step);
+
+/* Message for the last failing call on ctx (or of lb_create, with ctx == NULL). */
+const char *lb_last_error(const lb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H */

@@ -1,0 +1,338 @@
+// C-ABI of the solver (declared in include/lb.h): argument checks, device
+// memory, parameters, and the order of kernel launches.  No arithmetic of
+// the method runs on the host beyond the scalar relaxation set.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "lb_internal.cuh"
+
+namespace {
+
+thread_local std::string g_create_err;
+
+lb_status fail(lb_ctx *c, lb_status s, const std::string &msg)
+{
+    if (c)
+        c->err = msg;
+    else
+        g_create_err = msg;
+    return s;
+}
+
+lb_status cuda_fail(lb_ctx *c, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(c, LB_ENOMEM, m);
+    return fail(c, LB_ECUDA, m);
+}
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+void free_ctx(lb_ctx *c)
+{
+    if (!c) return;
+    cudaFree(c->f[0]);
+    cudaFree(c->f[1]);
+    cudaFree(c->scratch);
+    cudaFree(c->dout);
+    cudaFree(c->dflag);
+    cudaFree(c->gradtmp);
+    delete c;
+}
+
+// Make the calling thread's current device the context's device.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(const lb_ctx *c)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != c->device) cudaSetDevice(c->device);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt, const lb_relax *rs, int precision,
+                    void *stream, lb_ctx **out)
+{
+    if (!out) return fail(nullptr, LB_EINVAL, "lb_create: out is NULL");
+    *out = nullptr;
+    if (d < 1 || d > 3) return fail(nullptr, LB_EINVAL, "lb_create: d must be 1, 2 or 3");
+    if (!N) return fail(nullptr, LB_EINVAL, "lb_create: N is NULL");
+    if (!finite_pos(nu) || !finite_pos(dx) || !finite_pos(dt))
+        return fail(nullptr, LB_EINVAL, "lb_create: nu, dx and dt must be finite and > 0");
+    if (precision != LB_FP64 && precision != LB_FP32_SHIFTED)
+        return fail(nullptr, LB_EINVAL, "lb_create: unknown precision");
+    int64_t nodes = 1;
+    for (int a = 0; a < d; ++a) {
+        if (N[a] < 1 || N[a] > (1 << 24)) return fail(nullptr, LB_EINVAL, "lb_create: each N must be in [1, 2^24]");
+        nodes *= N[a];
+        if (nodes > (int64_t(1) << 31)) return fail(nullptr, LB_EINVAL, "lb_create: more than 2^31 nodes");
+    }
+
+    lb_ctx *c = new (std::nothrow) lb_ctx();
+    if (!c) return fail(nullptr, LB_ENOMEM, "lb_create: host allocation failed");
+    c->d = d;
+    c->q = 1 + 2 * d * d;
+    for (int a = 0; a < 3; ++a) c->N[a] = (a < d) ? N[a] : 1;
+    c->nodes = nodes;
+    c->precision = precision;
+    c->nu = nu;
+    c->dx = dx;
+    c->dt = dt;
+    c->c = dx / dt;
+    c->eps = nu * dt / (dx * dx);
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+
+    // Relaxation set: Theorem 2, Eq. (Bur-Sol), or the caller's.
+    const bool paper = !rs || rs->paper_set;
+    if (paper) {
+        const double a = 6.0 * c->eps + 1.0;
+        c->s1 = 2.0 / a;
+        c->s2x = 24.0 * c->eps / (a * a);
+        if (d == 1) {
+            c->s22 = 1.0;
+            c->w1 = 1.0 / 6.0;
+            c->wd = 0.0;
+        } else {
+            c->s22 = 4.0 / (6.0 * c->eps + 3.0);
+            c->w1 = 1.0 / 6.0 - (d - 1) * c->eps / 3.0;
+            c->wd = c->eps / 6.0;
+        }
+    } else {
+        c->s1 = rs->s1;
+        c->s2x = rs->s2x;
+        c->s22 = (d > 1) ? rs->s22 : 1.0;
+        c->w1 = rs->w1;
+        c->wd = (d > 1) ? rs->wd : 0.0;
+    }
+    c->theta_ref = rs ? rs->theta_ref : 0.0;
+    const bool rates_ok = c->s1 > 0 && c->s1 < 2 && c->s2x > 0 && c->s2x < 2 && (d == 1 || (c->s22 > 0 && c->s22 < 2));
+    if (!rates_ok || !isfinite(c->w1) || !isfinite(c->wd) || !isfinite(c->theta_ref)) {
+        free_ctx(c);
+        return fail(nullptr, LB_EINVAL, "lb_create: relaxation rates must lie in (0, 2) and weights be finite");
+    }
+    // Eq. (d1-3-weight) and c_s^2 = [2 w1 + 4(d-1) wd] c^2.
+    c->w0 = 1.0 - 2.0 * d * c->w1 - 2.0 * d * (d - 1) * c->wd;
+    c->sigma = 2.0 * c->w1 + 4.0 * (d - 1) * c->wd;
+    c->cs2 = c->sigma * c->c * c->c;
+
+    // Layout.
+    const int V = (precision == LB_FP64) ? lbk::Vec<double>::V : lbk::Vec<float>::V;
+    c->elem = (precision == LB_FP64) ? 8 : 4;
+    lbk::Geom &g = c->geom;
+    g.N0 = (int)c->N[0];
+    g.N1 = (int)c->N[1];
+    g.N2 = (int)c->N[2];
+    const int segw = 32 * V;
+    g.pitch = (int)((c->N[0] + segw - 1) / segw * segw);
+    g.rows = c->N[1] * c->N[2];
+    g.slab = (int64_t)g.pitch * g.rows;
+    g.seg_per_row = g.pitch / segw;
+    g.nseg = g.rows * g.seg_per_row;
+
+    const size_t fbytes = (size_t)c->q * (size_t)g.slab * c->elem;
+    cudaError_t e;
+    for (int b = 0; b < 2; ++b) {
+        e = cudaMalloc(&c->f[b], fbytes);
+        if (e != cudaSuccess) {
+            free_ctx(c);
+            return cuda_fail(nullptr, e, "lb_create: state allocation");
+        }
+        e = cudaMemsetAsync(c->f[b], 0, fbytes, c->stream);
+        if (e != cudaSuccess) {
+            free_ctx(c);
+            return cuda_fail(nullptr, e, "lb_create: memset");
+        }
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    c->scratch_blocks = (sms > 0 ? sms : 148) * 4;
+    if ((e = cudaMalloc(&c->scratch, sizeof(double) * lbk::kRedSlots * c->scratch_blocks)) != cudaSuccess ||
+        (e = cudaMalloc(&c->dout, sizeof(double) * 64)) != cudaSuccess ||
+        (e = cudaMalloc(&c->dflag, sizeof(int) * 4)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->dflag, 0, sizeof(int) * 4, c->stream)) != cudaSuccess) {
+        free_ctx(c);
+        return cuda_fail(nullptr, e, "lb_create: scratch allocation");
+    }
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_destroy(lb_ctx *c)
+{
+    if (!c) return LB_OK;
+    DeviceGuard dg(c);
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+    return LB_OK;
+}
+
+lb_status lb_get_params(const lb_ctx *c, double *out)
+{
+    if (!c || !out) return LB_EINVAL;
+    const double v[14] = {c->eps, c->c,  c->cs2, c->s1, c->s2x, c->s22,       c->w0,
+                          c->w1,  c->wd, c->nu,  c->dx, c->dt,  (double)c->q, c->theta_ref};
+    memcpy(out, v, sizeof v);
+    return LB_OK;
+}
+
+lb_status lb_set_theta0(lb_ctx *c, const double *theta0, const double *grad)
+{
+    if (!c) return LB_EINVAL;
+    if (!theta0) return fail(c, LB_EINVAL, "lb_set_theta0: theta0 is NULL");
+    DeviceGuard dg(c);
+    cudaError_t e;
+    c->initialized = false;
+    if (!grad) {
+        if (!c->gradtmp) {
+            e = cudaMalloc(&c->gradtmp, sizeof(double) * c->d * c->nodes);
+            if (e != cudaSuccess) return cuda_fail(c, e, "lb_set_theta0: gradient buffer");
+        }
+        if ((e = lbk::launch_fd4_grad(c, theta0, c->gradtmp)) != cudaSuccess)
+            return cuda_fail(c, e, "lb_set_theta0: fd4 launch");
+        grad = c->gradtmp;
+    }
+    if ((e = cudaMemsetAsync(c->dflag, 0, sizeof(int), c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "lb_set_theta0: flag reset");
+    c->cur = 0;
+    if ((e = lbk::launch_init(c, theta0, grad, c->dflag)) != cudaSuccess)
+        return cuda_fail(c, e, "lb_set_theta0: init launch");
+    int flag = 0;
+    if ((e = cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "lb_set_theta0");
+    if (flag) return fail(c, LB_ENONPOS, "lb_set_theta0: theta0 must be finite and > 0 (and grad finite)");
+    c->initialized = true;
+    c->step = 0;
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx *c, int64_t nsteps)
+{
+    if (!c) return LB_EINVAL;
+    if (nsteps < 0) return fail(c, LB_EINVAL, "lb_step: nsteps < 0");
+    if (!c->initialized) return fail(c, LB_ESTATE, "lb_step: call lb_set_theta0 first");
+    DeviceGuard dg(c);
+    for (int64_t s = 0; s < nsteps; ++s) {
+        cudaError_t e = lbk::launch_sweep(c, c->f[c->cur], c->f[c->cur ^ 1]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lb_step: sweep launch");
+        c->cur ^= 1;
+        ++c->step;
+    }
+    return LB_OK;
+}
+
+lb_status lb_get_step(const lb_ctx *c, int64_t *n)
+{
+    if (!c || !n) return LB_EINVAL;
+    *n = c->step;
+    return LB_OK;
+}
+
+lb_status lb_macros(lb_ctx *c, double *theta, double *grad, double *u)
+{
+    if (!c) return LB_EINVAL;
+    if (!c->initialized) return fail(c, LB_ESTATE, "lb_macros: call lb_set_theta0 first");
+    if (!theta && !grad && !u) return LB_OK;
+    DeviceGuard dg(c);
+    cudaError_t e = lbk::launch_macros(c, c->f[c->cur], theta, grad, u, c->dflag + 1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lb_macros: launch");
+    return LB_OK;
+}
+
+lb_status lb_sum_theta(lb_ctx *c, double *out)
+{
+    if (!c || !out) return LB_EINVAL;
+    if (!c->initialized) return fail(c, LB_ESTATE, "lb_sum_theta: call lb_set_theta0 first");
+    DeviceGuard dg(c);
+    cudaError_t e = lbk::launch_sum_state(c, c->f[c->cur], c->dout);
+    double v = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lb_sum_theta");
+    if (c->precision != LB_FP64) v += c->theta_ref * (double)c->nodes;
+    *out = v;
+    return LB_OK;
+}
+
+lb_status lb_reduce(lb_ctx *c, const double *theta, const double *u, const double *ex_theta, const double *ex_u,
+                    double *out)
+{
+    if (!c || !out) return LB_EINVAL;
+    if (!theta || !ex_theta) return fail(c, LB_EINVAL, "lb_reduce: theta and exact_theta are required");
+    if ((u == nullptr) != (ex_u == nullptr)) return fail(c, LB_EINVAL, "lb_reduce: u and exact_u go together");
+    DeviceGuard dg(c);
+    const int ns = 3 * (c->d + 1) + 1;
+    cudaError_t e = lbk::launch_norms(c, theta, u, ex_theta, ex_u, c->dout);
+    double raw[lbk::kRedSlots];
+    int flag = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(raw, c->dout, sizeof(double) * ns, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&flag, c->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dflag + 1, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lb_reduce");
+    const double n = (double)c->nodes;
+    for (int v = 0; v <= c->d; ++v) {
+        const double se = raw[3 * v], mx = raw[3 * v + 1], sx = raw[3 * v + 2];
+        const bool have = (v == 0) || u;
+        out[3 * v + 0] = have ? sqrt(se / n) : NAN;
+        out[3 * v + 1] = have ? mx : NAN;
+        out[3 * v + 2] = have ? (sx > 0 ? sqrt(se / sx) : (se > 0 ? INFINITY : 0.0)) : NAN;
+    }
+    out[3 * (c->d + 1)] = raw[ns - 1];
+    if (flag) return fail(c, LB_ENONPOS, "lb_macros saw theta <= 0 or non-finite");
+    return LB_OK;
+}
+
+lb_status lb_state_layout(const lb_ctx *c, int64_t *pitch, int64_t *slab, int64_t *elem_bytes)
+{
+    if (!c) return LB_EINVAL;
+    if (pitch) *pitch = c->geom.pitch;
+    if (slab) *slab = c->geom.slab;
+    if (elem_bytes) *elem_bytes = (int64_t)c->elem;
+    return LB_OK;
+}
+
+lb_status lb_save_state(lb_ctx *c, void *buf)
+{
+    if (!c || !buf) return LB_EINVAL;
+    if (!c->initialized) return fail(c, LB_ESTATE, "lb_save_state: nothing to save");
+    DeviceGuard dg(c);
+    cudaError_t e = cudaMemcpyAsync(buf, c->f[c->cur], (size_t)c->q * c->geom.slab * c->elem,
+                                    cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lb_save_state");
+    return LB_OK;
+}
+
+lb_status lb_load_state(lb_ctx *c, const void *buf, int64_t step)
+{
+    if (!c || !buf || step < 0) return LB_EINVAL;
+    DeviceGuard dg(c);
+    cudaError_t e = cudaMemcpyAsync(c->f[c->cur], buf, (size_t)c->q * c->geom.slab * c->elem,
+                                    cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lb_load_state");
+    c->initialized = true;
+    c->step = step;
+    return LB_OK;
+}
+
+const char *lb_last_error(const lb_ctx *c)
+{
+    if (!c) return g_create_err.c_str();
+    return c->err.c_str();
+}
+
+}  // extern "C"

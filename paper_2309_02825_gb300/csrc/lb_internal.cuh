@@ -1,0 +1,126 @@
+// Internal declarations shared by the C-ABI layer and the kernels.
+//
+// Storage ("P form"): q arrays, one per discrete velocity, each a padded
+// grid [N2][N1][pitch] with x fastest.  The value stored at (i, x) after
+// step n is the post-collision f*_i(x, n-1); the pre-collision
+// distribution at step n is therefore f_i(x, n) = P_i(x - e_i) (periodic).
+// One sweep pulls those values, collides them and writes P_{n+1} aligned,
+// so every store is a full aligned vector and only loads are shifted.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <type_traits>
+
+#include "../../include/lb.h"
+
+namespace lbk {
+
+// ---------------------------------------------------------------------------
+// Lattices DdQ(1+2d^2) for d = 1, 2, 3 in lattice units e_i = c_i / c, in
+// the order printed in Eqs. (d1q3), (d2q9) and (d3q19).
+// ---------------------------------------------------------------------------
+struct D1Q3 {
+    static constexpr int D = 1, Q = 3;
+    static constexpr int E[Q][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}};
+};
+struct D2Q9 {
+    static constexpr int D = 2, Q = 9;
+    static constexpr int E[Q][3] = {{0, 0, 0},  {1, 0, 0},  {0, 1, 0},   {-1, 0, 0}, {0, -1, 0},
+                                    {1, 1, 0},  {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+};
+struct D3Q19 {
+    static constexpr int D = 3, Q = 19;
+    static constexpr int E[Q][3] = {
+        {0, 0, 0},   {1, 0, 0},  {0, 1, 0},   {0, 0, 1},  {-1, 0, 0}, {0, -1, 0}, {0, 0, -1},
+        {1, 1, 0},   {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {1, 0, 1},  {-1, 0, 1}, {-1, 0, -1},
+        {1, 0, -1},  {0, 1, 1},  {0, -1, 1},  {0, -1, -1}, {0, 1, -1}};
+};
+
+// Storage vector per thread: 16-byte loads/stores covering V consecutive x.
+template <typename T> struct Vec;
+template <> struct Vec<double> { using type = double2; static constexpr int V = 2; };
+template <> struct Vec<float> { using type = float4; static constexpr int V = 4; };
+
+// Grid geometry of one padded state array.
+struct Geom {
+    int N0, N1, N2;      // sizes (N1 = N2 = 1 for missing axes)
+    int pitch;           // row pitch in elements, a multiple of 32*V
+    int64_t slab;        // pitch*N1*N2: elements per population
+    int64_t rows;        // N1*N2
+    int seg_per_row;     // pitch / (32*V)
+    int64_t nseg;        // rows * seg_per_row (one warp per segment)
+};
+
+// Collision constants (lattice units), precomputed on the host from the
+// relaxation set.  With sigma = c_s^2/c^2 = 2 w1 + 4(d-1) wd the
+// post-collision distributions are
+//   f0*       = c0 theta - 2 k2 sum_a P_aa
+//   f(+-e_a)* = k2 P_aa + cA theta +- k1 J_a
+//   f(diag)*  = wd theta + sa*sb k3 P_ab
+// with k1 = (1-s1)/2, k2 = (1-s2x)/2, k3 = (1-s22)/4,
+// c0 = 1 - d s2x sigma + 2 d(d-1) wd and cA = s2x sigma/2 - 2(d-1) wd.
+template <typename T> struct Coll {
+    T k1, k2, k3, c0, cA, wd;
+};
+
+// Recovery constants (Sec. III.C): u_a = ucoef * J_a / theta with
+// ucoef = (2 - s1) c; grad_a = gcoef * J_a with gcoef = -s1 / (sigma dx);
+// J_a = sum_k e_ka f_k.
+struct Recov {
+    double ucoef, gcoef, theta_ref;
+};
+
+// Initialisation constants (first two terms of Eq. (f-feq-o5), closed
+// form): f0 = w0 th; f(+-e_a) = w1 th -+ iax * d_a th;
+// f(diag e) = wd th - idg * (e . grad th).
+struct InitK {
+    double w0, w1, wd, iax, idg, theta_ref;
+};
+
+}  // namespace lbk
+
+// ---------------------------------------------------------------------------
+// Context.
+// ---------------------------------------------------------------------------
+struct lb_ctx {
+    int d = 0, q = 0;
+    int64_t N[3] = {1, 1, 1};
+    int64_t nodes = 0;
+    int precision = LB_FP64;
+    double nu = 0, dx = 0, dt = 0, c = 0, eps = 0, cs2 = 0, sigma = 0;
+    double s1 = 0, s2x = 0, s22 = 1, w0 = 0, w1 = 0, wd = 0, theta_ref = 0;
+    cudaStream_t stream = nullptr;
+    lbk::Geom geom{};
+    size_t elem = 8;
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;
+    double *scratch = nullptr;     // reduction partials
+    int scratch_blocks = 0;
+    double *dout = nullptr;        // small device result area
+    int *dflag = nullptr;          // device status flags
+    double *gradtmp = nullptr;     // FD gradient when none is supplied
+    bool initialized = false;
+    int64_t step = 0;
+    int device = 0;
+    std::string err;
+};
+
+namespace lbk {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedSlots = 16;  // doubles per block partial (>= 3*(d+1)+1)
+
+// Launchers (lb_kernels.cu).  All enqueue on ctx->stream and return the
+// launch error.
+cudaError_t launch_fd4_grad(const lb_ctx *c, const double *theta0, double *grad);
+cudaError_t launch_init(lb_ctx *c, const double *theta0, const double *grad, int *flag);
+cudaError_t launch_sweep(lb_ctx *c, const void *src, void *dst);
+cudaError_t launch_macros(lb_ctx *c, const void *src, double *theta, double *grad, double *u, int *flag);
+cudaError_t launch_sum_state(lb_ctx *c, const void *src, double *out_dev);
+cudaError_t launch_norms(lb_ctx *c, const double *theta, const double *u, const double *ex_theta,
+                         const double *ex_u, double *out_dev);
+
+}  // namespace lbk

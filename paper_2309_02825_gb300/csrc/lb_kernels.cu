@@ -1,0 +1,620 @@
+// CUDA kernels of the MRT-LB hot path (sm_103a).
+//
+// Sweep = pull-stream + MRT collision of Eq. (distribution-f), fused, one
+// warp per row segment of 32*V nodes (V = 2 doubles or 4 floats per thread,
+// one 16-byte vector per population).  Populations with e_x = 0 are plain
+// aligned vector loads; e_x = +-1 shifts by one element, done with an
+// aligned vector load plus one warp shuffle, and a scalar load only at the
+// warp edge and the periodic wrap.  Every store is an aligned vector.
+//
+// The collision is written in moment space in closed form (no q x q
+// product): from theta, J_a = sum e_a f, P_aa = sum e_a^2 f and
+// P_ab = sum e_a e_b f the relaxed moments follow from S; third-order
+// moments relax to 0 and fourth-order ones to 4 wd theta (rate 1), so they
+// are never formed; M^-1 is applied analytically.
+#include <math.h>
+
+#include "lb_internal.cuh"
+
+namespace lbk {
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
+    }
+}
+
+__device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+__device__ __forceinline__ void ld_vec(const double *p, double (&a)[2])
+{
+    double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    a[0] = v.x;
+    a[1] = v.y;
+}
+__device__ __forceinline__ void ld_vec(const float *p, float (&a)[4])
+{
+    float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    a[0] = v.x;
+    a[1] = v.y;
+    a[2] = v.z;
+    a[3] = v.w;
+}
+__device__ __forceinline__ void st_vec(double *p, const double (&a)[2])
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(a[0], a[1]);
+}
+__device__ __forceinline__ void st_vec(float *p, const float (&a)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(a[0], a[1], a[2], a[3]);
+}
+
+// Pull V consecutive values of one population along x with shift EX:
+// out[k] = row[(xb + k - EX) mod N0] for the valid nodes xb + k < N0 of this
+// lane (xb = x0 + V*lane).  Values for padding nodes are unspecified but
+// every access stays inside the row (the pitch is a multiple of 32*V).
+// Must be called by all 32 lanes of the warp together.
+template <typename T, int EX>
+__device__ __forceinline__ void pull_row(const T *__restrict__ row, int x0, int lane, int N0,
+                                         T (&out)[Vec<T>::V])
+{
+    constexpr int V = Vec<T>::V;
+    const int xb = x0 + V * lane;
+    T a[V];
+    ld_vec(row + xb, a);
+    if constexpr (EX == 0) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) out[k] = a[k];
+    } else if constexpr (EX == 1) {
+        T left = __shfl_up_sync(0xffffffffu, a[V - 1], 1);
+        if (lane == 0) left = row[xb == 0 ? N0 - 1 : xb - 1];
+        out[0] = left;
+#pragma unroll
+        for (int k = 1; k < V; ++k) out[k] = a[k - 1];
+    } else {
+        T right = __shfl_down_sync(0xffffffffu, a[0], 1);
+#pragma unroll
+        for (int k = 0; k < V - 1; ++k) out[k] = a[k + 1];
+        out[V - 1] = right;
+        if (lane == 31 || xb + V >= N0) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                const int x = xb + k;
+                if (x + 1 == N0)
+                    out[k] = row[0];
+                else if (k == V - 1 && lane == 31 && x + 1 < N0)
+                    out[k] = row[x + 1];
+            }
+        }
+    }
+}
+
+// Gather the pre-collision f(x, n) for the V nodes of this lane.
+template <class L, typename T>
+__device__ __forceinline__ void gather(const T *__restrict__ src, const Geom &g, int64_t row, int x0, int lane,
+                                       T (&f)[L::Q][Vec<T>::V])
+{
+    const int y = (int)(row % g.N1);
+    const int z = (int)(row / g.N1);
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
+        const int ys = (ey == 0) ? y : wrapi(y - ey, g.N1);
+        const int zs = (ez == 0) ? z : wrapi(z - ez, g.N2);
+        const T *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
+        pull_row<T, ex>(rp, x0, lane, g.N0, f[i]);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Collision, in place on one node's q values.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void collide(D1Q3, T *f, const Coll<T> &k)
+{
+    const T P = f[1] + f[2];
+    const T th = f[0] + P;
+    const T J = f[1] - f[2];
+    const T A = fma(k.k2, P, k.cA * th);
+    const T B = k.k1 * J;
+    f[0] = fma(-2 * k.k2, P, k.c0 * th);
+    f[1] = A + B;
+    f[2] = A - B;
+}
+
+template <typename T>
+__device__ __forceinline__ void collide(D2Q9, T *f, const Coll<T> &k)
+{
+    const T a = f[1] + f[3], b = f[2] + f[4];
+    const T p = f[5] + f[7], r = f[6] + f[8];
+    const T Fd = p + r;
+    const T th = (f[0] + a) + (b + Fd);
+    const T Pxx = a + Fd, Pyy = b + Fd, Pxy = p - r;
+    const T g = f[5] - f[7], h = f[8] - f[6];
+    const T Jx = (f[1] - f[3]) + (g + h);
+    const T Jy = (f[2] - f[4]) + (g - h);
+    const T cth = k.cA * th;
+    const T Ax = fma(k.k2, Pxx, cth), Bx = k.k1 * Jx;
+    const T Ay = fma(k.k2, Pyy, cth), By = k.k1 * Jy;
+    const T wth = k.wd * th;
+    const T dp = fma(k.k3, Pxy, wth), dm = fma(-k.k3, Pxy, wth);
+    f[0] = fma(-2 * k.k2, Pxx + Pyy, k.c0 * th);
+    f[1] = Ax + Bx;
+    f[3] = Ax - Bx;
+    f[2] = Ay + By;
+    f[4] = Ay - By;
+    f[5] = dp;
+    f[7] = dp;
+    f[6] = dm;
+    f[8] = dm;
+}
+
+// One coordinate plane (a, b) of D3Q19: g0..g3 are the velocities with
+// (e_a, e_b) = (1,1), (-1,1), (-1,-1), (1,-1).
+template <typename T> struct Plane {
+    T F, P, Ja, Jb;
+};
+template <typename T> __device__ __forceinline__ Plane<T> plane(T g0, T g1, T g2, T g3)
+{
+    const T p = g0 + g2, r = g1 + g3;
+    const T u = g0 - g2, v = g3 - g1;
+    return {p + r, p - r, u + v, u - v};
+}
+
+template <typename T>
+__device__ __forceinline__ void collide(D3Q19, T *f, const Coll<T> &k)
+{
+    const Plane<T> xy = plane(f[7], f[8], f[9], f[10]);
+    const Plane<T> xz = plane(f[11], f[12], f[13], f[14]);
+    const Plane<T> yz = plane(f[15], f[16], f[17], f[18]);
+    const T ax = f[1] + f[4], ay = f[2] + f[5], az = f[3] + f[6];
+    const T th = (f[0] + (ax + ay) + az) + ((xy.F + xz.F) + yz.F);
+    const T Pxx = ax + (xy.F + xz.F);
+    const T Pyy = ay + (xy.F + yz.F);
+    const T Pzz = az + (xz.F + yz.F);
+    const T Jx = (f[1] - f[4]) + (xy.Ja + xz.Ja);
+    const T Jy = (f[2] - f[5]) + (xy.Jb + yz.Ja);
+    const T Jz = (f[3] - f[6]) + (xz.Jb + yz.Jb);
+    const T cth = k.cA * th;
+    const T wth = k.wd * th;
+    f[0] = fma(-2 * k.k2, (Pxx + Pyy) + Pzz, k.c0 * th);
+    {
+        const T A = fma(k.k2, Pxx, cth), B = k.k1 * Jx;
+        f[1] = A + B;
+        f[4] = A - B;
+    }
+    {
+        const T A = fma(k.k2, Pyy, cth), B = k.k1 * Jy;
+        f[2] = A + B;
+        f[5] = A - B;
+    }
+    {
+        const T A = fma(k.k2, Pzz, cth), B = k.k1 * Jz;
+        f[3] = A + B;
+        f[6] = A - B;
+    }
+    {
+        const T dp = fma(k.k3, xy.P, wth), dm = fma(-k.k3, xy.P, wth);
+        f[7] = dp; f[9] = dp; f[8] = dm; f[10] = dm;
+    }
+    {
+        const T dp = fma(k.k3, xz.P, wth), dm = fma(-k.k3, xz.P, wth);
+        f[11] = dp; f[13] = dp; f[12] = dm; f[14] = dm;
+    }
+    {
+        const T dp = fma(k.k3, yz.P, wth), dm = fma(-k.k3, yz.P, wth);
+        f[15] = dp; f[17] = dp; f[16] = dm; f[18] = dm;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sweep kernel.
+// ---------------------------------------------------------------------------
+constexpr int kSweepThreads = 256;
+
+template <class L, typename T>
+__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const T *__restrict__ src, T *__restrict__ dst,
+                                                              Geom g, Coll<T> k)
+{
+    constexpr int V = Vec<T>::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t seg = (int64_t)blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
+    if (seg >= g.nseg) return;  // warp-uniform
+    const int64_t row = seg / g.seg_per_row;
+    const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
+
+    T f[L::Q][V];
+    gather<L, T>(src, g, row, x0, lane, f);
+
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        T n[L::Q];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) n[i] = f[i][v];
+        collide(L{}, n, k);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) f[i][v] = n[i];
+    }
+
+    T *dp = dst + row * g.pitch + x0 + V * lane;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, f[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Recovery (Sec. III.C) from the pulled pre-collision f.
+// ---------------------------------------------------------------------------
+template <class L, typename T>
+__global__ void __launch_bounds__(kSweepThreads) macros_kernel(const T *__restrict__ src, Geom g, Recov r,
+                                                               double *__restrict__ theta,
+                                                               double *__restrict__ grad,
+                                                               double *__restrict__ u, int *__restrict__ flag)
+{
+    constexpr int V = Vec<T>::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t seg = (int64_t)blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
+    if (seg >= g.nseg) return;
+    const int64_t row = seg / g.seg_per_row;
+    const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
+
+    T f[L::Q][V];
+    gather<L, T>(src, g, row, x0, lane, f);
+
+    const int64_t nodes = (int64_t)g.N0 * g.rows;
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int x = x0 + V * lane + v;
+        if (x >= g.N0) continue;
+        double th = r.theta_ref;
+        double J[3] = {0.0, 0.0, 0.0};
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const double fv = (double)f[i][v];
+            th += fv;
+            static_for<0, L::D>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                constexpr int e = L::E[i][a];
+                if constexpr (e == 1) J[a] += fv;
+                if constexpr (e == -1) J[a] -= fv;
+            });
+        });
+        const int64_t node = row * g.N0 + x;
+        if (theta) theta[node] = th;
+        if (!(th > 0.0) || !isfinite(th)) bad = true;
+        const double inv = 1.0 / th;
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) {
+            if (grad) grad[a * nodes + node] = r.gcoef * J[a];
+            if (u) u[a * nodes + node] = r.ucoef * J[a] * inv;
+        }
+    }
+    if (bad) atomicOr(flag, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation, written in P form: P_0(y, i) = f_i(y + e_i, 0) with
+// f_i = w_i theta0 - dt [M^-1 S^-1 M Dbar f^eq]_i in closed form.
+// ---------------------------------------------------------------------------
+template <class L, typename T>
+__global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *__restrict__ theta0,
+                            const double *__restrict__ grad, int *__restrict__ flag)
+{
+    const int64_t nodes = (int64_t)g.N0 * g.rows;
+    const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= nodes) return;
+    const int x = (int)(node % g.N0);
+    const int64_t rw = node / g.N0;
+    const int y = (int)(rw % g.N1);
+    const int z = (int)(rw / g.N1);
+    {
+        const double t0 = theta0[node];
+        bool bad = !(t0 > 0.0) || !isfinite(t0);
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) bad |= !isfinite(grad[a * nodes + node]);
+        if (bad) atomicOr(flag, 1);
+    }
+    T *out = dst + ((int64_t)z * g.N1 + y) * g.pitch + x;
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
+        const int xs = wrapi(x + ex, g.N0);
+        const int ys = wrapi(y + ey, g.N1);
+        const int zs = wrapi(z + ez, g.N2);
+        const int64_t src = ((int64_t)zs * g.N1 + ys) * g.N0 + xs;
+        const double th = theta0[src];
+        double val;
+        constexpr int nz = (ex != 0) + (ey != 0) + (ez != 0);
+        if constexpr (nz == 0) {
+            val = K.w0 * th;
+        } else if constexpr (nz == 1) {
+            constexpr int a = (ex != 0) ? 0 : ((ey != 0) ? 1 : 2);
+            constexpr int s = (ex != 0) ? ex : ((ey != 0) ? ey : ez);
+            val = K.w1 * th - (double)s * K.iax * grad[a * nodes + src];
+            val -= K.w1 * K.theta_ref;
+        } else {
+            double edg = 0.0;
+            if constexpr (ex != 0) edg += (double)ex * grad[src];
+            if constexpr (ey != 0) edg += (double)ey * grad[nodes + src];
+            if constexpr (ez != 0) edg += (double)ez * grad[2 * nodes + src];
+            val = K.wd * th - K.idg * edg;
+            val -= K.wd * K.theta_ref;
+        }
+        if constexpr (nz == 0) val -= K.w0 * K.theta_ref;
+        out[(int64_t)i * g.slab] = (T)val;
+    });
+}
+
+// Fourth-order central difference of theta along each axis (periodic).
+__global__ void fd4_kernel(const double *__restrict__ th, double *__restrict__ grad, int d, int N0, int N1,
+                           int N2, double inv12dx)
+{
+    const int64_t nodes = (int64_t)N0 * N1 * N2;
+    const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= nodes) return;
+    const int x = (int)(node % N0);
+    const int64_t rw = node / N0;
+    const int y = (int)(rw % N1);
+    const int z = (int)(rw / N1);
+    const int n[3] = {N0, N1, N2};
+    for (int a = 0; a < d; ++a) {
+        double acc = 0.0;
+        const int off[4] = {2, 1, -1, -2};
+        const double cof[4] = {-1.0, 8.0, -8.0, 1.0};
+        for (int k = 0; k < 4; ++k) {
+            int c[3] = {x, y, z};
+            c[a] = ((c[a] + off[k]) % n[a] + n[a]) % n[a];
+            acc += cof[k] * th[((int64_t)c[2] * N1 + c[1]) * N0 + c[0]];
+        }
+        grad[a * nodes + node] = acc * inv12dx;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic FP64 reductions: per-block partials (warp shuffles, then
+// shared memory), then one block folds the partials in a fixed order.
+// ---------------------------------------------------------------------------
+template <int NS> struct Acc {
+    double v[NS];
+};
+
+// op[k]: 0 = sum, 1 = max
+template <int NS>
+__device__ __forceinline__ void block_reduce_store(Acc<NS> &a, const int (&op)[NS], double *dst)
+{
+    __shared__ double sh[kRedThreads / 32][NS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double t = __shfl_xor_sync(0xffffffffu, a.v[k], o);
+            a.v[k] = op[k] ? fmax(a.v[k], t) : a.v[k] + t;
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) sh[wid][k] = a.v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < NS) {
+        const int k = threadIdx.x;
+        double s = sh[0][k];
+        for (int w = 1; w < kRedThreads / 32; ++w) s = op[k] ? fmax(s, sh[w][k]) : s + sh[w][k];
+        dst[k] = s;
+    }
+}
+
+// Sum of the stored state over populations and valid nodes.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) sum_state_kernel(const T *__restrict__ src, Geom g, int q,
+                                                                double *__restrict__ partial)
+{
+    Acc<1> a{{0.0}};
+    const int64_t total = (int64_t)q * g.rows * g.N0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(t % g.N0);
+        const int64_t rr = t / g.N0;  // population * rows + row
+        a.v[0] += (double)src[rr * g.pitch + x];
+    }
+    const int op[1] = {0};
+    block_reduce_store<1>(a, op, partial + (int64_t)blockIdx.x * kRedSlots);
+}
+
+// Error norms: slots 3v+0 sum err^2, 3v+1 max |err|, 3v+2 sum exact^2 for
+// v = 0 (theta), 1..d (u); slot 3(d+1) = sum theta.
+template <int D>
+__global__ void __launch_bounds__(kRedThreads) norms_kernel(const double *__restrict__ th,
+                                                            const double *__restrict__ u,
+                                                            const double *__restrict__ eth,
+                                                            const double *__restrict__ eu, int64_t nodes,
+                                                            double *__restrict__ partial)
+{
+    constexpr int NS = 3 * (D + 1) + 1;
+    Acc<NS> a;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) a.v[k] = 0.0;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < nodes;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        const double t = th[n], te = eth[n];
+        const double e = t - te;
+        a.v[0] += e * e;
+        a.v[1] = fmax(a.v[1], fabs(e));
+        a.v[2] += te * te;
+        a.v[NS - 1] += t;
+        if (u) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const double uv = u[c * nodes + n], ue = eu[c * nodes + n];
+                const double eu2 = uv - ue;
+                a.v[3 * (c + 1) + 0] += eu2 * eu2;
+                a.v[3 * (c + 1) + 1] = fmax(a.v[3 * (c + 1) + 1], fabs(eu2));
+                a.v[3 * (c + 1) + 2] += ue * ue;
+            }
+        }
+    }
+    int op[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) op[k] = (k < NS - 1 && k % 3 == 1) ? 1 : 0;
+    block_reduce_store<NS>(a, op, partial + (int64_t)blockIdx.x * kRedSlots);
+}
+
+// Fold nb partial rows of kRedSlots in a fixed order.  opmask bit k = max.
+__global__ void __launch_bounds__(kRedThreads) fold_kernel(const double *__restrict__ partial, int nb, int ns,
+                                                           unsigned opmask, double *__restrict__ out)
+{
+    __shared__ double sh[kRedThreads];
+    for (int k = 0; k < ns; ++k) {
+        const bool mx = (opmask >> k) & 1u;
+        double s = mx ? 0.0 : 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const double v = partial[(int64_t)b * kRedSlots + k];
+            s = mx ? fmax(s, v) : s + v;
+        }
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sh[threadIdx.x] = mx ? fmax(sh[threadIdx.x], sh[threadIdx.x + w])
+                                                       : sh[threadIdx.x] + sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] = sh[0];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side dispatch.
+// ---------------------------------------------------------------------------
+template <typename T> static Coll<T> make_coll(const lb_ctx *c)
+{
+    const double d = c->d;
+    const double s2x = c->s2x, s22 = (c->d > 1) ? c->s22 : 1.0, wd = (c->d > 1) ? c->wd : 0.0;
+    Coll<T> k;
+    k.k1 = (T)((1.0 - c->s1) / 2.0);
+    k.k2 = (T)((1.0 - s2x) / 2.0);
+    k.k3 = (T)((1.0 - s22) / 4.0);
+    k.c0 = (T)(1.0 - d * s2x * c->sigma + 2.0 * d * (d - 1.0) * wd);
+    k.cA = (T)(s2x * c->sigma / 2.0 - 2.0 * (d - 1.0) * wd);
+    k.wd = (T)wd;
+    return k;
+}
+
+static int64_t sweep_blocks(const Geom &g) { return (g.nseg + kSweepThreads / 32 - 1) / (kSweepThreads / 32); }
+
+template <class L, typename T> static cudaError_t sweep_t(lb_ctx *c, const void *src, void *dst)
+{
+    sweep_kernel<L, T><<<(unsigned)sweep_blocks(c->geom), kSweepThreads, 0, c->stream>>>(
+        (const T *)src, (T *)dst, c->geom, make_coll<T>(c));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(lb_ctx *c, const void *src, void *dst)
+{
+    const bool f64 = c->precision == LB_FP64;
+    switch (c->d) {
+    case 1: return f64 ? sweep_t<D1Q3, double>(c, src, dst) : sweep_t<D1Q3, float>(c, src, dst);
+    case 2: return f64 ? sweep_t<D2Q9, double>(c, src, dst) : sweep_t<D2Q9, float>(c, src, dst);
+    default: return f64 ? sweep_t<D3Q19, double>(c, src, dst) : sweep_t<D3Q19, float>(c, src, dst);
+    }
+}
+
+static Recov make_recov(const lb_ctx *c)
+{
+    Recov r;
+    r.ucoef = (2.0 - c->s1) * c->c;
+    r.gcoef = -c->s1 / (c->sigma * c->dx);
+    r.theta_ref = (c->precision == LB_FP64) ? 0.0 : c->theta_ref;
+    return r;
+}
+
+template <class L, typename T>
+static cudaError_t macros_t(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
+{
+    macros_kernel<L, T><<<(unsigned)sweep_blocks(c->geom), kSweepThreads, 0, c->stream>>>(
+        (const T *)src, c->geom, make_recov(c), th, gr, u, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macros(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
+{
+    const bool f64 = c->precision == LB_FP64;
+    switch (c->d) {
+    case 1: return f64 ? macros_t<D1Q3, double>(c, src, th, gr, u, flag) : macros_t<D1Q3, float>(c, src, th, gr, u, flag);
+    case 2: return f64 ? macros_t<D2Q9, double>(c, src, th, gr, u, flag) : macros_t<D2Q9, float>(c, src, th, gr, u, flag);
+    default: return f64 ? macros_t<D3Q19, double>(c, src, th, gr, u, flag) : macros_t<D3Q19, float>(c, src, th, gr, u, flag);
+    }
+}
+
+cudaError_t launch_fd4_grad(const lb_ctx *c, const double *theta0, double *grad)
+{
+    const int64_t nodes = c->nodes;
+    fd4_kernel<<<(unsigned)((nodes + 255) / 256), 256, 0, c->stream>>>(
+        theta0, grad, c->d, (int)c->N[0], (int)c->N[1], (int)c->N[2], 1.0 / (12.0 * c->dx));
+    return cudaGetLastError();
+}
+
+template <class L, typename T>
+static cudaError_t init_t(lb_ctx *c, const double *theta0, const double *grad, int *flag)
+{
+    InitK K;
+    const double d = c->d;
+    const double wd = (c->d > 1) ? c->wd : 0.0;
+    K.w0 = c->w0;
+    K.w1 = c->w1;
+    K.wd = wd;
+    K.iax = 0.5 * c->dx * (c->sigma / c->s1 - 4.0 * (d - 1.0) * wd);
+    K.idg = wd * c->dx;
+    K.theta_ref = (c->precision == LB_FP64) ? 0.0 : c->theta_ref;
+    init_kernel<L, T><<<(unsigned)((c->nodes + 255) / 256), 256, 0, c->stream>>>(
+        (T *)c->f[c->cur], c->geom, K, theta0, grad, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(lb_ctx *c, const double *theta0, const double *grad, int *flag)
+{
+    const bool f64 = c->precision == LB_FP64;
+    switch (c->d) {
+    case 1: return f64 ? init_t<D1Q3, double>(c, theta0, grad, flag) : init_t<D1Q3, float>(c, theta0, grad, flag);
+    case 2: return f64 ? init_t<D2Q9, double>(c, theta0, grad, flag) : init_t<D2Q9, float>(c, theta0, grad, flag);
+    default: return f64 ? init_t<D3Q19, double>(c, theta0, grad, flag) : init_t<D3Q19, float>(c, theta0, grad, flag);
+    }
+}
+
+cudaError_t launch_sum_state(lb_ctx *c, const void *src, double *out_dev)
+{
+    const int nb = c->scratch_blocks;
+    if (c->precision == LB_FP64)
+        sum_state_kernel<double><<<nb, kRedThreads, 0, c->stream>>>((const double *)src, c->geom, c->q, c->scratch);
+    else
+        sum_state_kernel<float><<<nb, kRedThreads, 0, c->stream>>>((const float *)src, c->geom, c->q, c->scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    fold_kernel<<<1, kRedThreads, 0, c->stream>>>(c->scratch, nb, 1, 0u, out_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norms(lb_ctx *c, const double *th, const double *u, const double *eth, const double *eu,
+                         double *out_dev)
+{
+    const int nb = c->scratch_blocks;
+    const int ns = 3 * (c->d + 1) + 1;
+    unsigned mask = 0;
+    for (int k = 0; k < ns - 1; ++k)
+        if (k % 3 == 1) mask |= 1u << k;
+    switch (c->d) {
+    case 1: norms_kernel<1><<<nb, kRedThreads, 0, c->stream>>>(th, u, eth, eu, c->nodes, c->scratch); break;
+    case 2: norms_kernel<2><<<nb, kRedThreads, 0, c->stream>>>(th, u, eth, eu, c->nodes, c->scratch); break;
+    default: norms_kernel<3><<<nb, kRedThreads, 0, c->stream>>>(th, u, eth, eu, c->nodes, c->scratch); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    fold_kernel<<<1, kRedThreads, 0, c->stream>>>(c->scratch, nb, ns, mask, out_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace lbk

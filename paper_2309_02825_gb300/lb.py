@@ -1,0 +1,290 @@
+"""Thin ctypes binding of the C ABI in include/lb.h (argument marshalling only).
+
+The functions ``lb_create``, ``lb_set_theta0``, ``lb_step``, ``lb_macros``,
+``lb_sum_theta``, ``lb_reduce``, ... keep the C names and signatures but take
+torch tensors for device arrays; :class:`Solver` wraps one context.  Every
+step of the method runs in the library's CUDA kernels; there is no Python or
+CPU fallback: if the compiled library is missing or no GPU is present, the
+calls raise.
+
+Array conventions (as in the C ABI): scalar fields are contiguous float64
+CUDA tensors of shape (N[d-1], ..., N[0]) (x fastest); vector fields have a
+leading axis of length d, entry a being the component along axis a.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ESTATE, LB_ETIMEOUT, LB_ENONPOS = range(7)
+LB_FP64, LB_FP32_SHIFTED = 0, 1
+_STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ESTATE",
+           5: "LB_ETIMEOUT", 6: "LB_ENONPOS"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class lb_relax(ctypes.Structure):
+    _fields_ = [("paper_set", ctypes.c_int), ("s1", ctypes.c_double), ("s2x", ctypes.c_double),
+                ("s22", ctypes.c_double), ("w1", ctypes.c_double), ("wd", ctypes.c_double),
+                ("theta_ref", ctypes.c_double)]
+
+
+def library_path():
+    return _build.LIB
+
+
+def load():
+    """Load the compiled library (building it if the toolkit is present)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB) or not _build.up_to_date():
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        p64 = ctypes.POINTER(ctypes.c_int64)
+        pd = ctypes.POINTER(ctypes.c_double)
+        sigs = {
+            "lb_create": ([ctypes.c_int, p64, dbl, dbl, dbl, ctypes.POINTER(lb_relax), ctypes.c_int, vp,
+                           ctypes.POINTER(vp)], ctypes.c_int),
+            "lb_destroy": ([vp], ctypes.c_int),
+            "lb_get_params": ([vp, pd], ctypes.c_int),
+            "lb_set_theta0": ([vp, vp, vp], ctypes.c_int),
+            "lb_step": ([vp, i64], ctypes.c_int),
+            "lb_get_step": ([vp, p64], ctypes.c_int),
+            "lb_macros": ([vp, vp, vp, vp], ctypes.c_int),
+            "lb_sum_theta": ([vp, pd], ctypes.c_int),
+            "lb_reduce": ([vp, vp, vp, vp, vp, pd], ctypes.c_int),
+            "lb_state_layout": ([vp, p64, p64, p64], ctypes.c_int),
+            "lb_save_state": ([vp, vp], ctypes.c_int),
+            "lb_load_state": ([vp, vp, i64], ctypes.c_int),
+            "lb_last_error": ([vp], ctypes.c_char_p),
+        }
+        for name, (args, res) in sigs.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _ptr(t, what, dtype=torch.float64, numel=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % what)
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous %s tensor" % (what, dtype))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s must have %d elements, got %d" % (what, numel, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(lib, ctx, status, call):
+    if status != LB_OK:
+        msg = lib.lb_last_error(ctx)
+        raise LBError(status, "%s: %s" % (call, msg.decode() if msg else ""))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# --------------------------------------------------------------------------
+# Same names as the C ABI.
+# --------------------------------------------------------------------------
+
+def lb_create(d, N, nu, dx, dt, relax=None, precision=LB_FP64, stream=None):
+    lib = load()
+    arr = (ctypes.c_int64 * 3)(*[int(n) for n in N])
+    rs = lb_relax(1, 0, 0, 0, 0, 0, 0.0)
+    if relax is not None:
+        if relax.get("paper_set", False) or "s1" not in relax:
+            rs.paper_set = 1
+        else:
+            rs.paper_set = 0
+            rs.s1, rs.s2x, rs.s22 = relax["s1"], relax["s2x"], relax.get("s22", 1.0)
+            rs.w1, rs.wd = relax["w1"], relax.get("wd", 0.0)
+        rs.theta_ref = float(relax.get("theta_ref", 0.0))
+    out = ctypes.c_void_p()
+    st = lib.lb_create(int(d), arr, float(nu), float(dx), float(dt), ctypes.byref(rs), int(precision),
+                       _stream_handle(stream), ctypes.byref(out))
+    _check(lib, None, st, "lb_create")
+    return out
+
+
+def lb_destroy(ctx):
+    load().lb_destroy(ctx)
+
+
+def lb_get_params(ctx):
+    lib = load()
+    buf = (ctypes.c_double * 14)()
+    _check(lib, ctx, lib.lb_get_params(ctx, buf), "lb_get_params")
+    keys = ("eps", "c", "cs2", "s1", "s2x", "s22", "w0", "w1", "wd", "nu", "dx", "dt", "q", "theta_ref")
+    return dict(zip(keys, list(buf)))
+
+
+def lb_set_theta0(ctx, theta0, grad_theta0=None, nodes=None, d=None):
+    lib = load()
+    n = nodes
+    st = lib.lb_set_theta0(ctx, _ptr(theta0, "theta0", numel=n),
+                           _ptr(grad_theta0, "grad_theta0", numel=None if n is None else n * d))
+    _check(lib, ctx, st, "lb_set_theta0")
+
+
+def lb_step(ctx, nsteps):
+    lib = load()
+    _check(lib, ctx, lib.lb_step(ctx, int(nsteps)), "lb_step")
+
+
+def lb_get_step(ctx):
+    lib = load()
+    v = ctypes.c_int64()
+    _check(lib, ctx, lib.lb_get_step(ctx, ctypes.byref(v)), "lb_get_step")
+    return v.value
+
+
+def lb_macros(ctx, theta=None, grad_theta=None, u=None):
+    lib = load()
+    st = lib.lb_macros(ctx, _ptr(theta, "theta"), _ptr(grad_theta, "grad_theta"), _ptr(u, "u"))
+    _check(lib, ctx, st, "lb_macros")
+
+
+def lb_sum_theta(ctx):
+    lib = load()
+    v = ctypes.c_double()
+    _check(lib, ctx, lib.lb_sum_theta(ctx, ctypes.byref(v)), "lb_sum_theta")
+    return v.value
+
+
+def lb_reduce(ctx, theta, u, exact_theta, exact_u, d):
+    lib = load()
+    buf = (ctypes.c_double * (3 * (d + 1) + 1))()
+    st = lib.lb_reduce(ctx, _ptr(theta, "theta"), _ptr(u, "u"), _ptr(exact_theta, "exact_theta"),
+                       _ptr(exact_u, "exact_u"), buf)
+    _check(lib, ctx, st, "lb_reduce")
+    vals = list(buf)
+    names = ["theta"] + ["u%d" % a for a in range(d)]
+    out = {nm: {"rmse": vals[3 * v], "linf": vals[3 * v + 1], "rel_l2": vals[3 * v + 2]}
+           for v, nm in enumerate(names)}
+    out["sum_theta"] = vals[-1]
+    return out
+
+
+def lb_state_layout(ctx):
+    lib = load()
+    p, s, e = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib, ctx, lib.lb_state_layout(ctx, ctypes.byref(p), ctypes.byref(s), ctypes.byref(e)),
+           "lb_state_layout")
+    return p.value, s.value, e.value
+
+
+def lb_save_state(ctx, buf):
+    lib = load()
+    _check(lib, ctx, lib.lb_save_state(ctx, ctypes.c_void_p(buf.data_ptr())), "lb_save_state")
+
+
+def lb_load_state(ctx, buf, step):
+    lib = load()
+    _check(lib, ctx, lib.lb_load_state(ctx, ctypes.c_void_p(buf.data_ptr()), int(step)), "lb_load_state")
+
+
+# --------------------------------------------------------------------------
+# Convenience wrapper.
+# --------------------------------------------------------------------------
+
+class Solver:
+    """One periodic MRT-LB solver context on the current CUDA device.
+
+    ``relax`` = None uses Theorem 2's relaxation set; a dict with s1, s2x,
+    s22, w1, wd overrides it.  ``precision`` is "fp64" or "fp32s" (FP32
+    shifted storage around ``theta_ref``).
+    """
+
+    def __init__(self, d, N, nu, dx, dt, relax=None, precision="fp64", theta_ref=0.0, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the MRT-LB solver needs a CUDA GPU; no CPU fallback exists")
+        self.d = int(d)
+        self.N = tuple(int(n) for n in N)
+        if len(self.N) != self.d:
+            raise ValueError("N must have d entries")
+        self.shape = tuple(reversed(self.N))
+        self.nodes = 1
+        for n in self.N:
+            self.nodes *= n
+        self.precision = {"fp64": LB_FP64, "fp32s": LB_FP32_SHIFTED}[precision]
+        rel = dict(relax or {})
+        rel["theta_ref"] = float(theta_ref)
+        self.stream = stream
+        self._lib = load()
+        self.ctx = lb_create(self.d, self.N, nu, dx, dt, rel, self.precision, stream)
+        self.params = lb_get_params(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _field(self, comps=0):
+        shape = self.shape if comps == 0 else (comps,) + self.shape
+        return torch.empty(shape, dtype=torch.float64, device="cuda")
+
+    def set_theta0(self, theta0, grad_theta0=None):
+        lb_set_theta0(self.ctx, theta0, grad_theta0, self.nodes, self.d)
+
+    def step(self, n):
+        lb_step(self.ctx, n)
+
+    @property
+    def nsteps(self):
+        return lb_get_step(self.ctx)
+
+    def macros(self, theta=None, grad=None, u=None, want=("theta", "grad", "u")):
+        theta = theta if theta is not None or "theta" not in want else self._field()
+        grad = grad if grad is not None or "grad" not in want else self._field(self.d)
+        u = u if u is not None or "u" not in want else self._field(self.d)
+        lb_macros(self.ctx, theta, grad, u)
+        return theta, grad, u
+
+    def sum_theta(self):
+        return lb_sum_theta(self.ctx)
+
+    def reduce(self, theta, u, exact_theta, exact_u):
+        return lb_reduce(self.ctx, theta, u, exact_theta, exact_u, self.d)
+
+    def state_layout(self):
+        return lb_state_layout(self.ctx)
+
+    def save_state(self):
+        pitch, slab, eb = self.state_layout()
+        q = int(self.params["q"])
+        buf = torch.empty(q * slab * eb, dtype=torch.uint8, device="cuda")
+        lb_save_state(self.ctx, buf)
+        return buf
+
+    def load_state(self, buf, step):
+        lb_load_state(self.ctx, buf, step)

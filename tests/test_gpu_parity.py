@@ -1,0 +1,151 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+FP64: theta, grad theta and u must match to a max normwise relative
+difference of 1e-12 (|gpu - oracle|_max <= 1e-12 * |oracle|_max per field).
+Grids are chosen to span several warp segments (64 nodes in x for FP64,
+128 for FP32) with ragged tails, plus degenerate sizes (N = 1, 2, 3 along an
+axis) where every node is at the periodic wrap.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2309_02825_gb300 import lb
+from paper_2309_02825_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _host(t):
+    return t.detach().cpu().numpy()
+
+
+def _relmax(a, b):
+    scale = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (scale if scale > 0 else 1.0))
+
+
+def _problem(d, N, seed, nu=0.02):
+    prob = W.FourierProblem.random(d, nu, 6, 3, 0.1, 1.5, seed)
+    dx = 1.0 / max(N)
+    dt = 0.2 * dx * dx / nu
+    return prob, dx, dt
+
+
+def _run_both(d, N, nsteps, seed=11, precision="fp64", grad=True, relax=None, theta_ref=1.5):
+    prob, dx, dt = _problem(d, N, seed)
+    nu = prob.nu
+    th0 = prob.theta(N, dx)
+    g0 = prob.grad(N, dx) if grad else None
+    m = O.Model(d, N, nu, dx, dt, relax)
+    th_o, g_o, u_o = m.recover(m.run(m.initialize(th0, g0), nsteps))
+    s = lb.Solver(d, N, nu, dx, dt, relax=relax, precision=precision, theta_ref=theta_ref)
+    s.set_theta0(_dev(th0), None if g0 is None else _dev(g0))
+    s.step(nsteps)
+    th, g, u = s.macros()
+    torch.cuda.synchronize()
+    return (th_o, g_o, u_o), (_host(th), _host(g), _host(u)), s, m
+
+
+CASES = [
+    (1, (100,), 1), (1, (100,), 37), (1, (1,), 5), (1, (2,), 4), (1, (3,), 9), (1, (64,), 20), (1, (129,), 13),
+    (2, (70, 45), 1), (2, (70, 45), 23), (2, (64, 64), 20), (2, (130, 3), 7), (2, (5, 33), 6), (2, (1, 9), 4),
+    (2, (200, 17), 150),
+    (3, (37, 22, 13), 1), (3, (37, 22, 13), 9), (3, (64, 16, 8), 16), (3, (3, 4, 5), 5), (3, (70, 1, 6), 4),
+]
+
+
+@pytest.mark.parametrize("d,N,nsteps", CASES)
+def test_fp64_matches_oracle(d, N, nsteps):
+    ref, got, _, _ = _run_both(d, N, nsteps)
+    for name, a, b in zip(("theta", "grad", "u"), got, ref):
+        assert _relmax(a, b) <= TOL64, (name, _relmax(a, b))
+
+
+@pytest.mark.parametrize("d,N", [(1, (50,)), (2, (66, 40)), (3, (20, 18, 9))])
+def test_fp64_fd_gradient_fallback(d, N):
+    ref, got, _, _ = _run_both(d, N, 5, grad=False)
+    for name, a, b in zip(("theta", "grad", "u"), got, ref):
+        assert _relmax(a, b) <= TOL64, name
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_fp64_custom_relaxation_set(d):
+    relax = {"s1": 1.3, "s2x": 0.7, "s22": 1.1, "w1": 0.12, "wd": 0.02 if d > 1 else 0.0}
+    N = [(90,), (40, 30), (20, 12, 10)][d - 1]
+    ref, got, _, _ = _run_both(d, N, 11, relax=relax)
+    for name, a, b in zip(("theta", "grad", "u"), got, ref):
+        assert _relmax(a, b) <= TOL64, name
+
+
+@pytest.mark.parametrize("d,N", [(1, (77,)), (2, (70, 45)), (3, (24, 10, 7))])
+def test_sum_theta_conserved_and_matches_oracle(d, N):
+    (th_o, _, _), _, s, m = _run_both(d, N, 30)
+    total = s.sum_theta()
+    assert abs(total - th_o.sum()) <= 1e-13 * abs(th_o.sum())
+    prob, dx, _ = _problem(d, N, 11)
+    assert abs(total - prob.theta(N, dx).sum()) <= 1e-12 * abs(total)
+
+
+def test_reduce_norms_match_numpy():
+    d, N = 2, (96, 50)
+    (th_o, _, u_o), (th, _, u), s, _ = _run_both(d, N, 12)
+    rng = np.random.default_rng(5)
+    ex_t = th + rng.normal(0, 1e-3, size=th.shape)
+    ex_u = u + rng.normal(0, 1e-4, size=u.shape)
+    r = s.reduce(_dev(th), _dev(u), _dev(ex_t), _dev(ex_u))
+    assert r["theta"]["rmse"] == pytest.approx(O.rmse(th, ex_t), rel=1e-12)
+    assert r["theta"]["linf"] == pytest.approx(O.linf(th, ex_t), rel=1e-15)
+    for a in range(d):
+        assert r["u%d" % a]["rmse"] == pytest.approx(O.rmse(u[a], ex_u[a]), rel=1e-12)
+        assert r["u%d" % a]["rel_l2"] == pytest.approx(
+            np.sqrt(np.sum((u[a] - ex_u[a]) ** 2) / np.sum(ex_u[a] ** 2)), rel=1e-12)
+    assert r["sum_theta"] == pytest.approx(th.sum(), rel=1e-14)
+
+
+def test_state_save_load_roundtrip():
+    d, N = 2, (70, 45)
+    prob, dx, dt = _problem(d, N, 3)
+    s = lb.Solver(d, N, prob.nu, dx, dt)
+    s.set_theta0(_dev(prob.theta(N, dx)), _dev(prob.grad(N, dx)))
+    s.step(5)
+    snap = s.save_state()
+    th_a, _, u_a = s.macros()
+    s.step(7)
+    s.load_state(snap, 5)
+    assert s.nsteps == 5
+    th_b, _, u_b = s.macros()
+    torch.cuda.synchronize()
+    assert torch.equal(th_a, th_b) and torch.equal(u_a, u_b)
+
+
+def test_invalid_inputs_are_reported():
+    with pytest.raises(lb.LBError) as ei:
+        lb.Solver(4, (4, 4, 4, 4), 0.1, 0.1, 0.1)
+    assert ei.value.status == lb.LB_EINVAL
+    with pytest.raises(lb.LBError):
+        lb.Solver(2, (8, 8), -1.0, 0.1, 0.1)
+    with pytest.raises(lb.LBError):
+        lb.Solver(2, (8, 8), 0.1, 0.1, 0.1, relax={"s1": 2.5, "s2x": 1, "s22": 1, "w1": 0.1, "wd": 0.01})
+    s = lb.Solver(2, (8, 8), 0.02, 1 / 8, 0.01)
+    with pytest.raises(lb.LBError) as ei:
+        s.step(1)
+    assert ei.value.status == lb.LB_ESTATE
+    bad = torch.ones((8, 8), dtype=torch.float64, device="cuda")
+    bad[3, 4] = -1.0
+    with pytest.raises(lb.LBError) as ei:
+        s.set_theta0(bad)
+    assert ei.value.status == lb.LB_ENONPOS
+    bad[3, 4] = float("nan")
+    with pytest.raises(lb.LBError) as ei:
+        s.set_theta0(bad)
+    assert ei.value.status == lb.LB_ENONPOS
+    with pytest.raises(ValueError):
+        s.set_theta0(torch.ones(7, dtype=torch.float64, device="cuda"))
