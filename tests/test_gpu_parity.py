@@ -17,6 +17,7 @@ from paper_2309_02825_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
+EPS64 = 2.0 ** -53
 
 
 def _dev(a):
@@ -30,6 +31,27 @@ def _host(t):
 def _relmax(a, b):
     scale = np.max(np.abs(b))
     return float(np.max(np.abs(a - b)) / (scale if scale > 0 else 1.0))
+
+
+def _check_fp64(ref, got, m, nsteps):
+    """theta: max |gpu - oracle| <= 1e-12 max |theta|.  grad and u come from
+    J = sum_k e_k f_k, a sum whose terms are O(theta): its rounding floor is
+    about q eps sum_k |f_k| no matter how small J is, so for them the bound is
+    1e-12 max|field| plus that floor (times sqrt(steps + 1) for the rounding
+    carried by f), scaled by the recovery coefficient of each field."""
+    th_o = ref[0]
+    p = m.params
+    sigma = 2 * p["w1"] + 4 * (m.d - 1) * p["wd"]
+    floor_j = 8 * m.q * EPS64 * np.max(np.abs(th_o)) * np.sqrt(nsteps + 1)
+    coef = {"grad": p["s1"] / (sigma * p["dx"]), "u": (2 - p["s1"]) * p["c"] / np.min(th_o)}
+    out = {}
+    for name, a, b in zip(("theta", "grad", "u"), got, ref):
+        diff = float(np.max(np.abs(a - b)))
+        scale = float(np.max(np.abs(b)))
+        bound = TOL64 * scale + (coef[name] * floor_j if name in coef else 0.0)
+        out[name] = diff / scale if scale > 0 else diff
+        assert diff <= bound, (name, diff, bound, out[name])
+    return out
 
 
 def _problem(d, N, seed, nu=0.02):
@@ -64,25 +86,23 @@ CASES = [
 
 @pytest.mark.parametrize("d,N,nsteps", CASES)
 def test_fp64_matches_oracle(d, N, nsteps):
-    ref, got, _, _ = _run_both(d, N, nsteps)
-    for name, a, b in zip(("theta", "grad", "u"), got, ref):
-        assert _relmax(a, b) <= TOL64, (name, _relmax(a, b))
+    ref, got, _, m = _run_both(d, N, nsteps)
+    rel = _check_fp64(ref, got, m, nsteps)
+    print("fp64 parity d=%d N=%s steps=%d rel: %s" % (d, N, nsteps, rel))
 
 
 @pytest.mark.parametrize("d,N", [(1, (50,)), (2, (66, 40)), (3, (20, 18, 9))])
 def test_fp64_fd_gradient_fallback(d, N):
-    ref, got, _, _ = _run_both(d, N, 5, grad=False)
-    for name, a, b in zip(("theta", "grad", "u"), got, ref):
-        assert _relmax(a, b) <= TOL64, name
+    ref, got, _, m = _run_both(d, N, 5, grad=False)
+    _check_fp64(ref, got, m, 5)
 
 
 @pytest.mark.parametrize("d", [1, 2, 3])
 def test_fp64_custom_relaxation_set(d):
     relax = {"s1": 1.3, "s2x": 0.7, "s22": 1.1, "w1": 0.12, "wd": 0.02 if d > 1 else 0.0}
     N = [(90,), (40, 30), (20, 12, 10)][d - 1]
-    ref, got, _, _ = _run_both(d, N, 11, relax=relax)
-    for name, a, b in zip(("theta", "grad", "u"), got, ref):
-        assert _relmax(a, b) <= TOL64, name
+    ref, got, _, m = _run_both(d, N, 11, relax=relax)
+    _check_fp64(ref, got, m, 11)
 
 
 @pytest.mark.parametrize("d,N", [(1, (77,)), (2, (70, 45)), (3, (24, 10, 7))])

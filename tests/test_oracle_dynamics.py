@@ -124,3 +124,29 @@ def test_fd_gradient_used_when_none_given():
     rng = np.random.default_rng(4)
     th0 = rng.uniform(1.0, 2.0, size=(8, 8))
     assert np.array_equal(m.initialize(th0), m.initialize(th0, m.fd4_gradient(th0)))
+
+
+@pytest.mark.parametrize("d,N,n", [(1, (40,), 4), (2, (30, 22), 3), (3, (14, 12, 11), 2)])
+def test_patch_of_side_2n_plus_3_reproduces_the_full_grid(d, N, n):
+    """The full-size GPU tests sample nodes by running the oracle on a small
+    periodic patch: after n steps a node only sees the initial data within
+    Chebyshev distance n.  Check that argument on the oracle itself."""
+    from paper_2309_02825_gb300 import workloads as W
+    from tests.test_gpu_fullsize import _patch
+
+    prob = W.FourierProblem.random(d, 0.02, 6, 3, 0.1, 1.5, 5)
+    dx = 1.0 / max(N)
+    dt = 0.2 * dx * dx / 0.02
+    th0, g0 = prob.theta(N, dx), prob.grad(N, dx)
+    full = O.Model(d, N, 0.02, dx, dt)
+    th, _, u = full.recover(full.run(full.initialize(th0, g0), n))
+    half = n + 1
+    pm = O.Model(d, [2 * half + 1] * d, 0.02, dx, dt)
+    rng = np.random.default_rng(0)
+    for _ in range(6):
+        c = tuple(int(rng.integers(0, k)) for k in N)
+        pt, pg = _patch(th0, c, half), _patch(g0, c, half)
+        tho, _, uo = pm.recover(pm.run(pm.initialize(pt, pg), n))
+        mid = (half,) * d
+        assert abs(tho[mid] - th[tuple(reversed(c))]) < 1e-14
+        assert np.allclose(uo[(slice(None),) + mid], u[(slice(None),) + tuple(reversed(c))], atol=1e-15, rtol=0)
