@@ -46,12 +46,13 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32s"])
+    p.add_argument("--precision", default="fx64", choices=["fx64", "fp64", "fp32s"],
+                   help="headline precision; the other two are reported as variants")
     p.add_argument("--N", type=int, default=4096)
     p.add_argument("--sweeps", type=int, default=100, help="sweeps per benchmark step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--no-variant", action="store_true", help="skip the other precision's sub-result")
+    p.add_argument("--no-variant", action="store_true", help="skip the other precisions' sub-results")
     return p.parse_args()
 
 
@@ -222,10 +223,11 @@ def run_ours(args, precision, world, rank, local, peaks, with_e2e, label_main):
     lups = nodes * S * args.steps * world
     value = lups / elapsed / 1e6
     q = 9
-    elem = 8 if precision == "fp64" else 4
+    elem = 4 if precision == "fp32s" else 8
     bytes_lu = 2 * q * elem
     achieved = bytes_lu * nodes / (sweep_ms / 1e3) / 1e9
     norms = out["norms"]
+    ctype = {"fp64": "double", "fp32s": "float", "fx64": "long long"}[precision]
     res = {
         "value": value,
         "ms_per_step": elapsed / args.steps * 1e3,
@@ -235,7 +237,7 @@ def run_ours(args, precision, world, rank, local, peaks, with_e2e, label_main):
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"],
             "traffic": profile_traffic("sweep_d2q9_%s_%d" % (precision, args.N)),
-            "kernel": "sweep_kernel<D2Q9,%s>" % ("double" if precision == "fp64" else "float"),
+            "kernel": "sweep_kernel<D2Q9,%s>" % ctype,
             "algorithmic_bytes_per_launch": bytes_lu * nodes,
             "peak_source": peaks["source"],
         },
@@ -245,8 +247,17 @@ def run_ours(args, precision, world, rank, local, peaks, with_e2e, label_main):
                   "u_rel_l2": math.sqrt(sum(norms["u%d" % a]["rel_l2"] ** 2 for a in range(d)) / d),
                   "sum_theta_drift": abs(out["total"] - float(th0_h.sum())) / float(th0_h.sum())},
         "clocks": clk,
-        "gpu_launches": args.steps * (S + 6),
+        "gpu_launches": args.steps * (S + 6 + (2 if precision == "fx64" else 0)),
     }
+    if precision == "fp64":
+        # The FP64 sweep is bound by the FP64 pipe: 34 FP64 instructions per
+        # D2Q9 update (closed-form collision), 2 per SM per clock on GB300.
+        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        peak_inst = 152 * 2 * sm_mhz * 1e6 / 1e9
+        ach_inst = 34 * nodes / (sweep_ms / 1e3) / 1e9
+        res["roofline_fp64_pipe"] = {"bound": "alu", "achieved": ach_inst, "peak": peak_inst,
+                                     "unit": "G FP64 inst/s", "frac": ach_inst / peak_inst,
+                                     "fp64_inst_per_lu": 34}
 
     if with_e2e:
         res["e2e"] = run_e2e(args, s, case, th0_h, g0_h, ex_t_h, ex_u_h, stream, world)
@@ -358,12 +369,17 @@ def main():
         dist.init_process_group("nccl")
     peaks = load_peaks()
     main_res = run_ours(args, args.precision, world, rank, local, peaks, not args.no_e2e, True)
-    other = "fp32s" if args.precision == "fp64" else "fp64"
-    variant = None
+    variants = []
     if not args.no_variant:
-        v = run_ours(args, other, world, rank, local, peaks, False, False)
-        variant = {"precision": other, "value": v["value"], "unit": UNIT, "roofline": v["roofline"],
-                   "error": v["error"], "sweep_ms": v["sweep_ms"]}
+        for other in ("fx64", "fp64", "fp32s"):
+            if other == args.precision:
+                continue
+            v = run_ours(args, other, world, rank, local, peaks, False, False)
+            entry = {"precision": other, "value": v["value"], "unit": UNIT, "roofline": v["roofline"],
+                     "error": v["error"], "sweep_ms": v["sweep_ms"]}
+            if "roofline_fp64_pipe" in v:
+                entry["roofline_fp64_pipe"] = v["roofline_fp64_pipe"]
+            variants.append(entry)
     base = None
     if rank == 0 and not args.no_cpu_baseline:
         base = cpu_baseline(args)
@@ -372,13 +388,13 @@ def main():
             "metric": METRIC, "value": main_res["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": main_res["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32",
+            "dtype": {"fp64": "f64", "fp32s": "f32", "fx64": "int64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": "2D D2Q9 periodic %d^2 sine, nu=0.02, eps=0.2048; step = init + %d fused "
                        "sweeps + recovery + sum theta + error norms" % (args.N, args.sweeps),
                        "precision": args.precision, "sweeps_per_step": args.sweeps,
                        "l2_flush": "inputs larger than L2 (state %.1f GB)" % (
-                           2 * 9 * (8 if args.precision == "fp64" else 4) * args.N ** 2 / 1e9),
+                           2 * 9 * (4 if args.precision == "fp32s" else 8) * args.N ** 2 / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": main_res["roofline"],
             "cpu_baseline": base,
@@ -388,8 +404,10 @@ def main():
             "error": main_res["error"],
             "sweep_ms": main_res["sweep_ms"],
         }
-        if variant:
-            line["variant"] = variant
+        if "roofline_fp64_pipe" in main_res:
+            line["roofline_fp64_pipe"] = main_res["roofline_fp64_pipe"]
+        if variants:
+            line["variants"] = variants
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

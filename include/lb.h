@@ -49,7 +49,14 @@ typedef enum {
 
 typedef enum {
     LB_FP64 = 0,         /* distributions stored and updated in IEEE double */
-    LB_FP32_SHIFTED = 1  /* stored and updated in float as f - w*theta_ref */
+    LB_FP32_SHIFTED = 1, /* stored and updated in float as f - w*theta_ref */
+    LB_FX64 = 2          /* stored as 64-bit fixed point round(f * 2^F), with F
+                            chosen by lb_set_theta0 from max|theta0| (about 55 -
+                            log2 max|theta0|, i.e. 7 bits of headroom); moment
+                            sums are exact integer additions, each relaxation
+                            product is rounded once (2^-62 relative), and the
+                            rest population is theta minus the others, so
+                            sum theta is conserved exactly.  Recovery is FP64. */
 } lb_precision;
 
 /*
@@ -78,7 +85,7 @@ typedef struct {
  *   nu, dx, dt  viscosity, lattice spacing, time step (all > 0, finite);
  *            c = dx/dt is the lattice speed.
  *   rs       relaxation set (NULL = paper set, theta_ref = 0).
- *   precision  LB_FP64 or LB_FP32_SHIFTED.
+ *   precision  LB_FP64, LB_FP32_SHIFTED or LB_FX64.
  *   stream   a cudaStream_t (NULL = the legacy default stream).
  *   out      receives the context; set to NULL on failure.
  * Allocates 2*q*pitch*N[1]*N[2] distribution values on the current device.
@@ -91,9 +98,10 @@ lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt,
 lb_status lb_destroy(lb_ctx *ctx);
 
 /*
- * Parameters in use, written to out[0..13] (host):
+ * Parameters in use, written to out[0..14] (host):
  *   eps, c, cs2 (= c_s^2, Eq. (conseved-moment)), s1, s2x, s22, w0, w1, wd,
- *   nu, dx, dt, q, theta_ref.
+ *   nu, dx, dt, q, theta_ref, F (LB_FX64 fraction bits; 0 before
+ *   lb_set_theta0 and for the other precisions).
  */
 lb_status lb_get_params(const lb_ctx *ctx, double *out);
 
@@ -104,7 +112,8 @@ lb_status lb_get_params(const lb_ctx *ctx, double *out);
  *   theta0       device, scalar field, every value finite and > 0.
  *   grad_theta0  device, vector field (d*nodes) holding grad theta0, or NULL
  *                to use a fourth-order central difference of theta0.
- * Resets the step counter to 0.  Synchronises the stream.
+ * Resets the step counter to 0.  For LB_FX64 it also fixes the fixed-point
+ * scale F from max|theta0|.  Synchronises the stream.
  * Errors: LB_EINVAL (NULL theta0), LB_ENONPOS (theta0 <= 0 or non-finite
  * somewhere, or a non-finite gradient; the state is then left uninitialised),
  * LB_ECUDA.
@@ -166,7 +175,9 @@ lb_status lb_reduce(lb_ctx *ctx, const double *theta, const double *u,
  * value (i, x, y, z) sits at element i*slab + (z*N[1] + y)*pitch + x.
  * Values are stored after collision and before streaming: the pre-collision
  * distribution at the current step n is f_i(x, n) = state_i(x - e_i)
- * (periodic).  For LB_FP32_SHIFTED the stored value is f - w_i*theta_ref.
+ * (periodic).  For LB_FP32_SHIFTED the stored value is f - w_i*theta_ref;
+ * for LB_FX64 it is round(f * 2^F) as int64 (F from lb_get_params; a state
+ * loaded into another context is read with that context's F).
  * Padding entries (x >= N[0]) are ignored.  buf is a device pointer of
  * q*slab*elem_bytes bytes.  lb_load_state sets the step counter to `step`.
  */

@@ -70,7 +70,7 @@ lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt, co
     if (!N) return fail(nullptr, LB_EINVAL, "lb_create: N is NULL");
     if (!finite_pos(nu) || !finite_pos(dx) || !finite_pos(dt))
         return fail(nullptr, LB_EINVAL, "lb_create: nu, dx and dt must be finite and > 0");
-    if (precision != LB_FP64 && precision != LB_FP32_SHIFTED)
+    if (precision != LB_FP64 && precision != LB_FP32_SHIFTED && precision != LB_FX64)
         return fail(nullptr, LB_EINVAL, "lb_create: unknown precision");
     int64_t nodes = 1;
     for (int a = 0; a < d; ++a) {
@@ -128,8 +128,8 @@ lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt, co
     c->cs2 = c->sigma * c->c * c->c;
 
     // Layout.
-    const int V = (precision == LB_FP64) ? lbk::Vec<double>::V : lbk::Vec<float>::V;
-    c->elem = (precision == LB_FP64) ? 8 : 4;
+    const int V = (precision == LB_FP32_SHIFTED) ? lbk::Vec<float>::V : lbk::Vec<double>::V;
+    c->elem = (precision == LB_FP32_SHIFTED) ? 4 : 8;
     lbk::Geom &g = c->geom;
     g.N0 = (int)c->N[0];
     g.N1 = (int)c->N[1];
@@ -181,8 +181,8 @@ lb_status lb_destroy(lb_ctx *c)
 lb_status lb_get_params(const lb_ctx *c, double *out)
 {
     if (!c || !out) return LB_EINVAL;
-    const double v[14] = {c->eps, c->c,  c->cs2, c->s1, c->s2x, c->s22,       c->w0,
-                          c->w1,  c->wd, c->nu,  c->dx, c->dt,  (double)c->q, c->theta_ref};
+    const double v[15] = {c->eps, c->c,  c->cs2, c->s1, c->s2x, c->s22,       c->w0,       c->w1,
+                          c->wd,  c->nu, c->dx,  c->dt, (double)c->q, c->theta_ref, (double)c->fx_bits};
     memcpy(out, v, sizeof v);
     return LB_OK;
 }
@@ -205,6 +205,19 @@ lb_status lb_set_theta0(lb_ctx *c, const double *theta0, const double *grad)
     }
     if ((e = cudaMemsetAsync(c->dflag, 0, sizeof(int), c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "lb_set_theta0: flag reset");
+    if (c->precision == LB_FX64) {
+        // Fixed-point scale: max|theta0| * 2^F <= 2^55 leaves 7 bits of
+        // headroom for sums of up to 19 values and for transients.
+        double mx = 0.0;
+        if ((e = lbk::launch_maxabs(c, theta0, c->nodes, c->dout)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&mx, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "lb_set_theta0: max|theta0|");
+        if (!(mx > 0.0) || !isfinite(mx)) return fail(c, LB_ENONPOS, "lb_set_theta0: theta0 must be finite and > 0");
+        int ex = 0;
+        frexp(mx, &ex);  // mx < 2^ex
+        c->fx_bits = 55 - ex;
+    }
     c->cur = 0;
     if ((e = lbk::launch_init(c, theta0, grad, c->dflag)) != cudaSuccess)
         return cuda_fail(c, e, "lb_set_theta0: init launch");
@@ -261,7 +274,7 @@ lb_status lb_sum_theta(lb_ctx *c, double *out)
     if (e == cudaSuccess) e = cudaMemcpyAsync(&v, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lb_sum_theta");
-    if (c->precision != LB_FP64) v += c->theta_ref * (double)c->nodes;
+    if (c->precision == LB_FP32_SHIFTED) v += c->theta_ref * (double)c->nodes;
     *out = v;
     return LB_OK;
 }

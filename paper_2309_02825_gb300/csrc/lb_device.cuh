@@ -1,0 +1,257 @@
+// Device-side building blocks shared by the sweep, recovery and fixed-point
+// kernels: compile-time loops, periodic wrap, 16-byte vector access, the
+// shifted pull of one population along x, and the closed-form moment-space
+// collision for D1Q3, D2Q9 and D3Q19 (Eq. (distribution-f)).
+#pragma once
+
+#include "lb_internal.cuh"
+
+namespace lbk {
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
+    }
+}
+
+__device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+__device__ __forceinline__ void ld_vec(const double *p, double (&a)[2])
+{
+    double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    a[0] = v.x;
+    a[1] = v.y;
+}
+__device__ __forceinline__ void ld_vec(const float *p, float (&a)[4])
+{
+    float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    a[0] = v.x;
+    a[1] = v.y;
+    a[2] = v.z;
+    a[3] = v.w;
+}
+__device__ __forceinline__ void st_vec(double *p, const double (&a)[2])
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(a[0], a[1]);
+}
+__device__ __forceinline__ void st_vec(float *p, const float (&a)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(a[0], a[1], a[2], a[3]);
+}
+__device__ __forceinline__ void ld_vec(const long long *p, long long (&a)[2])
+{
+    longlong2 v = __ldg(reinterpret_cast<const longlong2 *>(p));
+    a[0] = v.x;
+    a[1] = v.y;
+}
+__device__ __forceinline__ void st_vec(long long *p, const long long (&a)[2])
+{
+    *reinterpret_cast<longlong2 *>(p) = make_longlong2(a[0], a[1]);
+}
+
+// Conversion of an FP64 value to the storage type (64-bit fixed point uses
+// round-to-nearest of v * 2^F).
+template <typename T> __device__ __forceinline__ T to_store(double v, double) { return (T)v; }
+template <> __device__ __forceinline__ long long to_store<long long>(double v, double fxscale)
+{
+    return __double2ll_rn(v * fxscale);
+}
+
+// Pull V consecutive values of one population along x with shift EX:
+// out[k] = row[(xb + k - EX) mod N0] for the valid nodes xb + k < N0 of this
+// lane (xb = x0 + V*lane).  Values for padding nodes are unspecified but
+// every access stays inside the row (the pitch is a multiple of 32*V).
+// Must be called by all 32 lanes of the warp together.
+template <typename T, int EX>
+__device__ __forceinline__ void pull_row(const T *__restrict__ row, int x0, int lane, int N0,
+                                         T (&out)[Vec<T>::V])
+{
+    constexpr int V = Vec<T>::V;
+    const int xb = x0 + V * lane;
+    T a[V];
+    ld_vec(row + xb, a);
+    if constexpr (EX == 0) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) out[k] = a[k];
+    } else if constexpr (EX == 1) {
+        T left = __shfl_up_sync(0xffffffffu, a[V - 1], 1);
+        if (lane == 0) left = row[xb == 0 ? N0 - 1 : xb - 1];
+        out[0] = left;
+#pragma unroll
+        for (int k = 1; k < V; ++k) out[k] = a[k - 1];
+    } else {
+        T right = __shfl_down_sync(0xffffffffu, a[0], 1);
+#pragma unroll
+        for (int k = 0; k < V - 1; ++k) out[k] = a[k + 1];
+        out[V - 1] = right;
+        if (lane == 31 || xb + V >= N0) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                const int x = xb + k;
+                if (x + 1 == N0)
+                    out[k] = row[0];
+                else if (k == V - 1 && lane == 31 && x + 1 < N0)
+                    out[k] = row[x + 1];
+            }
+        }
+    }
+}
+
+// Gather the pre-collision f(x, n) for the V nodes of this lane.
+template <class L, typename T>
+__device__ __forceinline__ void gather(const T *__restrict__ src, const Geom &g, int64_t row, int x0, int lane,
+                                       T (&f)[L::Q][Vec<T>::V])
+{
+    const int y = (int)(row % g.N1);
+    const int z = (int)(row / g.N1);
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
+        const int ys = (ey == 0) ? y : wrapi(y - ey, g.N1);
+        const int zs = (ez == 0) ? z : wrapi(z - ez, g.N2);
+        const T *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
+        pull_row<T, ex>(rp, x0, lane, g.N0, f[i]);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Collision, in place on one node's q values.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void collide(D1Q3, T *f, const Coll<T> &k)
+{
+    const T P = f[1] + f[2];
+    const T th = f[0] + P;
+    const T J = f[1] - f[2];
+    const T A = fma(k.k2, P, k.cA * th);
+    const T B = k.k1 * J;
+    f[0] = fma(-2 * k.k2, P, k.c0 * th);
+    f[1] = A + B;
+    f[2] = A - B;
+}
+
+template <typename T>
+__device__ __forceinline__ void collide(D2Q9, T *f, const Coll<T> &k)
+{
+    const T a = f[1] + f[3], b = f[2] + f[4];
+    const T p = f[5] + f[7], r = f[6] + f[8];
+    const T Fd = p + r;
+    const T th = (f[0] + a) + (b + Fd);
+    const T Pxx = a + Fd, Pyy = b + Fd, Pxy = p - r;
+    const T g = f[5] - f[7], h = f[8] - f[6];
+    const T Jx = (f[1] - f[3]) + (g + h);
+    const T Jy = (f[2] - f[4]) + (g - h);
+    const T cth = k.cA * th;
+    const T Ax = fma(k.k2, Pxx, cth), Bx = k.k1 * Jx;
+    const T Ay = fma(k.k2, Pyy, cth), By = k.k1 * Jy;
+    const T wth = k.wd * th;
+    const T dp = fma(k.k3, Pxy, wth), dm = fma(-k.k3, Pxy, wth);
+    f[0] = fma(-2 * k.k2, Pxx + Pyy, k.c0 * th);
+    f[1] = Ax + Bx;
+    f[3] = Ax - Bx;
+    f[2] = Ay + By;
+    f[4] = Ay - By;
+    f[5] = dp;
+    f[7] = dp;
+    f[6] = dm;
+    f[8] = dm;
+}
+
+// One coordinate plane (a, b) of D3Q19: g0..g3 are the velocities with
+// (e_a, e_b) = (1,1), (-1,1), (-1,-1), (1,-1).
+template <typename T> struct Plane {
+    T F, P, Ja, Jb;
+};
+template <typename T> __device__ __forceinline__ Plane<T> plane(T g0, T g1, T g2, T g3)
+{
+    const T p = g0 + g2, r = g1 + g3;
+    const T u = g0 - g2, v = g3 - g1;
+    return {p + r, p - r, u + v, u - v};
+}
+
+template <typename T>
+__device__ __forceinline__ void collide(D3Q19, T *f, const Coll<T> &k)
+{
+    const Plane<T> xy = plane(f[7], f[8], f[9], f[10]);
+    const Plane<T> xz = plane(f[11], f[12], f[13], f[14]);
+    const Plane<T> yz = plane(f[15], f[16], f[17], f[18]);
+    const T ax = f[1] + f[4], ay = f[2] + f[5], az = f[3] + f[6];
+    const T th = (f[0] + (ax + ay) + az) + ((xy.F + xz.F) + yz.F);
+    const T Pxx = ax + (xy.F + xz.F);
+    const T Pyy = ay + (xy.F + yz.F);
+    const T Pzz = az + (xz.F + yz.F);
+    const T Jx = (f[1] - f[4]) + (xy.Ja + xz.Ja);
+    const T Jy = (f[2] - f[5]) + (xy.Jb + yz.Ja);
+    const T Jz = (f[3] - f[6]) + (xz.Jb + yz.Jb);
+    const T cth = k.cA * th;
+    const T wth = k.wd * th;
+    f[0] = fma(-2 * k.k2, (Pxx + Pyy) + Pzz, k.c0 * th);
+    {
+        const T A = fma(k.k2, Pxx, cth), B = k.k1 * Jx;
+        f[1] = A + B;
+        f[4] = A - B;
+    }
+    {
+        const T A = fma(k.k2, Pyy, cth), B = k.k1 * Jy;
+        f[2] = A + B;
+        f[5] = A - B;
+    }
+    {
+        const T A = fma(k.k2, Pzz, cth), B = k.k1 * Jz;
+        f[3] = A + B;
+        f[6] = A - B;
+    }
+    {
+        const T dp = fma(k.k3, xy.P, wth), dm = fma(-k.k3, xy.P, wth);
+        f[7] = dp; f[9] = dp; f[8] = dm; f[10] = dm;
+    }
+    {
+        const T dp = fma(k.k3, xz.P, wth), dm = fma(-k.k3, xz.P, wth);
+        f[11] = dp; f[13] = dp; f[12] = dm; f[14] = dm;
+    }
+    {
+        const T dp = fma(k.k3, yz.P, wth), dm = fma(-k.k3, yz.P, wth);
+        f[15] = dp; f[17] = dp; f[16] = dm; f[18] = dm;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sweep kernel.
+// ---------------------------------------------------------------------------
+constexpr int kSweepThreads = 256;
+
+// K is the collision-constant type; the matching collide() overload (float,
+// double or 64-bit fixed point) is picked by overload resolution.
+template <class L, typename T, class K>
+__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const T *__restrict__ src, T *__restrict__ dst,
+                                                              Geom g, K k)
+{
+    constexpr int V = Vec<T>::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t seg = (int64_t)blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
+    if (seg >= g.nseg) return;  // warp-uniform
+    const int64_t row = seg / g.seg_per_row;
+    const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
+
+    T f[L::Q][V];
+    gather<L, T>(src, g, row, x0, lane, f);
+
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        T n[L::Q];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) n[i] = f[i][v];
+        collide(L{}, n, k);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) f[i][v] = n[i];
+    }
+
+    T *dp = dst + row * g.pitch + x0 + V * lane;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, f[i]);
+}
+
+}  // namespace lbk

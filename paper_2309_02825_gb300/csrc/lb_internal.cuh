@@ -43,6 +43,7 @@ struct D3Q19 {
 template <typename T> struct Vec;
 template <> struct Vec<double> { using type = double2; static constexpr int V = 2; };
 template <> struct Vec<float> { using type = float4; static constexpr int V = 4; };
+template <> struct Vec<long long> { using type = longlong2; static constexpr int V = 2; };
 
 // Grid geometry of one padded state array.
 struct Geom {
@@ -66,6 +67,15 @@ template <typename T> struct Coll {
     T k1, k2, k3, c0, cA, wd;
 };
 
+// The same constants in 64-bit fixed point with 62 fractional bits (every
+// constant lies in (-2, 2)); products are rounded to nearest.  The rest
+// population is formed as theta minus the others, so the collision
+// conserves sum f exactly.
+struct CollFx {
+    long long k1, k2, k3, cA, wd;
+};
+constexpr int kFxCoefBits = 62;
+
 // Recovery constants (Sec. III.C): u_a = ucoef * J_a / theta with
 // ucoef = (2 - s1) c; grad_a = gcoef * J_a with gcoef = -s1 / (sigma dx);
 // J_a = sum_k e_ka f_k.
@@ -78,6 +88,7 @@ struct Recov {
 // f(diag e) = wd th - idg * (e . grad th).
 struct InitK {
     double w0, w1, wd, iax, idg, theta_ref;
+    double fxscale;  // 2^F for 64-bit fixed-point storage, unused otherwise
 };
 
 }  // namespace lbk
@@ -92,6 +103,7 @@ struct lb_ctx {
     int precision = LB_FP64;
     double nu = 0, dx = 0, dt = 0, c = 0, eps = 0, cs2 = 0, sigma = 0;
     double s1 = 0, s2x = 0, s22 = 1, w0 = 0, w1 = 0, wd = 0, theta_ref = 0;
+    int fx_bits = 0;          // LB_FX64: stored value = round(f * 2^fx_bits)
     cudaStream_t stream = nullptr;
     lbk::Geom geom{};
     size_t elem = 8;
@@ -120,6 +132,10 @@ cudaError_t launch_init(lb_ctx *c, const double *theta0, const double *grad, int
 cudaError_t launch_sweep(lb_ctx *c, const void *src, void *dst);
 cudaError_t launch_macros(lb_ctx *c, const void *src, double *theta, double *grad, double *u, int *flag);
 cudaError_t launch_sum_state(lb_ctx *c, const void *src, double *out_dev);
+cudaError_t launch_maxabs(lb_ctx *c, const double *x, int64_t n, double *out_dev);
+// 64-bit fixed-point path (lb_fx.cu).
+cudaError_t launch_sweep_fx(lb_ctx *c, const void *src, void *dst);
+cudaError_t launch_macros_fx(lb_ctx *c, const void *src, double *theta, double *grad, double *u, int *flag);
 cudaError_t launch_norms(lb_ctx *c, const double *theta, const double *u, const double *ex_theta,
                          const double *ex_u, double *out_dev);
 

@@ -14,235 +14,9 @@
 // are never formed; M^-1 is applied analytically.
 #include <math.h>
 
-#include "lb_internal.cuh"
+#include "lb_device.cuh"
 
 namespace lbk {
-
-template <int I, int N, class F>
-__device__ __forceinline__ void static_for(F &&f)
-{
-    if constexpr (I < N) {
-        f(std::integral_constant<int, I>{});
-        static_for<I + 1, N>(f);
-    }
-}
-
-__device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-
-__device__ __forceinline__ void ld_vec(const double *p, double (&a)[2])
-{
-    double2 v = __ldg(reinterpret_cast<const double2 *>(p));
-    a[0] = v.x;
-    a[1] = v.y;
-}
-__device__ __forceinline__ void ld_vec(const float *p, float (&a)[4])
-{
-    float4 v = __ldg(reinterpret_cast<const float4 *>(p));
-    a[0] = v.x;
-    a[1] = v.y;
-    a[2] = v.z;
-    a[3] = v.w;
-}
-__device__ __forceinline__ void st_vec(double *p, const double (&a)[2])
-{
-    *reinterpret_cast<double2 *>(p) = make_double2(a[0], a[1]);
-}
-__device__ __forceinline__ void st_vec(float *p, const float (&a)[4])
-{
-    *reinterpret_cast<float4 *>(p) = make_float4(a[0], a[1], a[2], a[3]);
-}
-
-// Pull V consecutive values of one population along x with shift EX:
-// out[k] = row[(xb + k - EX) mod N0] for the valid nodes xb + k < N0 of this
-// lane (xb = x0 + V*lane).  Values for padding nodes are unspecified but
-// every access stays inside the row (the pitch is a multiple of 32*V).
-// Must be called by all 32 lanes of the warp together.
-template <typename T, int EX>
-__device__ __forceinline__ void pull_row(const T *__restrict__ row, int x0, int lane, int N0,
-                                         T (&out)[Vec<T>::V])
-{
-    constexpr int V = Vec<T>::V;
-    const int xb = x0 + V * lane;
-    T a[V];
-    ld_vec(row + xb, a);
-    if constexpr (EX == 0) {
-#pragma unroll
-        for (int k = 0; k < V; ++k) out[k] = a[k];
-    } else if constexpr (EX == 1) {
-        T left = __shfl_up_sync(0xffffffffu, a[V - 1], 1);
-        if (lane == 0) left = row[xb == 0 ? N0 - 1 : xb - 1];
-        out[0] = left;
-#pragma unroll
-        for (int k = 1; k < V; ++k) out[k] = a[k - 1];
-    } else {
-        T right = __shfl_down_sync(0xffffffffu, a[0], 1);
-#pragma unroll
-        for (int k = 0; k < V - 1; ++k) out[k] = a[k + 1];
-        out[V - 1] = right;
-        if (lane == 31 || xb + V >= N0) {
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-                const int x = xb + k;
-                if (x + 1 == N0)
-                    out[k] = row[0];
-                else if (k == V - 1 && lane == 31 && x + 1 < N0)
-                    out[k] = row[x + 1];
-            }
-        }
-    }
-}
-
-// Gather the pre-collision f(x, n) for the V nodes of this lane.
-template <class L, typename T>
-__device__ __forceinline__ void gather(const T *__restrict__ src, const Geom &g, int64_t row, int x0, int lane,
-                                       T (&f)[L::Q][Vec<T>::V])
-{
-    const int y = (int)(row % g.N1);
-    const int z = (int)(row / g.N1);
-    static_for<0, L::Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
-        const int ys = (ey == 0) ? y : wrapi(y - ey, g.N1);
-        const int zs = (ez == 0) ? z : wrapi(z - ez, g.N2);
-        const T *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
-        pull_row<T, ex>(rp, x0, lane, g.N0, f[i]);
-    });
-}
-
-// ---------------------------------------------------------------------------
-// Collision, in place on one node's q values.
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void collide(D1Q3, T *f, const Coll<T> &k)
-{
-    const T P = f[1] + f[2];
-    const T th = f[0] + P;
-    const T J = f[1] - f[2];
-    const T A = fma(k.k2, P, k.cA * th);
-    const T B = k.k1 * J;
-    f[0] = fma(-2 * k.k2, P, k.c0 * th);
-    f[1] = A + B;
-    f[2] = A - B;
-}
-
-template <typename T>
-__device__ __forceinline__ void collide(D2Q9, T *f, const Coll<T> &k)
-{
-    const T a = f[1] + f[3], b = f[2] + f[4];
-    const T p = f[5] + f[7], r = f[6] + f[8];
-    const T Fd = p + r;
-    const T th = (f[0] + a) + (b + Fd);
-    const T Pxx = a + Fd, Pyy = b + Fd, Pxy = p - r;
-    const T g = f[5] - f[7], h = f[8] - f[6];
-    const T Jx = (f[1] - f[3]) + (g + h);
-    const T Jy = (f[2] - f[4]) + (g - h);
-    const T cth = k.cA * th;
-    const T Ax = fma(k.k2, Pxx, cth), Bx = k.k1 * Jx;
-    const T Ay = fma(k.k2, Pyy, cth), By = k.k1 * Jy;
-    const T wth = k.wd * th;
-    const T dp = fma(k.k3, Pxy, wth), dm = fma(-k.k3, Pxy, wth);
-    f[0] = fma(-2 * k.k2, Pxx + Pyy, k.c0 * th);
-    f[1] = Ax + Bx;
-    f[3] = Ax - Bx;
-    f[2] = Ay + By;
-    f[4] = Ay - By;
-    f[5] = dp;
-    f[7] = dp;
-    f[6] = dm;
-    f[8] = dm;
-}
-
-// One coordinate plane (a, b) of D3Q19: g0..g3 are the velocities with
-// (e_a, e_b) = (1,1), (-1,1), (-1,-1), (1,-1).
-template <typename T> struct Plane {
-    T F, P, Ja, Jb;
-};
-template <typename T> __device__ __forceinline__ Plane<T> plane(T g0, T g1, T g2, T g3)
-{
-    const T p = g0 + g2, r = g1 + g3;
-    const T u = g0 - g2, v = g3 - g1;
-    return {p + r, p - r, u + v, u - v};
-}
-
-template <typename T>
-__device__ __forceinline__ void collide(D3Q19, T *f, const Coll<T> &k)
-{
-    const Plane<T> xy = plane(f[7], f[8], f[9], f[10]);
-    const Plane<T> xz = plane(f[11], f[12], f[13], f[14]);
-    const Plane<T> yz = plane(f[15], f[16], f[17], f[18]);
-    const T ax = f[1] + f[4], ay = f[2] + f[5], az = f[3] + f[6];
-    const T th = (f[0] + (ax + ay) + az) + ((xy.F + xz.F) + yz.F);
-    const T Pxx = ax + (xy.F + xz.F);
-    const T Pyy = ay + (xy.F + yz.F);
-    const T Pzz = az + (xz.F + yz.F);
-    const T Jx = (f[1] - f[4]) + (xy.Ja + xz.Ja);
-    const T Jy = (f[2] - f[5]) + (xy.Jb + yz.Ja);
-    const T Jz = (f[3] - f[6]) + (xz.Jb + yz.Jb);
-    const T cth = k.cA * th;
-    const T wth = k.wd * th;
-    f[0] = fma(-2 * k.k2, (Pxx + Pyy) + Pzz, k.c0 * th);
-    {
-        const T A = fma(k.k2, Pxx, cth), B = k.k1 * Jx;
-        f[1] = A + B;
-        f[4] = A - B;
-    }
-    {
-        const T A = fma(k.k2, Pyy, cth), B = k.k1 * Jy;
-        f[2] = A + B;
-        f[5] = A - B;
-    }
-    {
-        const T A = fma(k.k2, Pzz, cth), B = k.k1 * Jz;
-        f[3] = A + B;
-        f[6] = A - B;
-    }
-    {
-        const T dp = fma(k.k3, xy.P, wth), dm = fma(-k.k3, xy.P, wth);
-        f[7] = dp; f[9] = dp; f[8] = dm; f[10] = dm;
-    }
-    {
-        const T dp = fma(k.k3, xz.P, wth), dm = fma(-k.k3, xz.P, wth);
-        f[11] = dp; f[13] = dp; f[12] = dm; f[14] = dm;
-    }
-    {
-        const T dp = fma(k.k3, yz.P, wth), dm = fma(-k.k3, yz.P, wth);
-        f[15] = dp; f[17] = dp; f[16] = dm; f[18] = dm;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Sweep kernel.
-// ---------------------------------------------------------------------------
-constexpr int kSweepThreads = 256;
-
-template <class L, typename T>
-__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const T *__restrict__ src, T *__restrict__ dst,
-                                                              Geom g, Coll<T> k)
-{
-    constexpr int V = Vec<T>::V;
-    const int lane = threadIdx.x & 31;
-    const int64_t seg = (int64_t)blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
-    if (seg >= g.nseg) return;  // warp-uniform
-    const int64_t row = seg / g.seg_per_row;
-    const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
-
-    T f[L::Q][V];
-    gather<L, T>(src, g, row, x0, lane, f);
-
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        T n[L::Q];
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) n[i] = f[i][v];
-        collide(L{}, n, k);
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) f[i][v] = n[i];
-    }
-
-    T *dp = dst + row * g.pitch + x0 + V * lane;
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, f[i]);
-}
 
 // ---------------------------------------------------------------------------
 // Recovery (Sec. III.C) from the pulled pre-collision f.
@@ -344,7 +118,7 @@ __global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *
             val -= K.wd * K.theta_ref;
         }
         if constexpr (nz == 0) val -= K.w0 * K.theta_ref;
-        out[(int64_t)i * g.slab] = (T)val;
+        out[(int64_t)i * g.slab] = to_store<T>(val, K.fxscale);
     });
 }
 
@@ -411,7 +185,7 @@ __device__ __forceinline__ void block_reduce_store(Acc<NS> &a, const int (&op)[N
 // Sum of the stored state over populations and valid nodes.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) sum_state_kernel(const T *__restrict__ src, Geom g, int q,
-                                                                double *__restrict__ partial)
+                                                                double scale, double *__restrict__ partial)
 {
     Acc<1> a{{0.0}};
     const int64_t total = (int64_t)q * g.rows * g.N0;
@@ -419,7 +193,7 @@ __global__ void __launch_bounds__(kRedThreads) sum_state_kernel(const T *__restr
          t += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(t % g.N0);
         const int64_t rr = t / g.N0;  // population * rows + row
-        a.v[0] += (double)src[rr * g.pitch + x];
+        a.v[0] += (double)src[rr * g.pitch + x] * scale;
     }
     const int op[1] = {0};
     block_reduce_store<1>(a, op, partial + (int64_t)blockIdx.x * kRedSlots);
@@ -461,6 +235,17 @@ __global__ void __launch_bounds__(kRedThreads) norms_kernel(const double *__rest
 #pragma unroll
     for (int k = 0; k < NS; ++k) op[k] = (k < NS - 1 && k % 3 == 1) ? 1 : 0;
     block_reduce_store<NS>(a, op, partial + (int64_t)blockIdx.x * kRedSlots);
+}
+
+// max |x| over n values.
+__global__ void __launch_bounds__(kRedThreads) maxabs_kernel(const double *__restrict__ x, int64_t n,
+                                                             double *__restrict__ partial)
+{
+    Acc<1> a{{0.0}};
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        a.v[0] = fmax(a.v[0], fabs(x[t]));
+    const int op[1] = {1};
+    block_reduce_store<1>(a, op, partial + (int64_t)blockIdx.x * kRedSlots);
 }
 
 // Fold nb partial rows of kRedSlots in a fixed order.  opmask bit k = max.
@@ -508,13 +293,14 @@ static int64_t sweep_blocks(const Geom &g) { return (g.nseg + kSweepThreads / 32
 
 template <class L, typename T> static cudaError_t sweep_t(lb_ctx *c, const void *src, void *dst)
 {
-    sweep_kernel<L, T><<<(unsigned)sweep_blocks(c->geom), kSweepThreads, 0, c->stream>>>(
+    sweep_kernel<L, T, Coll<T>><<<(unsigned)sweep_blocks(c->geom), kSweepThreads, 0, c->stream>>>(
         (const T *)src, (T *)dst, c->geom, make_coll<T>(c));
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(lb_ctx *c, const void *src, void *dst)
 {
+    if (c->precision == LB_FX64) return launch_sweep_fx(c, src, dst);
     const bool f64 = c->precision == LB_FP64;
     switch (c->d) {
     case 1: return f64 ? sweep_t<D1Q3, double>(c, src, dst) : sweep_t<D1Q3, float>(c, src, dst);
@@ -528,7 +314,7 @@ static Recov make_recov(const lb_ctx *c)
     Recov r;
     r.ucoef = (2.0 - c->s1) * c->c;
     r.gcoef = -c->s1 / (c->sigma * c->dx);
-    r.theta_ref = (c->precision == LB_FP64) ? 0.0 : c->theta_ref;
+    r.theta_ref = (c->precision == LB_FP32_SHIFTED) ? c->theta_ref : 0.0;
     return r;
 }
 
@@ -542,6 +328,7 @@ static cudaError_t macros_t(lb_ctx *c, const void *src, double *th, double *gr, 
 
 cudaError_t launch_macros(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
 {
+    if (c->precision == LB_FX64) return launch_macros_fx(c, src, th, gr, u, flag);
     const bool f64 = c->precision == LB_FP64;
     switch (c->d) {
     case 1: return f64 ? macros_t<D1Q3, double>(c, src, th, gr, u, flag) : macros_t<D1Q3, float>(c, src, th, gr, u, flag);
@@ -569,7 +356,8 @@ static cudaError_t init_t(lb_ctx *c, const double *theta0, const double *grad, i
     K.wd = wd;
     K.iax = 0.5 * c->dx * (c->sigma / c->s1 - 4.0 * (d - 1.0) * wd);
     K.idg = wd * c->dx;
-    K.theta_ref = (c->precision == LB_FP64) ? 0.0 : c->theta_ref;
+    K.theta_ref = (c->precision == LB_FP32_SHIFTED) ? c->theta_ref : 0.0;
+    K.fxscale = ldexp(1.0, c->fx_bits);
     init_kernel<L, T><<<(unsigned)((c->nodes + 255) / 256), 256, 0, c->stream>>>(
         (T *)c->f[c->cur], c->geom, K, theta0, grad, flag);
     return cudaGetLastError();
@@ -577,6 +365,13 @@ static cudaError_t init_t(lb_ctx *c, const double *theta0, const double *grad, i
 
 cudaError_t launch_init(lb_ctx *c, const double *theta0, const double *grad, int *flag)
 {
+    if (c->precision == LB_FX64) {
+        switch (c->d) {
+        case 1: return init_t<D1Q3, long long>(c, theta0, grad, flag);
+        case 2: return init_t<D2Q9, long long>(c, theta0, grad, flag);
+        default: return init_t<D3Q19, long long>(c, theta0, grad, flag);
+        }
+    }
     const bool f64 = c->precision == LB_FP64;
     switch (c->d) {
     case 1: return f64 ? init_t<D1Q3, double>(c, theta0, grad, flag) : init_t<D1Q3, float>(c, theta0, grad, flag);
@@ -589,12 +384,27 @@ cudaError_t launch_sum_state(lb_ctx *c, const void *src, double *out_dev)
 {
     const int nb = c->scratch_blocks;
     if (c->precision == LB_FP64)
-        sum_state_kernel<double><<<nb, kRedThreads, 0, c->stream>>>((const double *)src, c->geom, c->q, c->scratch);
+        sum_state_kernel<double><<<nb, kRedThreads, 0, c->stream>>>((const double *)src, c->geom, c->q, 1.0,
+                                                                     c->scratch);
+    else if (c->precision == LB_FX64)
+        sum_state_kernel<long long><<<nb, kRedThreads, 0, c->stream>>>(
+            (const long long *)src, c->geom, c->q, ldexp(1.0, -c->fx_bits), c->scratch);
     else
-        sum_state_kernel<float><<<nb, kRedThreads, 0, c->stream>>>((const float *)src, c->geom, c->q, c->scratch);
+        sum_state_kernel<float><<<nb, kRedThreads, 0, c->stream>>>((const float *)src, c->geom, c->q, 1.0,
+                                                                    c->scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     fold_kernel<<<1, kRedThreads, 0, c->stream>>>(c->scratch, nb, 1, 0u, out_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxabs(lb_ctx *c, const double *x, int64_t n, double *out_dev)
+{
+    const int nb = c->scratch_blocks;
+    maxabs_kernel<<<nb, kRedThreads, 0, c->stream>>>(x, n, c->scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    fold_kernel<<<1, kRedThreads, 0, c->stream>>>(c->scratch, nb, 1, 1u, out_dev);
     return cudaGetLastError();
 }
 

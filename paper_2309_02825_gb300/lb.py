@@ -23,7 +23,7 @@ import torch
 from . import build as _build
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ESTATE, LB_ETIMEOUT, LB_ENONPOS = range(7)
-LB_FP64, LB_FP32_SHIFTED = 0, 1
+LB_FP64, LB_FP32_SHIFTED, LB_FX64 = 0, 1, 2
 _STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ESTATE",
            5: "LB_ETIMEOUT", 6: "LB_ENONPOS"}
 
@@ -113,7 +113,8 @@ def _stream_handle(stream):
 
 def lb_create(d, N, nu, dx, dt, relax=None, precision=LB_FP64, stream=None):
     lib = load()
-    arr = (ctypes.c_int64 * 3)(*[int(n) for n in N])
+    sizes = [int(n) for n in N]
+    arr = (ctypes.c_int64 * max(3, len(sizes)))(*sizes)
     rs = lb_relax(1, 0, 0, 0, 0, 0, 0.0)
     if relax is not None:
         if relax.get("paper_set", False) or "s1" not in relax:
@@ -136,9 +137,10 @@ def lb_destroy(ctx):
 
 def lb_get_params(ctx):
     lib = load()
-    buf = (ctypes.c_double * 14)()
+    buf = (ctypes.c_double * 15)()
     _check(lib, ctx, lib.lb_get_params(ctx, buf), "lb_get_params")
-    keys = ("eps", "c", "cs2", "s1", "s2x", "s22", "w0", "w1", "wd", "nu", "dx", "dt", "q", "theta_ref")
+    keys = ("eps", "c", "cs2", "s1", "s2x", "s22", "w0", "w1", "wd", "nu", "dx", "dt", "q", "theta_ref",
+            "fx_bits")
     return dict(zip(keys, list(buf)))
 
 
@@ -216,7 +218,8 @@ class Solver:
 
     ``relax`` = None uses Theorem 2's relaxation set; a dict with s1, s2x,
     s22, w1, wd overrides it.  ``precision`` is "fp64" or "fp32s" (FP32
-    shifted storage around ``theta_ref``).
+    shifted storage around ``theta_ref``) or "fx64" (64-bit fixed-point
+    storage with exact integer moment sums).
     """
 
     def __init__(self, d, N, nu, dx, dt, relax=None, precision="fp64", theta_ref=0.0, stream=None):
@@ -230,7 +233,7 @@ class Solver:
         self.nodes = 1
         for n in self.N:
             self.nodes *= n
-        self.precision = {"fp64": LB_FP64, "fp32s": LB_FP32_SHIFTED}[precision]
+        self.precision = {"fp64": LB_FP64, "fp32s": LB_FP32_SHIFTED, "fx64": LB_FX64}[precision]
         rel = dict(relax or {})
         rel["theta_ref"] = float(theta_ref)
         self.stream = stream

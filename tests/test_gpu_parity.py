@@ -84,24 +84,28 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fx64"])
 @pytest.mark.parametrize("d,N,nsteps", CASES)
-def test_fp64_matches_oracle(d, N, nsteps):
-    ref, got, _, m = _run_both(d, N, nsteps)
+def test_fp64_matches_oracle(d, N, nsteps, precision):
+    """FP64 storage and 64-bit fixed-point storage both meet the FP64 bar."""
+    ref, got, _, m = _run_both(d, N, nsteps, precision=precision)
     rel = _check_fp64(ref, got, m, nsteps)
-    print("fp64 parity d=%d N=%s steps=%d rel: %s" % (d, N, nsteps, rel))
+    print("%s parity d=%d N=%s steps=%d rel: %s" % (precision, d, N, nsteps, rel))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fx64"])
 @pytest.mark.parametrize("d,N", [(1, (50,)), (2, (66, 40)), (3, (20, 18, 9))])
-def test_fp64_fd_gradient_fallback(d, N):
-    ref, got, _, m = _run_both(d, N, 5, grad=False)
+def test_fp64_fd_gradient_fallback(d, N, precision):
+    ref, got, _, m = _run_both(d, N, 5, grad=False, precision=precision)
     _check_fp64(ref, got, m, 5)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fx64"])
 @pytest.mark.parametrize("d", [1, 2, 3])
-def test_fp64_custom_relaxation_set(d):
+def test_fp64_custom_relaxation_set(d, precision):
     relax = {"s1": 1.3, "s2x": 0.7, "s22": 1.1, "w1": 0.12, "wd": 0.02 if d > 1 else 0.0}
     N = [(90,), (40, 30), (20, 12, 10)][d - 1]
-    ref, got, _, m = _run_both(d, N, 11, relax=relax)
+    ref, got, _, m = _run_both(d, N, 11, relax=relax, precision=precision)
     _check_fp64(ref, got, m, 11)
 
 
@@ -112,6 +116,29 @@ def test_sum_theta_conserved_and_matches_oracle(d, N):
     assert abs(total - th_o.sum()) <= 1e-13 * abs(th_o.sum())
     prob, dx, _ = _problem(d, N, 11)
     assert abs(total - prob.theta(N, dx).sum()) <= 1e-12 * abs(total)
+
+
+@pytest.mark.parametrize("d,N", [(1, (77,)), (2, (70, 45)), (3, (24, 10, 7))])
+def test_fx64_conserves_sum_exactly(d, N):
+    """Fixed point: the rest population is theta minus the others, so the
+    integer sum of the state never changes; lb_sum_theta only rounds when it
+    converts each stored value to FP64."""
+    prob, dx, dt = _problem(d, N, 11)
+    s = lb.Solver(d, N, prob.nu, dx, dt, precision="fx64")
+    s.set_theta0(_dev(prob.theta(N, dx)), _dev(prob.grad(N, dx)))
+    t0 = s.sum_theta()
+    s.step(40)
+    t1 = s.sum_theta()
+    snap = s.save_state().view(torch.int64)
+    s.step(1)
+    snap2 = s.save_state().view(torch.int64)
+    pitch, slab, _ = s.state_layout()
+    q = int(s.params["q"])
+    mask = (torch.arange(pitch, device="cuda") < N[0])
+    tot = [int((sn.view(q, -1, pitch) * mask).sum().item()) for sn in (snap, snap2)]
+    assert tot[0] == tot[1]
+    assert abs(t1 - t0) <= 1e-14 * abs(t0)
+    assert 40 <= s.params["fx_bits"] <= 56
 
 
 def test_reduce_norms_match_numpy():
