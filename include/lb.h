@@ -51,8 +51,8 @@ typedef enum {
     LB_FP64 = 0,         /* distributions stored and updated in IEEE double */
     LB_FP32_SHIFTED = 1, /* stored and updated in float as f - w*theta_ref */
     LB_FX64 = 2          /* stored as 64-bit fixed point round(f * 2^F), with F
-                            chosen by lb_set_theta0 from max|theta0| (about 55 -
-                            log2 max|theta0|, i.e. 7 bits of headroom); moment
+                            chosen by lb_set_theta0 so that max|theta0| * 2^F <
+                            2^59 (sums up to 16 max|theta0| fit); moment
                             sums are exact integer additions, each relaxation
                             product is rounded once (2^-62 relative), and the
                             rest population is theta minus the others, so
@@ -114,7 +114,9 @@ lb_status lb_get_params(const lb_ctx *ctx, double *out);
  *                to use a fourth-order central difference of theta0.
  * Resets the step counter to 0.  For LB_FX64 it also fixes the fixed-point
  * scale F from max|theta0|.  Synchronises the stream.
- * Errors: LB_EINVAL (NULL theta0), LB_ENONPOS (theta0 <= 0 or non-finite
+ * Errors: LB_EINVAL (NULL theta0; for LB_FX64 also an initial value beyond
+ * 4 max|theta0|, i.e. a gradient too steep for the fixed-point range),
+ * LB_ENONPOS (theta0 <= 0 or non-finite
  * somewhere, or a non-finite gradient; the state is then left uninitialised),
  * LB_ECUDA.
  */

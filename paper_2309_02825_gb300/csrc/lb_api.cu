@@ -206,8 +206,10 @@ lb_status lb_set_theta0(lb_ctx *c, const double *theta0, const double *grad)
     if ((e = cudaMemsetAsync(c->dflag, 0, sizeof(int), c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "lb_set_theta0: flag reset");
     if (c->precision == LB_FX64) {
-        // Fixed-point scale: max|theta0| * 2^F <= 2^55 leaves 7 bits of
-        // headroom for sums of up to 19 values and for transients.
+        // Fixed-point scale: max|theta0| * 2^F < 2^59.  Every moment sum is
+        // bounded by sum_k |f_k|, which stays near theta for a stable run, so
+        // 4 bits of headroom (16 max|theta0|) cover the sums and transients;
+        // the initialisation flags any value beyond 4 max|theta0|.
         double mx = 0.0;
         if ((e = lbk::launch_maxabs(c, theta0, c->nodes, c->dout)) != cudaSuccess ||
             (e = cudaMemcpyAsync(&mx, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
@@ -216,7 +218,9 @@ lb_status lb_set_theta0(lb_ctx *c, const double *theta0, const double *grad)
         if (!(mx > 0.0) || !isfinite(mx)) return fail(c, LB_ENONPOS, "lb_set_theta0: theta0 must be finite and > 0");
         int ex = 0;
         frexp(mx, &ex);  // mx < 2^ex
-        c->fx_bits = 55 - ex;
+        c->fx_bits = 59 - ex;
+        if (c->fx_bits > 1000 || c->fx_bits < -1000)
+            return fail(c, LB_EINVAL, "lb_set_theta0: theta0 magnitude outside the fixed-point range");
     }
     c->cur = 0;
     if ((e = lbk::launch_init(c, theta0, grad, c->dflag)) != cudaSuccess)
@@ -225,6 +229,7 @@ lb_status lb_set_theta0(lb_ctx *c, const double *theta0, const double *grad)
     if ((e = cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "lb_set_theta0");
+    if (flag & 2) return fail(c, LB_EINVAL, "lb_set_theta0: initial distributions exceed the fixed-point range");
     if (flag) return fail(c, LB_ENONPOS, "lb_set_theta0: theta0 must be finite and > 0 (and grad finite)");
     c->initialized = true;
     c->step = 0;

@@ -53,11 +53,17 @@ __device__ __forceinline__ void st_vec(long long *p, const long long (&a)[2])
 }
 
 // Conversion of an FP64 value to the storage type (64-bit fixed point uses
-// round-to-nearest of v * 2^F).
-template <typename T> __device__ __forceinline__ T to_store(double v, double) { return (T)v; }
-template <> __device__ __forceinline__ long long to_store<long long>(double v, double fxscale)
+// round-to-nearest of v * 2^F).  `range` is set when a fixed-point value
+// would exceed 2^61 (4x the largest theta0), leaving the sums their headroom.
+template <typename T> __device__ __forceinline__ T to_store(double v, double, bool &) { return (T)v; }
+template <> __device__ __forceinline__ long long to_store<long long>(double v, double fxscale, bool &range)
 {
-    return __double2ll_rn(v * fxscale);
+    const double s = v * fxscale;
+    if (!(fabs(s) < 0x1p61)) {
+        range = true;
+        return 0;
+    }
+    return __double2ll_rn(s);
 }
 
 // Pull V consecutive values of one population along x with shift EX:

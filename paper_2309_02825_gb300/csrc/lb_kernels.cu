@@ -92,6 +92,7 @@ __global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *
         if (bad) atomicOr(flag, 1);
     }
     T *out = dst + ((int64_t)z * g.N1 + y) * g.pitch + x;
+    bool range = false;
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
@@ -118,8 +119,9 @@ __global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *
             val -= K.wd * K.theta_ref;
         }
         if constexpr (nz == 0) val -= K.w0 * K.theta_ref;
-        out[(int64_t)i * g.slab] = to_store<T>(val, K.fxscale);
+        out[(int64_t)i * g.slab] = to_store<T>(val, K.fxscale, range);
     });
+    if (range) atomicOr(flag, 2);
 }
 
 // Fourth-order central difference of theta along each axis (periodic).

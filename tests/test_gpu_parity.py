@@ -6,6 +6,8 @@ Grids are chosen to span several warp segments (64 nodes in x for FP64,
 128 for FP32) with ragged tails, plus degenerate sizes (N = 1, 2, 3 along an
 axis) where every node is at the periodic wrap.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -125,7 +127,8 @@ def test_fx64_conserves_sum_exactly(d, N):
     converts each stored value to FP64."""
     prob, dx, dt = _problem(d, N, 11)
     s = lb.Solver(d, N, prob.nu, dx, dt, precision="fx64")
-    s.set_theta0(_dev(prob.theta(N, dx)), _dev(prob.grad(N, dx)))
+    th0 = prob.theta(N, dx)
+    s.set_theta0(_dev(th0), _dev(prob.grad(N, dx)))
     t0 = s.sum_theta()
     s.step(40)
     t1 = s.sum_theta()
@@ -138,7 +141,8 @@ def test_fx64_conserves_sum_exactly(d, N):
     tot = [int((sn.view(q, -1, pitch) * mask).sum().item()) for sn in (snap, snap2)]
     assert tot[0] == tot[1]
     assert abs(t1 - t0) <= 1e-14 * abs(t0)
-    assert 40 <= s.params["fx_bits"] <= 56
+    # max|theta0| * 2^F < 2^59 with the largest such F
+    assert lb.lb_get_params(s.ctx)["fx_bits"] == 59 - math.frexp(float(th0.max()))[1]
 
 
 def test_reduce_norms_match_numpy():
