@@ -172,6 +172,35 @@ lb_status lb_reduce(lb_ctx *ctx, const double *theta, const double *u,
                     const double *exact_theta, const double *exact_u, double *out);
 
 /*
+ * Error norms without any device allocation.  The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc -- a host application
+ * whose framework owns all device memory through its own caching allocator,
+ * a service held to a device-memory budget fixed up front, or code where the
+ * implicit synchronisation of an allocation is not allowed -- and that
+ * therefore have no context (lb_create allocates).
+ * Same inputs and results as lb_reduce, with device pointers throughout:
+ *   d            1, 2 or 3;  nodes: number of nodes, 1 .. 2^31.
+ *   theta, exact_theta  device, nodes values each; u, exact_u device,
+ *                d*nodes values each, or both NULL.
+ *   out          DEVICE pointer to 3(d+1)+1 doubles, written in lb_reduce's
+ *                layout (RMSE, Linf, rel L2 per variable, then sum theta).
+ *   stream       a cudaStream_t (NULL = legacy default stream); asynchronous.
+ * Scratch: a file-scope __device__ array of 131,200 bytes (1024 partial
+ * rows of 16 doubles plus one row of raw sums) that every GPU loading this
+ * library holds until the process exits.  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress) with the device
+ * current; make that first call before any stream capture.  Each call
+ * overwrites every row it reads, so nothing needs clearing between calls,
+ * but all calls share the one array: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be ordered by the caller.
+ * Errors: LB_EINVAL (d outside 1..3, nodes outside 1..2^31, a NULL input or
+ * out, u without exact_u), LB_ECUDA (address lookup or launch failed); no
+ * message is recorded for lb_last_error.
+ */
+lb_status lb_reduce_static(int d, int64_t nodes, const double *theta, const double *u,
+                           const double *exact_theta, const double *exact_u, double *out, void *stream);
+
+/*
  * Copy the raw distribution state to/from a caller buffer (checkpointing).
  * The state is q arrays in the context's padded layout (lb_state_layout):
  * value (i, x, y, z) sits at element i*slab + (z*N[1] + y)*pitch + x.

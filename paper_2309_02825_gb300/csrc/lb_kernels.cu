@@ -429,4 +429,24 @@ cudaError_t launch_norms(lb_ctx *c, const double *th, const double *u, const dou
     return cudaGetLastError();
 }
 
+// Norm reduction into caller-provided partial rows (nblocks of kRedSlots)
+// and one raw-sum row; used by the allocation-free entry point.
+cudaError_t launch_norms_into(int d, int64_t nodes, const double *th, const double *u, const double *eth,
+                              const double *eu, double *partials, int nb, double *raw_out, cudaStream_t s)
+{
+    const int ns = 3 * (d + 1) + 1;
+    unsigned mask = 0;
+    for (int k = 0; k < ns - 1; ++k)
+        if (k % 3 == 1) mask |= 1u << k;
+    switch (d) {
+    case 1: norms_kernel<1><<<nb, kRedThreads, 0, s>>>(th, u, eth, eu, nodes, partials); break;
+    case 2: norms_kernel<2><<<nb, kRedThreads, 0, s>>>(th, u, eth, eu, nodes, partials); break;
+    default: norms_kernel<3><<<nb, kRedThreads, 0, s>>>(th, u, eth, eu, nodes, partials); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    fold_kernel<<<1, kRedThreads, 0, s>>>(partials, nb, ns, mask, raw_out);
+    return cudaGetLastError();
+}
+
 }  // namespace lbk

@@ -74,6 +74,7 @@ def load():
             "lb_save_state": ([vp, vp], ctypes.c_int),
             "lb_load_state": ([vp, vp, i64], ctypes.c_int),
             "lb_last_error": ([vp], ctypes.c_char_p),
+            "lb_reduce_static": ([ctypes.c_int, i64, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -189,6 +190,17 @@ def lb_reduce(ctx, theta, u, exact_theta, exact_u, d):
            for v, nm in enumerate(names)}
     out["sum_theta"] = vals[-1]
     return out
+
+
+def lb_reduce_static(d, nodes, theta, u, exact_theta, exact_u, out, stream=None):
+    """Allocation-free error norms (device output ``out`` of 3(d+1)+1 doubles),
+    for callers that cannot allocate device memory; see include/lb.h."""
+    lib = load()
+    st = lib.lb_reduce_static(int(d), int(nodes), _ptr(theta, "theta"), _ptr(u, "u"),
+                              _ptr(exact_theta, "exact_theta"), _ptr(exact_u, "exact_u"),
+                              _ptr(out, "out"), _stream_handle(stream))
+    if st != LB_OK:
+        raise LBError(st, "lb_reduce_static")
 
 
 def lb_state_layout(ctx):
