@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variant", action="store_true", help="skip the other precisions' sub-results")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched 512-instance measurement")
     return p.parse_args()
 
 
@@ -307,6 +308,68 @@ def run_e2e(args, s, case, th0_h, g0_h, ex_t_h, ex_u_h, stream, world):
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
+def run_batched(local):
+    """512 independent 2D instances (N log-uniform in [32, 512], nu log-uniform
+    in [0.005, 0.1], dt = 4 dx^2), FP32 shifted, 2000 steps: autotuned L2-sized
+    groups vs one launch per instance per step vs one flat launch per step."""
+    import torch
+    from paper_2309_02825_gb300 import lb
+
+    torch.cuda.set_device(local)
+    cases = W.batched_2d(512, nsteps=2000)
+    sizes = [c.N for c in cases]
+    th0 = np.concatenate([c.problem.theta(c.N, c.dx).ravel() for c in cases])
+    g0 = np.concatenate([np.ascontiguousarray(c.problem.grad(c.N, c.dx)).ravel() for c in cases])
+    stream = torch.cuda.Stream()
+    b = lb.Batch(sizes, [c.nu for c in cases], [c.dx for c in cases], [c.dt for c in cases],
+                 precision="fp32s", theta_ref=[1.5] * len(cases), stream=stream)
+    choice = b.autotune(10)
+    th0_d, g0_d = torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda()
+    nodes = b.total_nodes
+    steps = cases[0].nsteps
+
+    def timed(n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            b.set_theta0(th0_d, g0_d)
+            b.step(64)  # warm-up (graphs recorded, L2 warm)
+            b.set_theta0(th0_d, g0_d)
+            e0.record(stream)
+            b.step(n)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    t_tuned = timed(steps)
+    with torch.cuda.stream(stream):
+        th, u = b.macros()
+        ex_t = np.concatenate([c.problem.theta(c.N, c.dx, c.t_end).ravel() for c in cases])
+        ex_u = np.concatenate([np.ascontiguousarray(c.problem.u(c.N, c.dx, c.t_end)).ravel() for c in cases])
+        err = b.errors(th, u, torch.from_numpy(ex_t).cuda(), torch.from_numpy(ex_u).cuda())
+    sched = b.schedule()
+    base_steps = 100
+    b.set_schedule(0.0, 256, False)
+    t_base = timed(base_steps) * steps / base_steps
+    b.set_schedule(1e18, 256, True)
+    t_flat = timed(base_steps * 2) * steps / (base_steps * 2)
+    b.close()
+    lu = nodes * steps
+    return {
+        "workload": "512 x 2D D2Q9, N log-uniform [32,512], nu log-uniform [0.005,0.1], dt=4dx^2, fp32 shifted, "
+                    "2000 steps",
+        "instances": len(cases), "total_nodes": nodes, "steps": steps,
+        "instances_per_s": len(cases) / t_tuned, "aggregate_mlups": lu / t_tuned / 1e6, "seconds": t_tuned,
+        "schedule": {"budget_bytes": sched["budget_bytes"], "threads": sched["threads"], "groups": sched["groups"]},
+        "autotune": choice,
+        "one_launch_per_instance": {"aggregate_mlups": lu / t_base / 1e6, "instances_per_s": len(cases) / t_base,
+                                    "sample_steps": base_steps},
+        "flat_one_group": {"aggregate_mlups": lu / t_flat / 1e6, "sample_steps": 2 * base_steps},
+        "speedup_vs_one_launch_per_instance": t_base / t_tuned,
+        "u_rmse_max_over_instances": float(np.max(err[:, 1])),
+        "theta_rmse_max_over_instances": float(np.max(err[:, 0])),
+    }
+
+
 # ---------------------------------------------------------------------------
 # The oracle (CPU baseline / reference arm).
 # ---------------------------------------------------------------------------
@@ -380,6 +443,9 @@ def main():
             if "roofline_fp64_pipe" in v:
                 entry["roofline_fp64_pipe"] = v["roofline_fp64_pipe"]
             variants.append(entry)
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(local)
     base = None
     if rank == 0 and not args.no_cpu_baseline:
         base = cpu_baseline(args)
@@ -408,6 +474,8 @@ def main():
             line["roofline_fp64_pipe"] = main_res["roofline_fp64_pipe"]
         if variants:
             line["variants"] = variants
+        if batched:
+            line["batched"] = batched
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -1,0 +1,107 @@
+/*
+ * lb_batch.h - many independent 2D periodic MRT-LB instances advanced together.
+ *
+ * Each instance is a separate D2Q9 problem of Sec. III.A (its own N, nu, dx,
+ * dt and relaxation set of Theorem 2, Eq. (Bur-Sol)); the paper runs one
+ * problem at a time, so batching is a throughput feature of this library.
+ * Conventions are those of lb.h (status codes, caller-owned device arrays,
+ * stream order).  Fields of all instances are concatenated in instance
+ * order: instance j contributes N0_j*N1_j values (x fastest) to a scalar
+ * array and 2*N0_j*N1_j (x component first) to a vector array; offsets are
+ * the prefix sums of N0_j*N1_j.
+ *
+ * Scheduling: instances are bin-packed (largest first) into groups whose two
+ * state buffers fit a byte budget chosen to stay resident in L2.  A group
+ * runs all requested steps back to back, one launch per step (each block of
+ * a launch belongs to one instance), so its state is read from L2 rather
+ * than HBM after the first step.  The launches are recorded once into CUDA
+ * graphs and replayed.  lb_batch_autotune times candidate budgets and block
+ * shapes on the caller's batch and keeps the fastest.
+ */
+#ifndef LB_BATCH_H
+#define LB_BATCH_H
+
+#include <stdint.h>
+
+#include "lb.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_batch lb_batch;
+
+/*
+ * Create a batch of `count` (1..65536) 2D instances.
+ *   N     host, 2*count sizes (N0_j, N1_j), each in [1, 2^16].
+ *   nu, dx, dt  host, count values each (> 0, finite).
+ *   rs    host, count relaxation sets, or NULL for Eq. (Bur-Sol) everywhere
+ *         (theta_ref then 0 for every instance; see lb_batch_set_theta_ref).
+ *   precision  LB_FP32_SHIFTED or LB_FP64.
+ *   stream     cudaStream_t (NULL = legacy default stream).
+ * Allocates two state buffers for all instances plus small tables.
+ * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA.
+ */
+lb_status lb_batch_create(int count, const int64_t *N, const double *nu, const double *dx, const double *dt,
+                          const lb_relax *rs, int precision, void *stream, lb_batch **out);
+
+lb_status lb_batch_destroy(lb_batch *b);
+
+/* FP32-shifted reference values, host array of count (default: from rs, else 0). */
+lb_status lb_batch_set_theta_ref(lb_batch *b, const double *theta_ref);
+
+/*
+ * Initialise every instance as lb_set_theta0 does (Sec. IV, Eq. (f-feq-o5)).
+ *   theta0  device, concatenated scalar fields (all > 0).
+ *   grad0   device, concatenated vector fields, or NULL for fourth-order
+ *           central differences.
+ * Synchronises the stream.  Errors: LB_EINVAL, LB_ENONPOS, LB_ECUDA.
+ */
+lb_status lb_batch_set_theta0(lb_batch *b, const double *theta0, const double *grad0);
+
+/* Advance every instance nsteps (Eq. (distribution-f)); asynchronous. */
+lb_status lb_batch_step(lb_batch *b, int64_t nsteps);
+
+/*
+ * Recovery for every instance (Sec. III.C), FP64.  theta: device,
+ * concatenated scalars; u: device, concatenated vectors; either may be NULL.
+ */
+lb_status lb_batch_macros(lb_batch *b, double *theta, double *u);
+
+/*
+ * Per-instance error norms against concatenated reference fields:
+ * out (host) receives 4 values per instance: RMSE(theta), RMSE(|u|) (root of
+ * the mean over nodes of the squared error summed over both components),
+ * Linf(theta), Linf(u components).  FP64.  Synchronises the stream.
+ */
+lb_status lb_batch_errors(lb_batch *b, const double *theta, const double *u, const double *exact_theta,
+                          const double *exact_u, double *out);
+
+/*
+ * Autotuner: times `trial_steps` steps for each candidate (group byte budget
+ * x block size) on this batch's real sizes and keeps the fastest.  Must be
+ * called before lb_batch_set_theta0 (it overwrites the state).  choice
+ * (host, may be NULL) receives {budget_bytes, threads_per_block, groups,
+ * microseconds per step of the winner}.  Synchronises the stream.
+ */
+lb_status lb_batch_autotune(lb_batch *b, int trial_steps, double *choice);
+
+/*
+ * Set the schedule explicitly: budget_bytes <= 0 puts every instance in its
+ * own group (one launch per instance per step), a budget above the total
+ * state puts all instances in one group (one launch per step); threads is
+ * 128, 256 or 512; use_graph = 0 launches every step directly instead of
+ * replaying recorded graphs.  Keeps the state.
+ */
+lb_status lb_batch_set_schedule(lb_batch *b, double budget_bytes, int threads, int use_graph);
+
+/* Current schedule: {budget_bytes, threads_per_block, groups, total nodes}. */
+lb_status lb_batch_schedule(const lb_batch *b, double *info);
+
+const char *lb_batch_last_error(const lb_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_BATCH_H */

@@ -22,7 +22,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbgb300.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+# Host code: no FP contraction, so the scalar parameter derivation gives the
+# same bits on x86 and Arm hosts and in every translation unit.
+NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
                   "-I", os.path.join(ROOT, "include")]
 
 

@@ -59,6 +59,44 @@ struct DeviceGuard {
 
 }  // namespace
 
+namespace lbk {
+
+bool derive_params(lb_ctx &c, const lb_relax *rs)
+{
+    const int d = c.d;
+    const bool paper = !rs || rs->paper_set;
+    if (paper) {
+        const double a = 6.0 * c.eps + 1.0;
+        c.s1 = 2.0 / a;
+        c.s2x = 24.0 * c.eps / (a * a);
+        if (d == 1) {
+            c.s22 = 1.0;
+            c.w1 = 1.0 / 6.0;
+            c.wd = 0.0;
+        } else {
+            c.s22 = 4.0 / (6.0 * c.eps + 3.0);
+            c.w1 = 1.0 / 6.0 - (d - 1) * c.eps / 3.0;
+            c.wd = c.eps / 6.0;
+        }
+    } else {
+        c.s1 = rs->s1;
+        c.s2x = rs->s2x;
+        c.s22 = (d > 1) ? rs->s22 : 1.0;
+        c.w1 = rs->w1;
+        c.wd = (d > 1) ? rs->wd : 0.0;
+    }
+    c.theta_ref = rs ? rs->theta_ref : 0.0;
+    const bool rates_ok = c.s1 > 0 && c.s1 < 2 && c.s2x > 0 && c.s2x < 2 && (d == 1 || (c.s22 > 0 && c.s22 < 2));
+    if (!rates_ok || !isfinite(c.w1) || !isfinite(c.wd) || !isfinite(c.theta_ref)) return false;
+    // Eq. (d1-3-weight) and c_s^2 = [2 w1 + 4(d-1) wd] c^2.
+    c.w0 = 1.0 - 2.0 * d * c.w1 - 2.0 * d * (d - 1) * c.wd;
+    c.sigma = 2.0 * c.w1 + 4.0 * (d - 1) * c.wd;
+    c.cs2 = c.sigma * c.c * c.c;
+    return true;
+}
+
+}  // namespace lbk
+
 extern "C" {
 
 lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt, const lb_relax *rs, int precision,
@@ -94,38 +132,10 @@ lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt, co
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
 
-    // Relaxation set: Theorem 2, Eq. (Bur-Sol), or the caller's.
-    const bool paper = !rs || rs->paper_set;
-    if (paper) {
-        const double a = 6.0 * c->eps + 1.0;
-        c->s1 = 2.0 / a;
-        c->s2x = 24.0 * c->eps / (a * a);
-        if (d == 1) {
-            c->s22 = 1.0;
-            c->w1 = 1.0 / 6.0;
-            c->wd = 0.0;
-        } else {
-            c->s22 = 4.0 / (6.0 * c->eps + 3.0);
-            c->w1 = 1.0 / 6.0 - (d - 1) * c->eps / 3.0;
-            c->wd = c->eps / 6.0;
-        }
-    } else {
-        c->s1 = rs->s1;
-        c->s2x = rs->s2x;
-        c->s22 = (d > 1) ? rs->s22 : 1.0;
-        c->w1 = rs->w1;
-        c->wd = (d > 1) ? rs->wd : 0.0;
-    }
-    c->theta_ref = rs ? rs->theta_ref : 0.0;
-    const bool rates_ok = c->s1 > 0 && c->s1 < 2 && c->s2x > 0 && c->s2x < 2 && (d == 1 || (c->s22 > 0 && c->s22 < 2));
-    if (!rates_ok || !isfinite(c->w1) || !isfinite(c->wd) || !isfinite(c->theta_ref)) {
+    if (!lbk::derive_params(*c, rs)) {
         free_ctx(c);
         return fail(nullptr, LB_EINVAL, "lb_create: relaxation rates must lie in (0, 2) and weights be finite");
     }
-    // Eq. (d1-3-weight) and c_s^2 = [2 w1 + 4(d-1) wd] c^2.
-    c->w0 = 1.0 - 2.0 * d * c->w1 - 2.0 * d * (d - 1) * c->wd;
-    c->sigma = 2.0 * c->w1 + 4.0 * (d - 1) * c->wd;
-    c->cs2 = c->sigma * c->c * c->c;
 
     // Layout.
     const int V = (precision == LB_FP32_SHIFTED) ? lbk::Vec<float>::V : lbk::Vec<double>::V;

@@ -1,0 +1,588 @@
+// Batched 2D MRT-LB (include/lb_batch.h): many independent D2Q9 instances.
+//
+// State: two big buffers; instance j owns q slabs of its own padded layout
+// at element offset off_j in both.  A step kernel launch covers one group
+// of instances; every block belongs to exactly one instance (its warps take
+// consecutive row segments of that instance), so a block reads the
+// instance descriptor once and then runs the same pull + collide as the
+// single-grid sweep.  Groups are sized so that their two buffers stay in
+// L2 while the group runs all its steps back to back; the launches are
+// replayed from CUDA graphs.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/lb_batch.h"
+#include "lb_device.cuh"
+
+namespace lbk {
+
+template <typename T> struct InstDesc {
+    Geom g;
+    Coll<T> k;
+    int64_t off;  // element offset of the instance's state in each buffer
+};
+
+constexpr int kBatchMaxThreads = 512;
+
+template <class L, typename T>
+__global__ void __launch_bounds__(kBatchMaxThreads) batch_sweep_kernel(const InstDesc<T> *__restrict__ inst,
+                                                                       const int *__restrict__ blk_inst,
+                                                                       const int *__restrict__ blk_seg0,
+                                                                       const T *__restrict__ src,
+                                                                       T *__restrict__ dst)
+{
+    constexpr int V = Vec<T>::V;
+    const InstDesc<T> D = inst[blk_inst[blockIdx.x]];
+    const int lane = threadIdx.x & 31;
+    const int64_t seg = (int64_t)blk_seg0[blockIdx.x] + (threadIdx.x >> 5);
+    if (seg >= D.g.nseg) return;  // warp-uniform
+    const int64_t row = seg / D.g.seg_per_row;
+    const int x0 = (int)(seg - row * D.g.seg_per_row) * (32 * V);
+    const T *s = src + D.off;
+    T *d = dst + D.off;
+
+    T f[L::Q][V];
+    gather<L, T>(s, D.g, row, x0, lane, f);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        T n[L::Q];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) n[i] = f[i][v];
+        collide(L{}, n, D.k);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) f[i][v] = n[i];
+    }
+    T *dp = d + row * D.g.pitch + x0 + V * lane;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * D.g.slab, f[i]);
+}
+
+// Per-instance error sums: one block per instance, FP64, fixed order.
+__global__ void __launch_bounds__(kRedThreads) batch_errors_kernel(const int64_t *__restrict__ node_off,
+                                                                   const double *__restrict__ th,
+                                                                   const double *__restrict__ u,
+                                                                   const double *__restrict__ eth,
+                                                                   const double *__restrict__ eu,
+                                                                   int64_t total_nodes, double *__restrict__ out)
+{
+    const int j = blockIdx.x;
+    const int64_t n0 = node_off[j], n1 = node_off[j + 1];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};  // sum e_theta^2, sum |e_u|^2, max|e_theta|, max|e_u|
+    for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+        const double et = th[n] - eth[n];
+        a[0] += et * et;
+        a[2] = fmax(a[2], fabs(et));
+        if (u) {
+            // components of instance j: x block then y block, each n1 - n0 long
+            const int64_t m = n - n0;
+            const double ex = u[2 * n0 + m] - eu[2 * n0 + m];
+            const double ey = u[2 * n0 + (n1 - n0) + m] - eu[2 * n0 + (n1 - n0) + m];
+            a[1] += ex * ex + ey * ey;
+            a[3] = fmax(a[3], fmax(fabs(ex), fabs(ey)));
+        }
+    }
+    __shared__ double sh[4][kRedThreads];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = a[k];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+            sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + w]);
+            sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double nn = (double)(n1 - n0);
+        out[4 * j + 0] = sqrt(sh[0][0] / nn);
+        out[4 * j + 1] = sqrt(sh[1][0] / nn);
+        out[4 * j + 2] = sh[2][0];
+        out[4 * j + 3] = sh[3][0];
+    }
+    (void)total_nodes;
+}
+
+}  // namespace lbk
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Group {
+    std::vector<int> members;
+    int64_t bytes = 0;
+    int nblocks = 0;
+    int *d_blk_inst = nullptr;
+    int *d_blk_seg0 = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by starting buffer
+};
+
+constexpr int kGraphSteps = 32;  // launches per recorded graph (even)
+
+}  // namespace
+
+struct lb_batch {
+    int count = 0;
+    int precision = LB_FP32_SHIFTED;
+    size_t elem = 4;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::vector<lb_ctx> inst;  // host views: parameters + geometry per instance
+    std::vector<int64_t> off, node_off;
+    int64_t total_elems = 0, total_nodes = 0;
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *d_desc = nullptr;
+    int64_t *d_node_off = nullptr;
+    double *d_err = nullptr;
+    int *d_flag = nullptr;
+    double *gradtmp = nullptr;
+    double budget = 0;
+    int threads = 256;
+    bool use_graph = true;
+    std::vector<Group> groups;
+    bool initialized = false;
+    std::string err;
+};
+
+namespace {
+
+lb_status bfail(lb_batch *b, lb_status s, const std::string &m)
+{
+    if (b) b->err = m;
+    return s;
+}
+
+lb_status bcuda(lb_batch *b, cudaError_t e, const char *where)
+{
+    return bfail(b, e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA,
+                 std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void free_groups(lb_batch *b)
+{
+    for (Group &g : b->groups) {
+        cudaFree(g.d_blk_inst);
+        cudaFree(g.d_blk_seg0);
+        for (auto &ge : g.graph)
+            if (ge) cudaGraphExecDestroy(ge);
+    }
+    b->groups.clear();
+}
+
+void free_batch(lb_batch *b)
+{
+    if (!b) return;
+    free_groups(b);
+    cudaFree(b->buf[0]);
+    cudaFree(b->buf[1]);
+    cudaFree(b->d_desc);
+    cudaFree(b->d_node_off);
+    cudaFree(b->d_err);
+    cudaFree(b->d_flag);
+    cudaFree(b->gradtmp);
+    delete b;
+}
+
+template <typename T> cudaError_t upload_desc(lb_batch *b)
+{
+    std::vector<lbk::InstDesc<T>> h(b->count);
+    for (int j = 0; j < b->count; ++j) {
+        h[j].g = b->inst[j].geom;
+        h[j].k = lbk::make_coll<T>(b->inst[j]);
+        h[j].off = b->off[j];
+    }
+    cudaError_t e = cudaMalloc(&b->d_desc, sizeof(lbk::InstDesc<T>) * b->count);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(b->d_desc, h.data(), sizeof(lbk::InstDesc<T>) * b->count, cudaMemcpyHostToDevice);
+}
+
+// Launch one step for group g from buffer `from`.
+cudaError_t launch_group(lb_batch *b, const Group &g, int from, cudaStream_t s)
+{
+    if (g.nblocks == 0) return cudaSuccess;
+    if (b->precision == LB_FP64)
+        lbk::batch_sweep_kernel<lbk::D2Q9, double><<<g.nblocks, b->threads, 0, s>>>(
+            (const lbk::InstDesc<double> *)b->d_desc, g.d_blk_inst, g.d_blk_seg0, (const double *)b->buf[from],
+            (double *)b->buf[from ^ 1]);
+    else
+        lbk::batch_sweep_kernel<lbk::D2Q9, float><<<g.nblocks, b->threads, 0, s>>>(
+            (const lbk::InstDesc<float> *)b->d_desc, g.d_blk_inst, g.d_blk_seg0, (const float *)b->buf[from],
+            (float *)b->buf[from ^ 1]);
+    return cudaGetLastError();
+}
+
+// Build groups and block tables for (budget, threads).  budget <= 0: every
+// instance alone; budget >= total: one group.
+lb_status build_schedule(lb_batch *b, double budget, int threads, bool use_graph)
+{
+    free_groups(b);
+    b->budget = budget;
+    b->threads = threads;
+    b->use_graph = use_graph;
+    std::vector<int> order(b->count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c) { return b->inst[a].geom.slab > b->inst[c].geom.slab; });
+    // first-fit decreasing on 2 * state bytes
+    for (int j : order) {
+        const int64_t bytes = 2 * (int64_t)b->inst[j].q * b->inst[j].geom.slab * (int64_t)b->elem;
+        bool placed = false;
+        if (budget > 0)
+            for (Group &g : b->groups)
+                if (g.bytes + bytes <= budget) {
+                    g.members.push_back(j);
+                    g.bytes += bytes;
+                    placed = true;
+                    break;
+                }
+        if (!placed) {
+            Group g;
+            g.members.push_back(j);
+            g.bytes = bytes;
+            b->groups.push_back(g);
+        }
+    }
+    const int warps = threads / 32;
+    for (Group &g : b->groups) {
+        std::vector<int> bi, bs;
+        for (int j : g.members) {
+            const int64_t nseg = b->inst[j].geom.nseg;
+            for (int64_t s0 = 0; s0 < nseg; s0 += warps) {
+                bi.push_back(j);
+                bs.push_back((int)s0);
+            }
+        }
+        g.nblocks = (int)bi.size();
+        cudaError_t e;
+        if ((e = cudaMalloc(&g.d_blk_inst, sizeof(int) * bi.size())) != cudaSuccess ||
+            (e = cudaMalloc(&g.d_blk_seg0, sizeof(int) * bs.size())) != cudaSuccess ||
+            (e = cudaMemcpy(g.d_blk_inst, bi.data(), sizeof(int) * bi.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(g.d_blk_seg0, bs.data(), sizeof(int) * bs.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bcuda(b, e, "lb_batch: schedule tables");
+    }
+    return LB_OK;
+}
+
+// Record kGraphSteps launches of group g starting from buffer `from`.
+cudaError_t record_graph(lb_batch *b, Group &g, int from)
+{
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        int p = from;
+        for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
+            e = launch_group(b, g, p, cs);
+            p ^= 1;
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.graph[from], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    return e;
+}
+
+cudaError_t run_steps(lb_batch *b, int64_t n)
+{
+    cudaError_t e = cudaSuccess;
+    for (Group &g : b->groups) {
+        int p = b->cur;
+        int64_t left = n;
+        if (b->use_graph) {
+            while (left >= kGraphSteps) {
+                if (!g.graph[p]) {
+                    e = record_graph(b, g, p);
+                    if (e != cudaSuccess) return e;
+                }
+                e = cudaGraphLaunch(g.graph[p], b->stream);
+                if (e != cudaSuccess) return e;
+                left -= kGraphSteps;  // even: parity unchanged
+            }
+        }
+        for (; left > 0; --left) {
+            e = launch_group(b, g, p, b->stream);
+            if (e != cudaSuccess) return e;
+            p ^= 1;
+        }
+    }
+    if (n & 1) b->cur ^= 1;
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_batch_create(int count, const int64_t *N, const double *nu, const double *dx, const double *dt,
+                          const lb_relax *rs, int precision, void *stream, lb_batch **out)
+{
+    if (!out) return LB_EINVAL;
+    *out = nullptr;
+    if (count < 1 || count > 65536 || !N || !nu || !dx || !dt) return LB_EINVAL;
+    if (precision != LB_FP32_SHIFTED && precision != LB_FP64) return LB_EINVAL;
+    lb_batch *b = new (std::nothrow) lb_batch();
+    if (!b) return LB_ENOMEM;
+    b->count = count;
+    b->precision = precision;
+    b->elem = precision == LB_FP64 ? 8 : 4;
+    b->stream = (cudaStream_t)stream;
+    cudaGetDevice(&b->device);
+    b->inst.resize(count);
+    b->off.resize(count);
+    b->node_off.resize(count + 1);
+    const int V = precision == LB_FP64 ? lbk::Vec<double>::V : lbk::Vec<float>::V;
+    int64_t off = 0, noff = 0;
+    for (int j = 0; j < count; ++j) {
+        lb_ctx &c = b->inst[j];
+        const int64_t n0 = N[2 * j], n1 = N[2 * j + 1];
+        if (n0 < 1 || n1 < 1 || n0 > 65536 || n1 > 65536 || !(nu[j] > 0) || !(dx[j] > 0) || !(dt[j] > 0) ||
+            !isfinite(nu[j]) || !isfinite(dx[j]) || !isfinite(dt[j])) {
+            free_batch(b);
+            return LB_EINVAL;
+        }
+        c.d = 2;
+        c.q = 9;
+        c.N[0] = n0;
+        c.N[1] = n1;
+        c.N[2] = 1;
+        c.nodes = n0 * n1;
+        c.precision = precision;
+        c.nu = nu[j];
+        c.dx = dx[j];
+        c.dt = dt[j];
+        c.c = dx[j] / dt[j];
+        c.eps = nu[j] * dt[j] / (dx[j] * dx[j]);
+        if (!lbk::derive_params(c, rs ? &rs[j] : nullptr)) {
+            free_batch(b);
+            return LB_EINVAL;
+        }
+        c.elem = b->elem;
+        lbk::Geom &g = c.geom;
+        g.N0 = (int)n0;
+        g.N1 = (int)n1;
+        g.N2 = 1;
+        const int segw = 32 * V;
+        g.pitch = (int)((n0 + segw - 1) / segw * segw);
+        g.rows = n1;
+        g.slab = (int64_t)g.pitch * g.rows;
+        g.seg_per_row = g.pitch / segw;
+        g.nseg = g.rows * g.seg_per_row;
+        c.stream = b->stream;
+        c.device = b->device;
+        b->off[j] = off;
+        b->node_off[j] = noff;
+        off += (int64_t)c.q * g.slab;
+        noff += c.nodes;
+    }
+    b->node_off[count] = noff;
+    b->total_elems = off;
+    b->total_nodes = noff;
+    cudaError_t e;
+    for (int k = 0; k < 2; ++k) {
+        if ((e = cudaMalloc(&b->buf[k], b->elem * (size_t)off)) != cudaSuccess ||
+            (e = cudaMemsetAsync(b->buf[k], 0, b->elem * (size_t)off, b->stream)) != cudaSuccess) {
+            free_batch(b);
+            return e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA;
+        }
+    }
+    e = precision == LB_FP64 ? upload_desc<double>(b) : upload_desc<float>(b);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_node_off, sizeof(int64_t) * (count + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_node_off, b->node_off.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(double) * 4 * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_flag, sizeof(int) * 2);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA;
+    }
+    for (int j = 0; j < count; ++j) {
+        b->inst[j].f[0] = (char *)b->buf[0] + b->elem * b->off[j];
+        b->inst[j].f[1] = (char *)b->buf[1] + b->elem * b->off[j];
+    }
+    // Default schedule: groups of at most 96 MB (A + B) so each stays in L2.
+    lb_status st = build_schedule(b, 96e6, 256, true);
+    if (st != LB_OK) {
+        free_batch(b);
+        return st;
+    }
+    *out = b;
+    return LB_OK;
+}
+
+lb_status lb_batch_destroy(lb_batch *b)
+{
+    if (!b) return LB_OK;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    return LB_OK;
+}
+
+lb_status lb_batch_set_theta_ref(lb_batch *b, const double *tr)
+{
+    if (!b || !tr) return LB_EINVAL;
+    for (int j = 0; j < b->count; ++j) {
+        if (!isfinite(tr[j])) return bfail(b, LB_EINVAL, "lb_batch_set_theta_ref: non-finite value");
+        b->inst[j].theta_ref = tr[j];
+    }
+    return LB_OK;
+}
+
+lb_status lb_batch_set_theta0(lb_batch *b, const double *theta0, const double *grad0)
+{
+    if (!b) return LB_EINVAL;
+    if (!theta0) return bfail(b, LB_EINVAL, "lb_batch_set_theta0: theta0 is NULL");
+    b->initialized = false;
+    cudaError_t e;
+    if (!grad0) {
+        if (!b->gradtmp && (e = cudaMalloc(&b->gradtmp, sizeof(double) * 2 * b->total_nodes)) != cudaSuccess)
+            return bcuda(b, e, "lb_batch_set_theta0: gradient buffer");
+    }
+    if ((e = cudaMemsetAsync(b->d_flag, 0, sizeof(int) * 2, b->stream)) != cudaSuccess)
+        return bcuda(b, e, "lb_batch_set_theta0");
+    b->cur = 0;
+    for (int j = 0; j < b->count; ++j) {
+        lb_ctx &c = b->inst[j];
+        c.cur = 0;
+        const double *th = theta0 + b->node_off[j];
+        const double *gr = grad0 ? grad0 + 2 * b->node_off[j] : b->gradtmp + 2 * b->node_off[j];
+        if (!grad0 && (e = lbk::launch_fd4_grad(&c, th, const_cast<double *>(gr))) != cudaSuccess)
+            return bcuda(b, e, "lb_batch_set_theta0: fd4");
+        if ((e = lbk::launch_init(&c, th, gr, b->d_flag)) != cudaSuccess)
+            return bcuda(b, e, "lb_batch_set_theta0: init");
+    }
+    int flag = 0;
+    if ((e = cudaMemcpyAsync(&flag, b->d_flag, sizeof(int), cudaMemcpyDeviceToHost, b->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+        return bcuda(b, e, "lb_batch_set_theta0");
+    if (flag) return bfail(b, LB_ENONPOS, "lb_batch_set_theta0: theta0 must be finite and > 0");
+    b->initialized = true;
+    return LB_OK;
+}
+
+lb_status lb_batch_step(lb_batch *b, int64_t n)
+{
+    if (!b) return LB_EINVAL;
+    if (n < 0) return bfail(b, LB_EINVAL, "lb_batch_step: n < 0");
+    if (!b->initialized) return bfail(b, LB_ESTATE, "lb_batch_step: call lb_batch_set_theta0 first");
+    cudaError_t e = run_steps(b, n);
+    if (e != cudaSuccess) return bcuda(b, e, "lb_batch_step");
+    return LB_OK;
+}
+
+lb_status lb_batch_macros(lb_batch *b, double *theta, double *u)
+{
+    if (!b) return LB_EINVAL;
+    if (!b->initialized) return bfail(b, LB_ESTATE, "lb_batch_macros: call lb_batch_set_theta0 first");
+    for (int j = 0; j < b->count; ++j) {
+        lb_ctx &c = b->inst[j];
+        c.cur = b->cur;
+        cudaError_t e = lbk::launch_macros(&c, c.f[b->cur], theta ? theta + b->node_off[j] : nullptr, nullptr,
+                                           u ? u + 2 * b->node_off[j] : nullptr, b->d_flag + 1);
+        if (e != cudaSuccess) return bcuda(b, e, "lb_batch_macros");
+    }
+    return LB_OK;
+}
+
+lb_status lb_batch_errors(lb_batch *b, const double *theta, const double *u, const double *eth, const double *eu,
+                          double *out)
+{
+    if (!b || !theta || !eth || !out) return LB_EINVAL;
+    if ((u == nullptr) != (eu == nullptr)) return bfail(b, LB_EINVAL, "lb_batch_errors: u and exact_u go together");
+    lbk::batch_errors_kernel<<<b->count, lbk::kRedThreads, 0, b->stream>>>(b->d_node_off, theta, u, eth, eu,
+                                                                           b->total_nodes, b->d_err);
+    cudaError_t e = cudaGetLastError();
+    int flag = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, b->d_err, sizeof(double) * 4 * b->count, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&flag, b->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "lb_batch_errors");
+    if (flag) return bfail(b, LB_ENONPOS, "lb_batch_macros saw theta <= 0");
+    return LB_OK;
+}
+
+lb_status lb_batch_autotune(lb_batch *b, int trial_steps, double *choice)
+{
+    if (!b || trial_steps < 2) return LB_EINVAL;
+    const double budgets[] = {0.0, 24e6, 48e6, 64e6, 96e6, 128e6, 1e18};
+    const int threads[] = {128, 256, 512};
+    double best = 1e300, best_b = b->budget;
+    int best_t = b->threads;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bfail(b, LB_ECUDA, "lb_batch_autotune: events");
+    lb_status st = LB_OK;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, LB_ECUDA, "lb_batch_autotune: sync");
+    for (double bud : budgets) {
+        for (int th : threads) {
+            if ((st = build_schedule(b, bud, th, true)) != LB_OK) break;
+            cudaError_t e = run_steps(b, trial_steps);  // warm-up: records the graphs, fills L2
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            if (e == cudaSuccess) e = run_steps(b, trial_steps);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                st = bcuda(b, e, "lb_batch_autotune");
+                break;
+            }
+            if (ms < best) {
+                best = ms;
+                best_b = bud;
+                best_t = th;
+            }
+        }
+        if (st != LB_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LB_OK) return st;
+    b->initialized = false;  // the trials overwrote the state
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, LB_ECUDA, "lb_batch_autotune: sync");
+    if ((st = build_schedule(b, best_b, best_t, true)) != LB_OK) return st;
+    if (choice) {
+        choice[0] = best_b;
+        choice[1] = best_t;
+        choice[2] = (double)b->groups.size();
+        choice[3] = 1e3 * best / trial_steps;
+    }
+    return LB_OK;
+}
+
+lb_status lb_batch_set_schedule(lb_batch *b, double budget, int threads, int use_graph)
+{
+    if (!b || !(threads == 128 || threads == 256 || threads == 512) || !isfinite(budget)) return LB_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);  // tables in use by queued launches
+    if (e != cudaSuccess) return bcuda(b, e, "lb_batch_set_schedule");
+    return build_schedule(b, budget, threads, use_graph != 0);
+}
+
+lb_status lb_batch_schedule(const lb_batch *b, double *info)
+{
+    if (!b || !info) return LB_EINVAL;
+    info[0] = b->budget;
+    info[1] = b->threads;
+    info[2] = (double)b->groups.size();
+    info[3] = (double)b->total_nodes;
+    return LB_OK;
+}
+
+const char *lb_batch_last_error(const lb_batch *b) { return b ? b->err.c_str() : "lb_batch: NULL handle"; }
+
+}  // extern "C"

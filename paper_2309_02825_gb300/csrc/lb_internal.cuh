@@ -122,6 +122,13 @@ struct lb_ctx {
 
 namespace lbk {
 
+// Host-side derivation shared by every entry point (single grid and batch):
+// relaxation set (Theorem 2, Eq. (Bur-Sol), or the caller's), weights
+// (Eq. (d1-3-weight)), sigma = c_s^2/c^2 and the collision constants.
+// Returns false if a rate leaves (0, 2) or a weight is not finite.
+bool derive_params(lb_ctx &c, const lb_relax *rs);
+template <typename T> Coll<T> make_coll(const lb_ctx &c);
+
 constexpr int kRedThreads = 256;
 constexpr int kRedSlots = 16;  // doubles per block partial (>= 3*(d+1)+1)
 

@@ -277,8 +277,9 @@ __global__ void __launch_bounds__(kRedThreads) fold_kernel(const double *__restr
 // ---------------------------------------------------------------------------
 // Host-side dispatch.
 // ---------------------------------------------------------------------------
-template <typename T> static Coll<T> make_coll(const lb_ctx *c)
+template <typename T> Coll<T> make_coll(const lb_ctx &cc)
 {
+    const lb_ctx *c = &cc;
     const double d = c->d;
     const double s2x = c->s2x, s22 = (c->d > 1) ? c->s22 : 1.0, wd = (c->d > 1) ? c->wd : 0.0;
     Coll<T> k;
@@ -290,13 +291,15 @@ template <typename T> static Coll<T> make_coll(const lb_ctx *c)
     k.wd = (T)wd;
     return k;
 }
+template Coll<double> make_coll<double>(const lb_ctx &);
+template Coll<float> make_coll<float>(const lb_ctx &);
 
 static int64_t sweep_blocks(const Geom &g) { return (g.nseg + kSweepThreads / 32 - 1) / (kSweepThreads / 32); }
 
 template <class L, typename T> static cudaError_t sweep_t(lb_ctx *c, const void *src, void *dst)
 {
     sweep_kernel<L, T, Coll<T>><<<(unsigned)sweep_blocks(c->geom), kSweepThreads, 0, c->stream>>>(
-        (const T *)src, (T *)dst, c->geom, make_coll<T>(c));
+        (const T *)src, (T *)dst, c->geom, make_coll<T>(*c));
     return cudaGetLastError();
 }
 

@@ -303,3 +303,130 @@ class Solver:
 
     def load_state(self, buf, step):
         lb_load_state(self.ctx, buf, step)
+
+
+# --------------------------------------------------------------------------
+# Batched 2D instances (include/lb_batch.h).
+# --------------------------------------------------------------------------
+
+_batch_sigs = {
+    "lb_batch_create": (["i", "p64", "pd", "pd", "pd", "relax", "i", "vp", "pvp"], "i"),
+    "lb_batch_destroy": (["vp"], "i"),
+    "lb_batch_set_theta_ref": (["vp", "pd"], "i"),
+    "lb_batch_set_theta0": (["vp", "vp", "vp"], "i"),
+    "lb_batch_step": (["vp", "i64"], "i"),
+    "lb_batch_macros": (["vp", "vp", "vp"], "i"),
+    "lb_batch_errors": (["vp", "vp", "vp", "vp", "vp", "pd"], "i"),
+    "lb_batch_autotune": (["vp", "i", "pd"], "i"),
+    "lb_batch_set_schedule": (["vp", "d", "i", "i"], "i"),
+    "lb_batch_schedule": (["vp", "pd"], "i"),
+    "lb_batch_last_error": (["vp"], "s"),
+}
+
+
+def _load_batch():
+    lib = load()
+    if getattr(lib, "_batch_ready", False):
+        return lib
+    m = {"i": ctypes.c_int, "i64": ctypes.c_int64, "d": ctypes.c_double, "vp": ctypes.c_void_p,
+         "p64": ctypes.POINTER(ctypes.c_int64), "pd": ctypes.POINTER(ctypes.c_double),
+         "relax": ctypes.POINTER(lb_relax), "pvp": ctypes.POINTER(ctypes.c_void_p), "s": ctypes.c_char_p}
+    for name, (args, res) in _batch_sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = [m[a] for a in args]
+        fn.restype = m[res]
+    lib._batch_ready = True
+    return lib
+
+
+class Batch:
+    """Many independent 2D periodic instances (D2Q9), advanced together.
+
+    ``sizes`` is a list of (N0, N1); ``nu``, ``dx``, ``dt`` are per-instance
+    sequences; relaxation sets follow Theorem 2 per instance.  Fields are
+    concatenated in instance order (see include/lb_batch.h).
+    """
+
+    def __init__(self, sizes, nu, dx, dt, precision="fp32s", theta_ref=None, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the batched solver needs a CUDA GPU; no CPU fallback exists")
+        self._lib = _load_batch()
+        self.count = len(sizes)
+        self.sizes = [tuple(int(n) for n in s) for s in sizes]
+        self.nodes = [s[0] * s[1] for s in self.sizes]
+        self.node_off = [0]
+        for n in self.nodes:
+            self.node_off.append(self.node_off[-1] + n)
+        flat = (ctypes.c_int64 * (2 * self.count))(*[v for s in self.sizes for v in s])
+        arr = lambda v: (ctypes.c_double * self.count)(*[float(x) for x in v])
+        self.precision = {"fp64": LB_FP64, "fp32s": LB_FP32_SHIFTED}[precision]
+        out = ctypes.c_void_p()
+        st = self._lib.lb_batch_create(self.count, flat, arr(nu), arr(dx), arr(dt), None, self.precision,
+                                       _stream_handle(stream), ctypes.byref(out))
+        if st != LB_OK:
+            raise LBError(st, "lb_batch_create")
+        self.h = out
+        if theta_ref is not None:
+            self._call("lb_batch_set_theta_ref", arr(theta_ref))
+
+    def _call(self, name, *args):
+        st = getattr(self._lib, name)(self.h, *args)
+        if st != LB_OK:
+            msg = self._lib.lb_batch_last_error(self.h)
+            raise LBError(st, "%s: %s" % (name, msg.decode() if msg else ""))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lb_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def total_nodes(self):
+        return self.node_off[-1]
+
+    def set_theta0(self, theta0, grad0=None):
+        self._call("lb_batch_set_theta0", _ptr(theta0, "theta0", numel=self.total_nodes),
+                   _ptr(grad0, "grad0", numel=2 * self.total_nodes))
+
+    def step(self, n):
+        self._call("lb_batch_step", int(n))
+
+    def macros(self, theta=None, u=None):
+        theta = theta if theta is not None else torch.empty(self.total_nodes, dtype=torch.float64, device="cuda")
+        u = u if u is not None else torch.empty(2 * self.total_nodes, dtype=torch.float64, device="cuda")
+        self._call("lb_batch_macros", _ptr(theta, "theta"), _ptr(u, "u"))
+        return theta, u
+
+    def errors(self, theta, u, exact_theta, exact_u):
+        buf = (ctypes.c_double * (4 * self.count))()
+        self._call("lb_batch_errors", _ptr(theta, "theta"), _ptr(u, "u"), _ptr(exact_theta, "exact_theta"),
+                   _ptr(exact_u, "exact_u"), buf)
+        import numpy as np
+        return np.array(list(buf)).reshape(self.count, 4)
+
+    def autotune(self, trial_steps=10):
+        buf = (ctypes.c_double * 4)()
+        self._call("lb_batch_autotune", int(trial_steps), buf)
+        return {"budget_bytes": buf[0], "threads": int(buf[1]), "groups": int(buf[2]), "us_per_step": buf[3]}
+
+    def set_schedule(self, budget_bytes, threads=256, use_graph=True):
+        self._call("lb_batch_set_schedule", float(budget_bytes), int(threads), int(bool(use_graph)))
+
+    def schedule(self):
+        buf = (ctypes.c_double * 4)()
+        self._call("lb_batch_schedule", buf)
+        return {"budget_bytes": buf[0], "threads": int(buf[1]), "groups": int(buf[2]), "nodes": int(buf[3])}
+
+    def split(self, flat, comps=1):
+        """Per-instance views (shape (comps, N1, N0) or (N1, N0)) of a concatenated field."""
+        out = []
+        for j, (n0, n1) in enumerate(self.sizes):
+            a = flat[comps * self.node_off[j]: comps * self.node_off[j + 1]]
+            out.append(a.reshape((comps, n1, n0)) if comps > 1 else a.reshape((n1, n0)))
+        return out

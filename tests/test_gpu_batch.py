@@ -1,0 +1,97 @@
+"""Batched 2D instances: bit-identical to the single-instance solver under
+every schedule (same kernel arithmetic), and within the FP64 / FP32 bounds
+of the oracle per instance."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2309_02825_gb300 import lb
+from paper_2309_02825_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(70, 45), (5, 7), (33, 20), (130, 3), (64, 64), (1, 9), (200, 17)]
+NUS = [0.02, 0.005, 0.08, 0.03, 0.011, 0.05, 0.1]
+
+
+def _setup(seed=7):
+    probs, dxs, dts, th0, g0 = [], [], [], [], []
+    for j, ((n0, n1), nu) in enumerate(zip(SIZES, NUS)):
+        p = W.FourierProblem.random(2, nu, 6, 3, 0.05, 1.5, seed + j)
+        dx = 1.0 / max(n0, n1)
+        dt = 4.0 * dx * dx
+        probs.append(p)
+        dxs.append(dx)
+        dts.append(dt)
+        th0.append(p.theta((n0, n1), dx).ravel())
+        g0.append(np.ascontiguousarray(p.grad((n0, n1), dx)).ravel())
+    return probs, dxs, dts, np.concatenate(th0), np.concatenate(g0)
+
+
+def _single(j, prob, dx, dt, n, precision, theta_ref):
+    N = SIZES[j]
+    s = lb.Solver(2, N, prob.nu, dx, dt, precision=precision, theta_ref=theta_ref)
+    s.set_theta0(torch.from_numpy(prob.theta(N, dx)).cuda(),
+                 torch.from_numpy(np.ascontiguousarray(prob.grad(N, dx))).cuda())
+    s.step(n)
+    th, _, u = s.macros()
+    return th, u
+
+
+@pytest.mark.parametrize("precision", ["fp32s", "fp64"])
+@pytest.mark.parametrize("sched", [(96e6, 256, True), (0.0, 128, False), (40e3, 512, True), (1e18, 256, True)])
+def test_batch_equals_single_instance_bitwise(precision, sched):
+    probs, dxs, dts, th0, g0 = _setup()
+    n = 37  # one recorded 32-step graph plus 5 direct launches, odd parity
+    b = lb.Batch(SIZES, NUS, dxs, dts, precision=precision, theta_ref=[1.5] * len(SIZES))
+    b.set_schedule(*sched)
+    b.set_theta0(torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda())
+    b.step(n)
+    th, u = b.macros()
+    ths, us = b.split(th), b.split(u, 2)
+    for j in range(len(SIZES)):
+        t1, u1 = _single(j, probs[j], dxs[j], dts[j], n, precision, 1.5)
+        assert torch.equal(ths[j], t1), j
+        assert torch.equal(us[j], u1), j
+
+
+def test_batch_fp64_matches_oracle():
+    probs, dxs, dts, th0, g0 = _setup(11)
+    n = 20
+    b = lb.Batch(SIZES, NUS, dxs, dts, precision="fp64")
+    b.set_theta0(torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda())
+    b.step(n)
+    th, u = b.macros()
+    ths, us = b.split(th), b.split(u, 2)
+    for j, N in enumerate(SIZES):
+        m = O.Model(2, N, NUS[j], dxs[j], dts[j])
+        p = probs[j]
+        tho, _, uo = m.recover(m.run(m.initialize(p.theta(N, dxs[j]), p.grad(N, dxs[j])), n))
+        assert np.max(np.abs(ths[j].cpu().numpy() - tho)) <= 1e-12 * np.max(np.abs(tho))
+        # u: 1e-12 of max|u| plus the rounding floor of J = sum e f (see test_gpu_parity)
+        floor = 8 * 9 * 2.0 ** -53 * np.max(tho) * np.sqrt(n + 1) * (2 - m.params["s1"]) * m.params["c"] / np.min(tho)
+        assert np.max(np.abs(us[j].cpu().numpy() - uo)) <= 1e-12 * np.max(np.abs(uo)) + floor
+
+
+def test_batch_autotune_and_errors():
+    probs, dxs, dts, th0, g0 = _setup(3)
+    b = lb.Batch(SIZES, NUS, dxs, dts, precision="fp32s", theta_ref=[1.5] * len(SIZES))
+    choice = b.autotune(4)
+    assert choice["threads"] in (128, 256, 512) and choice["groups"] >= 1 and choice["us_per_step"] > 0
+    b.set_theta0(torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda())
+    n = 40
+    b.step(n)
+    th, u = b.macros()
+    ex_t = np.concatenate([p.theta(N, dxs[j], n * dts[j]).ravel() for j, (p, N) in enumerate(zip(probs, SIZES))])
+    ex_u = np.concatenate([np.ascontiguousarray(p.u(N, dxs[j], n * dts[j])).ravel()
+                           for j, (p, N) in enumerate(zip(probs, SIZES))])
+    err = b.errors(th, u, torch.from_numpy(ex_t).cuda(), torch.from_numpy(ex_u).cuda())
+    tht, ut = th.cpu().numpy(), u.cpu().numpy()
+    for j, N in enumerate(SIZES):
+        a, z = b.node_off[j], b.node_off[j + 1]
+        et = tht[a:z] - ex_t[a:z]
+        eu = (ut[2 * a:2 * z] - ex_u[2 * a:2 * z]).reshape(2, -1)
+        assert err[j, 0] == pytest.approx(np.sqrt(np.mean(et ** 2)), rel=1e-12)
+        assert err[j, 1] == pytest.approx(np.sqrt(np.mean(np.sum(eu ** 2, axis=0))), rel=1e-12)
+        assert err[j, 2] == pytest.approx(np.max(np.abs(et)), rel=1e-15)
