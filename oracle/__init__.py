@@ -85,6 +85,10 @@ def _load():
         lib.orc_recover.argtypes = [vp, dp, dp, dp, dp]
         lib.orc_total.argtypes = [vp, dp]
         lib.orc_total.restype = ctypes.c_double
+        lib.orc_adjoint.argtypes = [vp, dp, dp, ctypes.c_long, dp, dp]
+        lib.orc_adjoint.restype = ctypes.c_double
+        lib.orc_loss.argtypes = [vp, dp, dp, ctypes.c_long]
+        lib.orc_loss.restype = ctypes.c_double
         _lib = lib
         return lib
 
@@ -233,6 +237,24 @@ class Model:
 
     def total(self, f) -> float:
         return float(self._lib.orc_total(self._h, _dp(_f64(f))))
+
+    def loss(self, theta0, utarget, T) -> float:
+        """L = 1/2 sum (u(T) - utarget)^2 with f_0 from theta0 and its FD4 gradient."""
+        th = _f64(theta0).reshape(self.shape)
+        ut = _f64(utarget).reshape((self.d,) + self.shape)
+        return float(self._lib.orc_loss(self._h, _dp(th), _dp(ut), int(T)))
+
+    def adjoint(self, theta0, utarget, T):
+        """(L, dL/dtheta0, dL/dnu) by the discrete adjoint (paper relaxation set)."""
+        th = _f64(theta0).reshape(self.shape)
+        ut = _f64(utarget).reshape((self.d,) + self.shape)
+        g = np.zeros(self.shape)
+        de = ctypes.c_double()
+        L = self._lib.orc_adjoint(self._h, _dp(th), _dp(ut), int(T), _dp(g), ctypes.byref(de))
+        if not np.isfinite(L):
+            raise MemoryError("oracle adjoint")
+        p = self.params
+        return float(L), g, de.value * p["dt"] / (p["dx"] * p["dx"])
 
 
 # --------------------------------------------------------------------------

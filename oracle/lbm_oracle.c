@@ -448,3 +448,217 @@ double orc_total(const orc_model *m, const double *f)
     for (long k = 0; k < total; ++k) s += f[k];
     return s;
 }
+
+/* ------------------------------------------------------------------ */
+/* Discrete adjoint of the whole forward map (reference gradient).     */
+/*                                                                     */
+/* Forward: f_0 = Init(theta0, G theta0) (first two terms of Eq.       */
+/* (f-feq-o5), G the fourth-order central difference), T steps of Eq.  */
+/* (distribution-f), u from Eq. (ui-compute) at t = T dt, and          */
+/* L = 1/2 sum_x sum_a (u_a - utarget_a)^2.  The adjoint runs the      */
+/* same operations transposed, in reverse order, with every forward    */
+/* state kept in memory (small grids only).  eps = nu dt / dx^2 enters */
+/* through the relaxation set of Eq. (Bur-Sol); its derivatives are    */
+/* those of the closed forms of Theorem 2.                             */
+/* ------------------------------------------------------------------ */
+
+/* d/d eps of the Eq. (Bur-Sol) quantities: s1, s2x, s22, w1, wd. */
+static void paper_set_deriv(int d, double eps, double *ds1, double *ds2x, double *ds22, double *dw1,
+                            double *dwd)
+{
+    double a = 6.0 * eps + 1.0;
+    *ds1 = -12.0 / (a * a);
+    *ds2x = 24.0 / (a * a) - 24.0 * eps * 12.0 / (a * a * a);
+    if (d == 1) {
+        *ds22 = 0.0;
+        *dw1 = 0.0;
+        *dwd = 0.0;
+    } else {
+        double b = 6.0 * eps + 3.0;
+        *ds22 = -24.0 / (b * b);
+        *dw1 = -(d - 1) / 3.0;
+        *dwd = 1.0 / 6.0;
+    }
+}
+
+/* L and its gradients with respect to theta0 (nodes values) and eps.
+ * Requires a model built with the paper's relaxation set.  Returns L, or
+ * NAN on allocation failure. */
+double orc_adjoint(const orc_model *m, const double *theta0, const double *utarget, long T,
+                   double *dL_dtheta0, double *dL_deps)
+{
+    int q = m->q, d = m->d;
+    long nodes = m->nodes;
+    size_t fs = (size_t)q * (size_t)nodes;
+    double *F = (double *)malloc(sizeof(double) * fs * (size_t)(T + 1));
+    double *grad = (double *)malloc(sizeof(double) * d * nodes);
+    double *phi = (double *)malloc(sizeof(double) * fs);
+    double *phin = (double *)malloc(sizeof(double) * fs);
+    double *h = (double *)malloc(sizeof(double) * d * nodes);
+    if (!F || !grad || !phi || !phin || !h) {
+        free(F); free(grad); free(phi); free(phin); free(h);
+        return NAN;
+    }
+    /* forward, keeping every state */
+    orc_fd4_gradient(m, theta0, grad);
+    orc_initialize(m, theta0, grad, F);
+    for (long n = 0; n < T; ++n) orc_step(m, F + fs * n, F + fs * (n + 1));
+
+    /* derivatives of the parameters with respect to eps */
+    double ds1, ds2x, ds22, dw1, dwd;
+    paper_set_deriv(d, m->eps, &ds1, &ds2x, &ds22, &dw1, &dwd);
+    double dw[ORC_MAXQ], dS[ORC_MAXQ];
+    dw[0] = -2.0 * d * dw1 - 2.0 * d * (d - 1) * dwd;
+    for (int i = 1; i <= 2 * d; ++i) dw[i] = dw1;
+    for (int i = 2 * d + 1; i < q; ++i) dw[i] = dwd;
+    for (int r = 0; r < q; ++r) {
+        switch (m->kind[r]) {
+        case 1: dS[r] = ds1; break;
+        case 2: dS[r] = ds2x; break;
+        case 3: dS[r] = ds22; break;
+        default: dS[r] = 0.0; break;
+        }
+    }
+    /* K = I - C (I - w 1^T) with C = M^-1 S M; dK = -C'(I - w 1^T) + C w' 1^T */
+    double K[ORC_MAXQ * ORC_MAXQ], dK[ORC_MAXQ * ORC_MAXQ], dC[ORC_MAXQ * ORC_MAXQ];
+    double dSM[ORC_MAXQ * ORC_MAXQ], dCinv[ORC_MAXQ * ORC_MAXQ], dSinvM[ORC_MAXQ * ORC_MAXQ];
+    for (int r = 0; r < q; ++r)
+        for (int i = 0; i < q; ++i) {
+            dSM[r * q + i] = dS[r] * m->M[r * q + i];
+            dSinvM[r * q + i] = -dS[r] / (m->sdiag[r] * m->sdiag[r]) * m->M[r * q + i];
+        }
+    matmul(q, m->Minv, dSM, dC);
+    matmul(q, m->Minv, dSinvM, dCinv);
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) {
+            double k = (i == j) ? 1.0 : 0.0, dk = 0.0;
+            for (int l = 0; l < q; ++l) {
+                double proj = ((l == j) ? 1.0 : 0.0) - m->w[l];
+                k -= m->Ccol[i * q + l] * proj;
+                dk -= dC[i * q + l] * proj;
+                dk += m->Ccol[i * q + l] * dw[l];
+            }
+            K[i * q + j] = k;
+            dK[i * q + j] = dk;
+        }
+
+    /* recovery at T and the seed phi_T = dL/df_T */
+    double L = 0.0, deps = 0.0;
+    const double *fT = F + fs * T;
+    for (long x = 0; x < nodes; ++x) {
+        double th = 0.0;
+        for (int k = 0; k < q; ++k) th += fT[k * nodes + x];
+        for (int k = 0; k < q; ++k) phi[k * nodes + x] = 0.0;
+        for (int a = 0; a < d; ++a) {
+            double j = 0.0, sew = 0.0, dsew = 0.0;
+            for (int k = 0; k < q; ++k) {
+                j += m->c * m->e[k * d + a] * (fT[k * nodes + x] - m->w[k] * th);
+                sew += m->c * m->e[k * d + a] * m->w[k];
+                dsew += m->c * m->e[k * d + a] * dw[k];
+            }
+            double u = (2.0 - m->s1) * j / th;
+            double r = u - utarget[a * nodes + x];
+            L += 0.5 * r * r;
+            for (int k = 0; k < q; ++k) {
+                double djdf = m->c * m->e[k * d + a] - sew;
+                phi[k * nodes + x] += r * (2.0 - m->s1) * (djdf * th - j) / (th * th);
+            }
+            /* explicit eps dependence of u: through s1 and through w in f^ne */
+            deps += r * (-ds1 * j / th + (2.0 - m->s1) * (-dsew * th) / th);
+        }
+    }
+
+    /* reverse steps: f_{n+1}(x + e_i)_i = (K f_n(x))_i */
+    long xc[ORC_MAXD], yc[ORC_MAXD];
+    double mu[ORC_MAXQ];
+    for (long n = T - 1; n >= 0; --n) {
+        const double *fn = F + fs * n;
+        for (long x = 0; x < nodes; ++x) {
+            node_coords(m, x, xc);
+            for (int i = 0; i < q; ++i) {
+                for (int a = 0; a < d; ++a) yc[a] = xc[a] + m->e[i * d + a];
+                mu[i] = phi[i * nodes + coords_node(m, yc)];
+            }
+            for (int j = 0; j < q; ++j) {
+                double s = 0.0;
+                for (int i = 0; i < q; ++i) s += K[i * q + j] * mu[i];
+                phin[j * nodes + x] = s;
+            }
+            for (int i = 0; i < q; ++i) {
+                double s = 0.0;
+                for (int j = 0; j < q; ++j) s += dK[i * q + j] * fn[j * nodes + x];
+                deps += mu[i] * s;
+            }
+        }
+        double *t = phi;
+        phi = phin;
+        phin = t;
+    }
+
+    /* initialisation: f_0 = w theta0 - dt Cinv (w o (c e . g)), g = G theta0 */
+    for (long x = 0; x < nodes; ++x) {
+        double s = 0.0;
+        for (int i = 0; i < q; ++i) s += m->w[i] * phi[i * nodes + x];
+        dL_dtheta0[x] = s;
+        for (int a = 0; a < d; ++a) {
+            double acc = 0.0;
+            for (int i = 0; i < q; ++i) {
+                double cw = 0.0;
+                for (int k = 0; k < q; ++k) cw += m->Cinv[i * q + k] * m->w[k] * m->c * m->e[k * d + a];
+                acc += phi[i * nodes + x] * cw;
+            }
+            h[a * nodes + x] = -m->dt * acc;
+        }
+        /* eps dependence of the initialisation */
+        for (int i = 0; i < q; ++i) {
+            double v = dw[i] * theta0[x];
+            for (int k = 0; k < q; ++k) {
+                double cg = 0.0;
+                for (int a = 0; a < d; ++a) cg += m->c * m->e[k * d + a] * grad[a * nodes + x];
+                v -= m->dt * (dCinv[i * q + k] * m->w[k] + m->Cinv[i * q + k] * dw[k]) * cg;
+            }
+            deps += phi[i * nodes + x] * v;
+        }
+    }
+    /* transpose of the fourth-order difference: (G^T h)(x) = sum_k cof_k h(x - off_k e_a) / (12 dx) */
+    static const int off[4] = {2, 1, -1, -2};
+    static const double cof[4] = {-1.0, 8.0, -8.0, 1.0};
+    for (long x = 0; x < nodes; ++x) {
+        node_coords(m, x, xc);
+        double s = 0.0;
+        for (int a = 0; a < d; ++a)
+            for (int k = 0; k < 4; ++k) {
+                memcpy(yc, xc, sizeof(long) * d);
+                yc[a] -= off[k];
+                s += cof[k] * h[a * nodes + coords_node(m, yc)];
+            }
+        dL_dtheta0[x] += s / (12.0 * m->dx);
+    }
+    *dL_deps = deps;
+    free(F); free(grad); free(phi); free(phin); free(h);
+    return L;
+}
+
+/* L only (the same forward as orc_adjoint), for finite-difference checks. */
+double orc_loss(const orc_model *m, const double *theta0, const double *utarget, long T)
+{
+    size_t fs = (size_t)m->q * (size_t)m->nodes;
+    double *f = (double *)malloc(sizeof(double) * fs);
+    double *grad = (double *)malloc(sizeof(double) * m->d * m->nodes);
+    double *u = (double *)malloc(sizeof(double) * m->d * m->nodes);
+    if (!f || !grad || !u) {
+        free(f); free(grad); free(u);
+        return NAN;
+    }
+    orc_fd4_gradient(m, theta0, grad);
+    orc_initialize(m, theta0, grad, f);
+    orc_run(m, f, T);
+    orc_recover(m, f, NULL, NULL, u);
+    double L = 0.0;
+    for (long k = 0; k < (long)m->d * m->nodes; ++k) {
+        double r = u[k] - utarget[k];
+        L += 0.5 * r * r;
+    }
+    free(f); free(grad); free(u);
+    return L;
+}
