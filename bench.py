@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-variant", action="store_true", help="skip the other precisions' sub-results")
     p.add_argument("--no-batched", action="store_true", help="skip the batched 512-instance measurement")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the 512^2 adjoint measurement")
     return p.parse_args()
 
 
@@ -370,6 +371,91 @@ def run_batched(local):
     }
 
 
+def run_adjoint(local, precision="fp64"):
+    """Adjoint cost at 512^2, T = 2000, sqrt(T) checkpoints: forward with
+    checkpoints, reverse pass with segment recompute, per-step cost against a
+    plain forward sweep, and central-difference checks of dL/dtheta0 along two
+    random directions and of dL/dnu."""
+    import torch
+    from paper_2309_02825_gb300 import lb
+
+    torch.cuda.set_device(local)
+    case = W.adjoint_2d(512, 2000)
+    N, d, T = case.N, case.d, case.nsteps
+    th0 = torch.from_numpy(case.problem.theta(N, case.dx)).cuda()
+    ut = torch.from_numpy(np.ascontiguousarray(case.extra["target"].u(N, case.dx, T * case.dt))).cuda()
+    stream = torch.cuda.Stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+
+    def grad(nu, th, timed=False):
+        s = lb.Solver(d, N, nu, case.dx, case.dt, precision=precision, stream=stream)
+        a = lb.Adjoint(s, T, checkpoint=0, want_nu=True)
+        with torch.cuda.stream(stream):
+            if timed:
+                ev[0].record(stream)
+            u = a.forward(th)
+            if timed:
+                ev[1].record(stream)
+            r = u - ut
+            a.seed(r)
+            a.step(T)
+            g, dnu = a.result()
+            if timed:
+                ev[2].record(stream)
+            L = 0.5 * float((r * r).sum())
+        info = a.info()
+        a.close()
+        s.close()
+        return L, g, dnu, info
+
+    def loss(nu, th):
+        s = lb.Solver(d, N, nu, case.dx, case.dt, precision=precision, stream=stream)
+        a = lb.Adjoint(s, T, want_nu=False)
+        with torch.cuda.stream(stream):
+            u = a.forward(th)
+            r = u - ut
+            L = 0.5 * float((r * r).sum())
+        a.close()
+        s.close()
+        return L
+
+    grad(case.nu, th0)  # warm-up
+    L, g, dnu, info = grad(case.nu, th0, timed=True)
+    torch.cuda.synchronize()
+    t_fwd = ev[0].elapsed_time(ev[1]) / 1e3
+    t_bwd = ev[1].elapsed_time(ev[2]) / 1e3
+    # plain forward sweep time at this size
+    s = lb.Solver(d, N, case.nu, case.dx, case.dt, precision=precision, stream=stream)
+    with torch.cuda.stream(stream):
+        s.set_theta0(th0)
+        s.step(50)
+        ev[3].record(stream)
+        s.step(T)
+        ev[4].record(stream)
+    torch.cuda.synchronize()
+    t_sweep = ev[3].elapsed_time(ev[4]) / 1e3 / T
+    s.close()
+    rng = np.random.default_rng(2314)
+    checks = []
+    for _ in range(2):
+        v = torch.from_numpy(rng.normal(size=tuple(th0.shape))).cuda()
+        h = 1e-5
+        fd = (loss(case.nu, th0 + h * v) - loss(case.nu, th0 - h * v)) / (2 * h)
+        checks.append(abs(float((g * v).sum()) / fd - 1.0))
+    hn = 1e-6 * case.nu
+    fd_nu = (loss(case.nu + hn, th0) - loss(case.nu - hn, th0)) / (2 * hn)
+    return {
+        "workload": "2D D2Q9 512^2, nu=0.02, eps=0.2048, T=2000, L=0.5||u(T)-u_target||^2, %s, checkpoint every %d "
+                    "steps (%d checkpoints)" % (precision, info["checkpoint"], info["checkpoints"]),
+        "forward_with_checkpoints_s": t_fwd, "reverse_s": t_bwd, "plain_sweep_us": t_sweep * 1e6,
+        "reverse_step_us": t_bwd / T * 1e6,
+        "adjoint_step_cost_vs_forward_step": t_bwd / T / t_sweep,
+        "gradient_total_cost_vs_forward": (t_fwd + t_bwd) / (T * t_sweep),
+        "loss": L, "dL_dnu": dnu, "fd_rel_err_theta0_dirs": checks, "fd_rel_err_nu": abs(dnu / fd_nu - 1.0),
+        "workspace_bytes": info["bytes"],
+    }
+
+
 # ---------------------------------------------------------------------------
 # The oracle (CPU baseline / reference arm).
 # ---------------------------------------------------------------------------
@@ -446,6 +532,9 @@ def main():
     batched = None
     if not args.no_batched:
         batched = run_batched(local)
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = run_adjoint(local)
     base = None
     if rank == 0 and not args.no_cpu_baseline:
         base = cpu_baseline(args)
@@ -476,6 +565,8 @@ def main():
             line["variants"] = variants
         if batched:
             line["batched"] = batched
+        if adjoint:
+            line["adjoint"] = adjoint
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

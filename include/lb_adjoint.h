@@ -1,0 +1,76 @@
+/*
+ * lb_adjoint.h - discrete adjoint of the MRT-LB forward map.
+ *
+ * Forward map of a context (lb.h): theta0 -> f_0 by Sec. IV's
+ * initialisation (first two terms of Eq. (f-feq-o5)) with grad theta0 taken
+ * as the fourth-order central difference of theta0 (so the map depends on
+ * theta0 alone), T steps of Eq. (distribution-f), and u(T) by
+ * Eq. (ui-compute).  The paper has no adjoint; this computes exact
+ * gradients of any loss L(u(T)) given dL/du:
+ *   dL/dtheta0 (one value per node) and dL/dnu (through eps = nu dt/dx^2 and
+ *   the relaxation set of Theorem 2, Eq. (Bur-Sol); dx and dt fixed).
+ * Reverse step: phi_n(x) = K^T [phi_{n+1}(x + e_i)_i]_i (reversed streaming,
+ * transposed collision, FP64), plus the eps-derivative term
+ * lambda_{n+1} . (dK/deps) f_n(x), which needs the forward states f_n: they
+ * are kept as checkpoints every C steps and recomputed one segment at a
+ * time (C = ceil(sqrt(T)) stores about 2 sqrt(T) states).
+ * All calls are stream-ordered on the context's stream.
+ */
+#ifndef LB_ADJOINT_H
+#define LB_ADJOINT_H
+
+#include <stdint.h>
+
+#include "lb.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_adj lb_adj;
+
+/*
+ * Adjoint workspace for `ctx` (any precision; d = 1, 2, 3).
+ *   T        forward steps (>= 1).
+ *   C        checkpoint interval, 1 <= C <= T, or 0 for ceil(sqrt(T)).
+ *   want_nu  nonzero to also compute dL/dnu (needs the paper's relaxation
+ *            set; keeps checkpoints and recomputes segments); zero computes
+ *            dL/dtheta0 only and keeps no forward states.
+ * Allocates ceil(T/C) + C state copies (want_nu) and two FP64 adjoint
+ * fields.  The context must outlive the workspace.
+ * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA.
+ */
+lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_adj **out);
+lb_status lb_adjoint_destroy(lb_adj *a);
+
+/*
+ * Forward pass: lb_set_theta0(ctx, theta0, NULL), T steps with checkpoints,
+ * then the recovery at T into u (device, d*nodes, may be NULL) and theta
+ * (device, nodes, may be NULL).  Errors as lb_set_theta0 / lb_step.
+ */
+lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, double *u);
+
+/*
+ * Start the reverse pass from dL/du at T (device, d*nodes): seeds
+ * phi_T = dL/df_T through Eq. (ui-compute).  Requires a completed forward.
+ */
+lb_status lb_adjoint_seed(lb_adj *a, const double *dL_du);
+
+/* Run `nsteps` reverse steps (the remaining count is T minus those done). */
+lb_status lb_adjoint_step(lb_adj *a, int64_t nsteps);
+
+/*
+ * After T reverse steps: dL/dtheta0 (device, nodes) and, if requested at
+ * creation, dL/dnu (host, 1 value; NULL to skip).  Synchronises the stream.
+ * Errors: LB_ESTATE if the reverse pass is incomplete.
+ */
+lb_status lb_adjoint_result(lb_adj *a, double *dL_dtheta0, double *dL_dnu);
+
+/* Workspace facts: {T, C, checkpoints, reverse steps done, bytes held}. */
+lb_status lb_adjoint_info(const lb_adj *a, double *info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_ADJOINT_H */

@@ -1,0 +1,660 @@
+// Discrete adjoint of the MRT-LB forward map (include/lb_adjoint.h).
+//
+// Notation: f_n(x) is the pre-collision distribution at step n, stored in
+// P form (P_{n+1}(x) = K f_n(x), f_n(x)_i = P_n(x - e_i)_i); phi_n(x) =
+// dL/df_n(x) is held aligned at x in FP64.  Then
+//   phi_n(x) = K^T lambda_{n+1}(x),  lambda_{n+1}(x)_i = phi_{n+1}(x + e_i)_i,
+//   dL/deps += lambda_{n+1}(x) . (dK/deps) f_n(x).
+// K^T is written in moment form by transposing the closed-form collision:
+// with Lt = c0 l0 + cA sum_axis l + wd sum_diag l, Laa = k2 (l_{+a} + l_{-a}
+// - 2 l0), Ja = k1 (l_{+a} - l_{-a}), Lab = k3 sum_{diag(a,b)} sa sb l,
+//   (K^T l)_j = Lt + sum_a e_ja^2 Laa + sum_a e_ja Ja + sum_{a<b} e_ja e_jb Lab.
+// (dK/deps) f is the forward collision formula evaluated with the
+// eps-derivatives of its constants (it is linear in them).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lb_adjoint.h"
+#include "lb_device.cuh"
+
+namespace lbk {
+
+constexpr int kAdjQ = 19;
+
+struct AdjK {
+    Coll<double> k;   // collision constants
+    Coll<double> kd;  // their eps-derivatives
+    double scale;     // stored value -> f: f_i = v * scale + shift[i]
+    double shift[kAdjQ];
+    double ucoef, ducoef;                      // (2 - s1) c and d/deps
+    double w[kAdjQ], dw[kAdjQ];                // weights and d/deps
+    double iax, idg, diax, didg;               // initialisation operator and d/deps
+    double inv12dx;
+};
+
+template <typename T> __device__ __forceinline__ double to_f(T v, double scale) { return (double)v * scale; }
+
+// Reverse pull: out[k] = phi(x + e_i) for the V nodes of this lane.
+template <class L>
+__device__ __forceinline__ void gather_rev(const double *__restrict__ src, const Geom &g, int64_t row, int x0,
+                                           int lane, double (&f)[L::Q][2])
+{
+    const int y = (int)(row % g.N1);
+    const int z = (int)(row / g.N1);
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
+        const int ys = (ey == 0) ? y : wrapi(y + ey, g.N1);
+        const int zs = (ez == 0) ? z : wrapi(z + ez, g.N2);
+        const double *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
+        pull_row<double, -ex>(rp, x0, lane, g.N0, f[i]);
+    });
+}
+
+// In-place K^T on one node's q adjoint values.
+template <class L> __device__ __forceinline__ void apply_KT(double *l, const Coll<double> &k)
+{
+    double sax = 0.0, sdg = 0.0;
+    double Laa[3] = {0, 0, 0}, Ja[3] = {0, 0, 0}, Lab[3] = {0, 0, 0};  // pairs xy, xz, yz
+    static_for<1, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
+        constexpr int nz = (ex != 0) + (ey != 0) + (ez != 0);
+        if constexpr (nz == 1) {
+            constexpr int a = (ex != 0) ? 0 : ((ey != 0) ? 1 : 2);
+            constexpr int s = (ex != 0) ? ex : ((ey != 0) ? ey : ez);
+            sax += l[i];
+            Laa[a] += l[i];
+            Ja[a] += s * l[i];
+        } else {
+            constexpr int p = (ez == 0) ? 0 : ((ey == 0) ? 1 : 2);
+            constexpr int ss = ex * ey + ex * ez + ey * ez;  // sa*sb of the nonzero pair
+            sdg += l[i];
+            Lab[p] += ss * l[i];
+        }
+    });
+    const double Lt = fma(k.c0, l[0], fma(k.cA, sax, k.wd * sdg));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        Laa[a] = k.k2 * (Laa[a] - 2.0 * l[0]);
+        Ja[a] = k.k1 * Ja[a];
+        Lab[a] = k.k3 * Lab[a];
+    }
+    l[0] = Lt;
+    static_for<1, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
+        double v = Lt;
+        if constexpr (ex != 0) v += Laa[0] + ex * Ja[0];
+        if constexpr (ey != 0) v += Laa[1] + ey * Ja[1];
+        if constexpr (ez != 0) v += Laa[2] + ez * Ja[2];
+        if constexpr (ex != 0 && ey != 0) v += ex * ey * Lab[0];
+        if constexpr (ex != 0 && ez != 0) v += ex * ez * Lab[1];
+        if constexpr (ey != 0 && ez != 0) v += ey * ez * Lab[2];
+        l[i] = v;
+    });
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// phi_T = dL/df_T through u_a = ucoef J_a / theta; eps-term of the recovery.
+template <class L, typename T>
+__global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__restrict__ P, Geom g, AdjK K,
+                                                                 const double *__restrict__ dLdu,
+                                                                 double *__restrict__ phi, double *__restrict__ slot)
+{
+    constexpr int V = 2;
+    const int lane = threadIdx.x & 31;
+    const int64_t seg = (int64_t)blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
+    if (seg >= g.nseg) return;
+    const int64_t row = seg / g.seg_per_row;
+    const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
+    T f[L::Q][V];
+    gather<L, T>(P, g, row, x0, lane, f);
+    const int64_t nodes = (int64_t)g.N0 * g.rows;
+    double out[L::Q][V];
+    double acc = 0.0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int x = x0 + V * lane + v;
+        double th = 0.0, J[3] = {0.0, 0.0, 0.0};
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const double fv = to_f(f[i][v], K.scale) + K.shift[i];
+            th += fv;
+            static_for<0, L::D>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                constexpr int e = L::E[i][a];
+                if constexpr (e != 0) J[a] += e * fv;
+            });
+        });
+        double gu[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 0.0};
+        if (x < g.N0) {
+            const int64_t node = row * g.N0 + x;
+#pragma unroll
+            for (int a = 0; a < L::D; ++a) {
+                gu[a] = dLdu[a * nodes + node];
+                u[a] = K.ucoef * J[a] / th;
+                acc += gu[a] * K.ducoef * J[a] / th;
+            }
+        }
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            double s = 0.0;
+            static_for<0, L::D>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                constexpr int e = L::E[i][a];
+                s += gu[a] * ((double)e * K.ucoef - u[a]);
+            });
+            out[i][v] = (x < g.N0) ? s / th : 0.0;
+        });
+    }
+    double *dp = phi + row * g.pitch + x0 + V * lane;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, out[i]);
+    acc = warp_sum(acc);
+    if (lane == 0) slot[seg] += acc;
+}
+
+// One reverse step: phi_out = K^T lambda(phi_in); eps-term if NU.
+template <class L, typename T, bool NU>
+__global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const double *__restrict__ phi_in,
+                                                                 const T *__restrict__ Pn,
+                                                                 double *__restrict__ phi_out, Geom g, AdjK K,
+                                                                 double *__restrict__ slot)
+{
+    constexpr int V = 2;
+    const int lane = threadIdx.x & 31;
+    const int64_t seg = (int64_t)blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
+    if (seg >= g.nseg) return;
+    const int64_t row = seg / g.seg_per_row;
+    const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
+    double lam[L::Q][V];
+    gather_rev<L>(phi_in, g, row, x0, lane, lam);
+    double acc = 0.0;
+    if constexpr (NU) {
+        T f[L::Q][V];
+        gather<L, T>(Pn, g, row, x0, lane, f);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            double fd[L::Q];
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) fd[i] = to_f(f[i][v], K.scale) + K.shift[i];
+            collide(L{}, fd, K.kd);
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) s = fma(lam[i][v], fd[i], s);
+            if (x0 + V * lane + v < g.N0) acc += s;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        double l[L::Q];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) l[i] = lam[i][v];
+        apply_KT<L>(l, K.k);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) lam[i][v] = l[i];
+    }
+    double *dp = phi_out + row * g.pitch + x0 + V * lane;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, lam[i]);
+    if constexpr (NU) {
+        acc = warp_sum(acc);
+        if (lane == 0) slot[seg] += acc;
+    }
+}
+
+// Adjoint of the initialisation f_i = w_i theta0 - sum_a A_ia d_a theta0:
+// dtheta0 = sum_i w_i phi_i, h_a = -sum_i A_ia phi_i (fed to G^T), and the
+// eps-term sum_i phi_i (w_i' theta0 - sum_a A'_ia d_a theta0).
+template <class L>
+__global__ void adj_init_kernel(const double *__restrict__ phi, Geom g, AdjK K, const double *__restrict__ th0,
+                                const double *__restrict__ grad, double *__restrict__ dth0,
+                                double *__restrict__ h, double *__restrict__ slot)
+{
+    const int64_t nodes = (int64_t)g.N0 * g.rows;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (n < nodes) {
+        const int x = (int)(n % g.N0);
+        const int64_t rw = n / g.N0;
+        const double *p = phi + rw * g.pitch + x;
+        const double t0 = th0[n];
+        double gr[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) gr[a] = grad[a * nodes + n];
+        double s = 0.0, hh[3] = {0.0, 0.0, 0.0};
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
+            constexpr int nz = (ex != 0) + (ey != 0) + (ez != 0);
+            const double ph = p[(int64_t)i * g.slab];
+            s = fma(K.w[i], ph, s);
+            double dfi = K.dw[i] * t0;
+            if constexpr (nz == 1) {
+                constexpr int a = (ex != 0) ? 0 : ((ey != 0) ? 1 : 2);
+                constexpr int sg = (ex != 0) ? ex : ((ey != 0) ? ey : ez);
+                hh[a] -= sg * K.iax * ph;
+                dfi -= sg * K.diax * gr[a];
+            } else if constexpr (nz == 2) {
+                if constexpr (ex != 0) hh[0] -= ex * K.idg * ph;
+                if constexpr (ey != 0) hh[1] -= ey * K.idg * ph;
+                if constexpr (ez != 0) hh[2] -= ez * K.idg * ph;
+                dfi -= K.didg * (ex * gr[0] + ey * gr[1] + ez * gr[2]);
+            }
+            acc = fma(ph, dfi, acc);
+        });
+        dth0[n] = s;
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) h[a * nodes + n] = hh[a];
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) slot[n >> 5] += acc;
+}
+
+// dth0 += G^T h, with (G^T h)(x) = sum_a sum_k cof_k h_a(x - off_k e_a) / (12 dx).
+__global__ void adj_fd4t_kernel(const double *__restrict__ h, double *__restrict__ dth0, int d, int N0, int N1,
+                                int N2, double inv12dx)
+{
+    const int64_t nodes = (int64_t)N0 * N1 * N2;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nodes) return;
+    const int x = (int)(n % N0);
+    const int64_t rw = n / N0;
+    const int y = (int)(rw % N1);
+    const int z = (int)(rw / N1);
+    const int nn[3] = {N0, N1, N2};
+    double s = 0.0;
+    for (int a = 0; a < d; ++a) {
+        const int off[4] = {2, 1, -1, -2};
+        const double cof[4] = {-1.0, 8.0, -8.0, 1.0};
+        for (int k = 0; k < 4; ++k) {
+            int c[3] = {x, y, z};
+            c[a] = ((c[a] - off[k]) % nn[a] + nn[a]) % nn[a];
+            s += cof[k] * h[a * nodes + ((int64_t)c[2] * N1 + c[1]) * N0 + c[0]];
+        }
+    }
+    dth0[n] += s * inv12dx;
+}
+
+// Fixed-order sum of n doubles into out[0] (one block).
+__global__ void __launch_bounds__(256) sum_slots_kernel(const double *__restrict__ a, int64_t n,
+                                                        const double *__restrict__ b, int64_t nb,
+                                                        double *__restrict__ out)
+{
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 256) s += a[i];
+    for (int64_t i = threadIdx.x; i < nb; i += 256) s += b[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+}  // namespace lbk
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+struct lb_adj {
+    lb_ctx *ctx = nullptr;
+    int64_t T = 0, C = 0, nck = 0;
+    bool want_nu = false;
+    size_t state_bytes = 0;
+    std::vector<void *> ck;   // checkpoints P_{kC}
+    std::vector<void *> seg;  // recomputed segment P_{kC + m}
+    int64_t seg_loaded = -1;
+    double *phi[2] = {nullptr, nullptr};
+    int pcur = 0;
+    double *th0 = nullptr, *grad = nullptr, *h = nullptr;
+    double *slot_step = nullptr, *slot_init = nullptr, *dsum = nullptr;
+    int64_t nslot_init = 0;
+    int64_t done = 0;  // reverse steps completed
+    bool forward_done = false, seeded = false;
+    lbk::AdjK K{};
+    size_t bytes = 0;
+};
+
+namespace {
+
+lb_status afail(lb_adj *a, lb_status s, const std::string &m)
+{
+    if (a && a->ctx) a->ctx->err = m;
+    return s;
+}
+
+lb_status acuda(lb_adj *a, cudaError_t e, const char *where)
+{
+    return afail(a, e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA,
+                 std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void free_adj(lb_adj *a)
+{
+    if (!a) return;
+    for (void *p : a->ck) cudaFree(p);
+    for (void *p : a->seg) cudaFree(p);
+    cudaFree(a->phi[0]);
+    cudaFree(a->phi[1]);
+    cudaFree(a->th0);
+    cudaFree(a->grad);
+    cudaFree(a->h);
+    cudaFree(a->slot_step);
+    cudaFree(a->slot_init);
+    cudaFree(a->dsum);
+    delete a;
+}
+
+// Collision, recovery and initialisation constants and their eps-derivatives
+// (Theorem 2, Eq. (Bur-Sol), differentiated in eps).
+void make_adjk(lb_adj *a)
+{
+    const lb_ctx &c = *a->ctx;
+    const int d = c.d;
+    const double eps = c.eps, A = 6.0 * eps + 1.0, B = 6.0 * eps + 3.0;
+    double ds1 = 0, ds2x = 0, ds22 = 0, dw1 = 0, dwd = 0;
+    if (c.paper) {
+        ds1 = -12.0 / (A * A);
+        ds2x = 24.0 / (A * A) - 288.0 * eps / (A * A * A);
+        if (d > 1) {
+            ds22 = -24.0 / (B * B);
+            dw1 = -(d - 1) / 3.0;
+            dwd = 1.0 / 6.0;
+        }
+    }
+    const double sigma = c.sigma, dsigma = 2.0 * dw1 + 4.0 * (d - 1) * dwd;
+    const double wd = (d > 1) ? c.wd : 0.0;
+    lbk::AdjK &K = a->K;
+    K.k = lbk::make_coll<double>(c);
+    K.kd.k1 = -ds1 / 2.0;
+    K.kd.k2 = -ds2x / 2.0;
+    K.kd.k3 = -ds22 / 4.0;
+    K.kd.c0 = -d * (ds2x * sigma + c.s2x * dsigma) + 2.0 * d * (d - 1) * dwd;
+    K.kd.cA = (ds2x * sigma + c.s2x * dsigma) / 2.0 - 2.0 * (d - 1) * dwd;
+    K.kd.wd = dwd;
+    const int q = c.q;
+    double w[lbk::kAdjQ], dw[lbk::kAdjQ];
+    w[0] = c.w0;
+    dw[0] = -2.0 * d * dw1 - 2.0 * d * (d - 1) * dwd;
+    for (int i = 1; i < q; ++i) {
+        w[i] = (i <= 2 * d) ? c.w1 : wd;
+        dw[i] = (i <= 2 * d) ? dw1 : dwd;
+    }
+    for (int i = 0; i < lbk::kAdjQ; ++i) {
+        K.w[i] = i < q ? w[i] : 0.0;
+        K.dw[i] = i < q ? dw[i] : 0.0;
+        K.shift[i] = 0.0;
+    }
+    K.scale = (c.precision == LB_FX64) ? ldexp(1.0, -c.fx_bits) : 1.0;
+    K.ucoef = (2.0 - c.s1) * c.c;
+    K.ducoef = -ds1 * c.c;
+    K.iax = 0.5 * c.dx * (sigma / c.s1 - 4.0 * (d - 1) * wd);
+    K.diax = 0.5 * c.dx * (dsigma / c.s1 - sigma * ds1 / (c.s1 * c.s1) - 4.0 * (d - 1) * dwd);
+    K.idg = wd * c.dx;
+    K.didg = dwd * c.dx;
+    K.inv12dx = 1.0 / (12.0 * c.dx);
+}
+
+int64_t sweep_blocks(const lbk::Geom &g) { return (g.nseg + lbk::kSweepThreads / 32 - 1) / (lbk::kSweepThreads / 32); }
+
+template <class L, typename T> cudaError_t seed_t(lb_adj *a, const double *dLdu)
+{
+    lb_ctx *c = a->ctx;
+    lbk::adj_seed_kernel<L, T><<<(unsigned)sweep_blocks(c->geom), lbk::kSweepThreads, 0, c->stream>>>(
+        (const T *)c->f[c->cur], c->geom, a->K, dLdu, a->phi[a->pcur], a->slot_step);
+    return cudaGetLastError();
+}
+
+template <class L, typename T> cudaError_t step_t(lb_adj *a, const void *Pn)
+{
+    lb_ctx *c = a->ctx;
+    const unsigned nb = (unsigned)sweep_blocks(c->geom);
+    if (a->want_nu)
+        lbk::adj_step_kernel<L, T, true><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
+            a->phi[a->pcur], (const T *)Pn, a->phi[a->pcur ^ 1], c->geom, a->K, a->slot_step);
+    else
+        lbk::adj_step_kernel<L, T, false><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
+            a->phi[a->pcur], (const T *)Pn, a->phi[a->pcur ^ 1], c->geom, a->K, a->slot_step);
+    return cudaGetLastError();
+}
+
+template <class L> cudaError_t init_t(lb_adj *a, double *dth0)
+{
+    lb_ctx *c = a->ctx;
+    const unsigned nb = (unsigned)((c->nodes + 255) / 256);
+    lbk::adj_init_kernel<L><<<nb, 256, 0, c->stream>>>(a->phi[a->pcur], c->geom, a->K, a->th0, a->grad, dth0, a->h,
+                                                       a->slot_init);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    lbk::adj_fd4t_kernel<<<nb, 256, 0, c->stream>>>(a->h, dth0, c->d, (int)c->N[0], (int)c->N[1], (int)c->N[2],
+                                                    a->K.inv12dx);
+    return cudaGetLastError();
+}
+
+cudaError_t do_seed(lb_adj *a, const double *dLdu)
+{
+    const bool fx = a->ctx->precision == LB_FX64;
+    switch (a->ctx->d) {
+    case 1: return fx ? seed_t<lbk::D1Q3, long long>(a, dLdu) : seed_t<lbk::D1Q3, double>(a, dLdu);
+    case 2: return fx ? seed_t<lbk::D2Q9, long long>(a, dLdu) : seed_t<lbk::D2Q9, double>(a, dLdu);
+    default: return fx ? seed_t<lbk::D3Q19, long long>(a, dLdu) : seed_t<lbk::D3Q19, double>(a, dLdu);
+    }
+}
+
+cudaError_t do_step(lb_adj *a, const void *Pn)
+{
+    const bool fx = a->ctx->precision == LB_FX64;
+    switch (a->ctx->d) {
+    case 1: return fx ? step_t<lbk::D1Q3, long long>(a, Pn) : step_t<lbk::D1Q3, double>(a, Pn);
+    case 2: return fx ? step_t<lbk::D2Q9, long long>(a, Pn) : step_t<lbk::D2Q9, double>(a, Pn);
+    default: return fx ? step_t<lbk::D3Q19, long long>(a, Pn) : step_t<lbk::D3Q19, double>(a, Pn);
+    }
+}
+
+cudaError_t do_init(lb_adj *a, double *dth0)
+{
+    switch (a->ctx->d) {
+    case 1: return init_t<lbk::D1Q3>(a, dth0);
+    case 2: return init_t<lbk::D2Q9>(a, dth0);
+    default: return init_t<lbk::D3Q19>(a, dth0);
+    }
+}
+
+// Make P_n available (n < T): checkpoint segment k = n / C recomputed into seg.
+cudaError_t state_at(lb_adj *a, int64_t n, const void **out)
+{
+    lb_ctx *c = a->ctx;
+    const int64_t k = n / a->C;
+    if (a->seg_loaded != k) {
+        cudaError_t e = cudaMemcpyAsync(a->seg[0], a->ck[k], a->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return e;
+        const int64_t len = std::min<int64_t>(a->C, a->T - k * a->C);
+        for (int64_t m = 1; m < len; ++m) {
+            e = lbk::launch_sweep(c, a->seg[m - 1], a->seg[m]);
+            if (e != cudaSuccess) return e;
+        }
+        a->seg_loaded = k;
+    }
+    *out = a->seg[n - k * a->C];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_adj **out)
+{
+    if (!out) return LB_EINVAL;
+    *out = nullptr;
+    if (!ctx || T < 1) return LB_EINVAL;
+    if (ctx->precision == LB_FP32_SHIFTED) {
+        ctx->err = "lb_adjoint_create: the adjoint supports LB_FP64 and LB_FX64 contexts";
+        return LB_EINVAL;
+    }
+    if (want_nu && !ctx->paper) {
+        ctx->err = "lb_adjoint_create: dL/dnu needs the paper's relaxation set";
+        return LB_EINVAL;
+    }
+    if (C == 0) C = (int64_t)ceil(sqrt((double)T));
+    if (C < 1 || C > T) {
+        ctx->err = "lb_adjoint_create: checkpoint interval out of range";
+        return LB_EINVAL;
+    }
+    lb_adj *a = new (std::nothrow) lb_adj();
+    if (!a) return LB_ENOMEM;
+    a->ctx = ctx;
+    a->T = T;
+    a->C = C;
+    a->want_nu = want_nu != 0;
+    a->state_bytes = (size_t)ctx->q * ctx->geom.slab * ctx->elem;
+    cudaError_t e = cudaSuccess;
+    const size_t pbytes = (size_t)ctx->q * ctx->geom.slab * sizeof(double);
+    if (a->want_nu) {
+        a->nck = (T + C - 1) / C;
+        a->ck.assign(a->nck, nullptr);
+        a->seg.assign(C, nullptr);
+        for (auto &p : a->ck)
+            if (e == cudaSuccess) e = cudaMalloc(&p, a->state_bytes);
+        for (auto &p : a->seg)
+            if (e == cudaSuccess) e = cudaMalloc(&p, a->state_bytes);
+        a->bytes += (a->nck + C) * a->state_bytes;
+    }
+    for (auto &p : a->phi)
+        if (e == cudaSuccess) e = cudaMalloc(&p, pbytes);
+    a->nslot_init = (ctx->nodes + 255) / 256 * 8;
+    if (e == cudaSuccess) e = cudaMalloc(&a->th0, sizeof(double) * ctx->nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&a->grad, sizeof(double) * ctx->d * ctx->nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&a->h, sizeof(double) * ctx->d * ctx->nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&a->slot_step, sizeof(double) * ctx->geom.nseg);
+    if (e == cudaSuccess) e = cudaMalloc(&a->slot_init, sizeof(double) * a->nslot_init);
+    if (e == cudaSuccess) e = cudaMalloc(&a->dsum, sizeof(double));
+    a->bytes += 2 * pbytes + sizeof(double) * ctx->nodes * (1 + 2 * ctx->d);
+    if (e != cudaSuccess) {
+        free_adj(a);
+        return e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA;
+    }
+    *out = a;
+    return LB_OK;
+}
+
+lb_status lb_adjoint_destroy(lb_adj *a)
+{
+    if (!a) return LB_OK;
+    cudaStreamSynchronize(a->ctx->stream);
+    free_adj(a);
+    return LB_OK;
+}
+
+lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, double *u)
+{
+    if (!a || !theta0) return LB_EINVAL;
+    lb_ctx *c = a->ctx;
+    a->forward_done = a->seeded = false;
+    a->seg_loaded = -1;
+    lb_status st = lb_set_theta0(c, theta0, nullptr);  // FD4 gradient: a function of theta0 alone
+    if (st != LB_OK) return st;
+    make_adjk(a);  // after lb_set_theta0: the FX64 scale is known now
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(a->th0, theta0, sizeof(double) * c->nodes, cudaMemcpyDeviceToDevice, c->stream)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(a->grad, c->gradtmp, sizeof(double) * c->d * c->nodes, cudaMemcpyDeviceToDevice,
+                             c->stream)) != cudaSuccess)
+        return acuda(a, e, "lb_adjoint_forward");
+    for (int64_t k = 0; k * a->C < a->T; ++k) {
+        if (a->want_nu &&
+            (e = cudaMemcpyAsync(a->ck[k], c->f[c->cur], a->state_bytes, cudaMemcpyDeviceToDevice, c->stream)) !=
+                cudaSuccess)
+            return acuda(a, e, "lb_adjoint_forward: checkpoint");
+        const int64_t n = std::min<int64_t>(a->C, a->T - k * a->C);
+        if ((st = lb_step(c, n)) != LB_OK) return st;
+    }
+    if ((theta || u) && (st = lb_macros(c, theta, nullptr, u)) != LB_OK) return st;
+    a->forward_done = true;
+    return LB_OK;
+}
+
+lb_status lb_adjoint_seed(lb_adj *a, const double *dLdu)
+{
+    if (!a || !dLdu) return LB_EINVAL;
+    if (!a->forward_done || a->ctx->step != a->T)
+        return afail(a, LB_ESTATE, "lb_adjoint_seed: run lb_adjoint_forward first (and do not step the context)");
+    lb_ctx *c = a->ctx;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(a->slot_step, 0, sizeof(double) * c->geom.nseg, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(a->slot_init, 0, sizeof(double) * a->nslot_init, c->stream)) != cudaSuccess)
+        return acuda(a, e, "lb_adjoint_seed");
+    a->pcur = 0;
+    if ((e = do_seed(a, dLdu)) != cudaSuccess) return acuda(a, e, "lb_adjoint_seed: launch");
+    a->done = 0;
+    a->seeded = true;
+    return LB_OK;
+}
+
+lb_status lb_adjoint_step(lb_adj *a, int64_t nsteps)
+{
+    if (!a || nsteps < 0) return LB_EINVAL;
+    if (!a->seeded) return afail(a, LB_ESTATE, "lb_adjoint_step: call lb_adjoint_seed first");
+    if (a->done + nsteps > a->T) return afail(a, LB_EINVAL, "lb_adjoint_step: more reverse steps than forward");
+    cudaError_t e;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        const int64_t n = a->T - 1 - a->done;  // producing phi_n from phi_{n+1}
+        const void *Pn = nullptr;
+        if (a->want_nu && (e = state_at(a, n, &Pn)) != cudaSuccess) return acuda(a, e, "lb_adjoint_step: recompute");
+        if ((e = do_step(a, Pn)) != cudaSuccess) return acuda(a, e, "lb_adjoint_step: launch");
+        a->pcur ^= 1;
+        ++a->done;
+    }
+    return LB_OK;
+}
+
+lb_status lb_adjoint_result(lb_adj *a, double *dL_dtheta0, double *dL_dnu)
+{
+    if (!a || !dL_dtheta0) return LB_EINVAL;
+    if (!a->seeded || a->done != a->T) return afail(a, LB_ESTATE, "lb_adjoint_result: reverse pass incomplete");
+    lb_ctx *c = a->ctx;
+    cudaError_t e = do_init(a, dL_dtheta0);
+    if (e != cudaSuccess) return acuda(a, e, "lb_adjoint_result: init adjoint");
+    if (dL_dnu) {
+        if (!a->want_nu) return afail(a, LB_EINVAL, "lb_adjoint_result: dL/dnu was not requested");
+        lbk::sum_slots_kernel<<<1, 256, 0, c->stream>>>(a->slot_step, c->geom.nseg, a->slot_init, a->nslot_init,
+                                                        a->dsum);
+        double deps = 0.0;
+        if ((e = cudaGetLastError()) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&deps, a->dsum, sizeof(double), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+            return acuda(a, e, "lb_adjoint_result: eps sum");
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return acuda(a, e, "lb_adjoint_result");
+        *dL_dnu = deps * c->dt / (c->dx * c->dx);  // d eps / d nu
+        return LB_OK;
+    }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return acuda(a, e, "lb_adjoint_result");
+    return LB_OK;
+}
+
+lb_status lb_adjoint_info(const lb_adj *a, double *info)
+{
+    if (!a || !info) return LB_EINVAL;
+    info[0] = (double)a->T;
+    info[1] = (double)a->C;
+    info[2] = (double)a->nck;
+    info[3] = (double)a->done;
+    info[4] = (double)a->bytes;
+    return LB_OK;
+}
+
+}  // extern "C"

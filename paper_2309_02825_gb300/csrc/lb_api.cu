@@ -65,6 +65,7 @@ bool derive_params(lb_ctx &c, const lb_relax *rs)
 {
     const int d = c.d;
     const bool paper = !rs || rs->paper_set;
+    c.paper = paper;
     if (paper) {
         const double a = 6.0 * c.eps + 1.0;
         c.s1 = 2.0 / a;

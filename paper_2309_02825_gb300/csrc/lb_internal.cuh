@@ -104,6 +104,7 @@ struct lb_ctx {
     double nu = 0, dx = 0, dt = 0, c = 0, eps = 0, cs2 = 0, sigma = 0;
     double s1 = 0, s2x = 0, s22 = 1, w0 = 0, w1 = 0, wd = 0, theta_ref = 0;
     int fx_bits = 0;          // LB_FX64: stored value = round(f * 2^fx_bits)
+    bool paper = true;        // relaxation set from Theorem 2 (eps-derivatives known)
     cudaStream_t stream = nullptr;
     lbk::Geom geom{};
     size_t elem = 8;

@@ -430,3 +430,85 @@ class Batch:
             a = flat[comps * self.node_off[j]: comps * self.node_off[j + 1]]
             out.append(a.reshape((comps, n1, n0)) if comps > 1 else a.reshape((n1, n0)))
         return out
+
+
+# --------------------------------------------------------------------------
+# Discrete adjoint (include/lb_adjoint.h).
+# --------------------------------------------------------------------------
+
+_adj_sigs = {
+    "lb_adjoint_create": (["vp", "i64", "i64", "i", "pvp"], "i"),
+    "lb_adjoint_destroy": (["vp"], "i"),
+    "lb_adjoint_forward": (["vp", "vp", "vp", "vp"], "i"),
+    "lb_adjoint_seed": (["vp", "vp"], "i"),
+    "lb_adjoint_step": (["vp", "i64"], "i"),
+    "lb_adjoint_result": (["vp", "vp", "pd"], "i"),
+    "lb_adjoint_info": (["vp", "pd"], "i"),
+}
+
+
+def _load_adj():
+    lib = load()
+    if getattr(lib, "_adj_ready", False):
+        return lib
+    m = {"i": ctypes.c_int, "i64": ctypes.c_int64, "vp": ctypes.c_void_p, "pd": ctypes.POINTER(ctypes.c_double),
+         "pvp": ctypes.POINTER(ctypes.c_void_p)}
+    for name, (args, res) in _adj_sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = [m[a] for a in args]
+        fn.restype = m[res]
+    lib._adj_ready = True
+    return lib
+
+
+class Adjoint:
+    """Adjoint workspace over a :class:`Solver` (FP64 or FX64): forward with
+    checkpoints, seed with dL/du at T, reverse steps, gradients."""
+
+    def __init__(self, solver, T, checkpoint=0, want_nu=True):
+        self._lib = _load_adj()
+        self.solver = solver
+        self.T = int(T)
+        out = ctypes.c_void_p()
+        st = self._lib.lb_adjoint_create(solver.ctx, self.T, int(checkpoint), int(bool(want_nu)), ctypes.byref(out))
+        _check(self._lib, solver.ctx, st, "lb_adjoint_create")
+        self.h = out
+        self.want_nu = bool(want_nu)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lb_adjoint_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, name, *args):
+        _check(self._lib, self.solver.ctx, getattr(self._lib, name)(self.h, *args), name)
+
+    def forward(self, theta0, theta=None, u=None):
+        s = self.solver
+        u = u if u is not None else torch.empty((s.d,) + s.shape, dtype=torch.float64, device="cuda")
+        self._call("lb_adjoint_forward", _ptr(theta0, "theta0", numel=s.nodes), _ptr(theta, "theta"), _ptr(u, "u"))
+        return u
+
+    def seed(self, dL_du):
+        self._call("lb_adjoint_seed", _ptr(dL_du, "dL_du", numel=self.solver.d * self.solver.nodes))
+
+    def step(self, n):
+        self._call("lb_adjoint_step", int(n))
+
+    def result(self):
+        g = torch.empty(self.solver.shape, dtype=torch.float64, device="cuda")
+        dnu = ctypes.c_double(float("nan"))
+        self._call("lb_adjoint_result", _ptr(g, "dL_dtheta0"), ctypes.byref(dnu) if self.want_nu else None)
+        return g, (dnu.value if self.want_nu else None)
+
+    def info(self):
+        buf = (ctypes.c_double * 5)()
+        self._call("lb_adjoint_info", buf)
+        return {"T": int(buf[0]), "checkpoint": int(buf[1]), "checkpoints": int(buf[2]), "done": int(buf[3]),
+                "bytes": int(buf[4])}
