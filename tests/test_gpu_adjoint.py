@@ -96,6 +96,6 @@ def test_autograd_function():
     loss = 0.5 * ((u - torch.from_numpy(ut).cuda()) ** 2).sum()
     loss.backward()
     L, g, dnu = _gpu_grad(d, N, nu, dx, dt, T, th0, ut)
-    assert float(loss) == pytest.approx(L, rel=1e-14)
+    assert float(loss.detach()) == pytest.approx(L, rel=1e-14)
     assert np.array_equal(theta0.grad.cpu().numpy(), g)
     assert float(nu_t.grad) == dnu
