@@ -13,6 +13,14 @@ stream.  ``e2e`` repeats the step through the public API from pinned host
 buffers (inputs copied in, theta and u copied out, inside the timed
 region).  ``--impl reference`` times the FP64 CPU oracle instead.
 
+Precisions: the headline is FX64 (64-bit fixed-point state, exact integer
+moment sums; FP64-accurate and HBM-bound on GB300, whose FP64 pipe runs at
+1/64 of FP32); FP64 and FP32-shifted are reported under ``variants``.
+Also reported: ``batched`` (512 uneven 2D instances x 2000 steps),
+``adjoint`` (512^2, T = 2000: reverse-step cost and finite-difference
+checks) and ``sweeps_3d`` (D3Q19 256^3).  ``--accuracy`` prints the
+error-vs-exact convergence table instead.
+
 Multi-GPU: the path is one periodic grid per GPU; ranks run independent
 replicas (weak scaling, no collective on the data path).
 """
@@ -55,6 +63,9 @@ def parse():
     p.add_argument("--no-variant", action="store_true", help="skip the other precisions' sub-results")
     p.add_argument("--no-batched", action="store_true", help="skip the batched 512-instance measurement")
     p.add_argument("--no-adjoint", action="store_true", help="skip the 512^2 adjoint measurement")
+    p.add_argument("--no-3d", action="store_true", help="skip the 3D 256^3 sweep measurement")
+    p.add_argument("--accuracy", action="store_true",
+                   help="print the error-vs-exact convergence table (1D, 2D up to 4096^2, 3D up to 256^3) and exit")
     return p.parse_args()
 
 
@@ -456,6 +467,91 @@ def run_adjoint(local, precision="fp64"):
     }
 
 
+def _run_case(case, precision, theta_ref, stream, th0=None, g0=None, nsteps=None, exact=None):
+    """Run one workload case to its end time; return the error norms."""
+    import torch
+    from paper_2309_02825_gb300 import lb
+    N, d = case.N, case.d
+    n = case.nsteps if nsteps is None else nsteps
+    th0 = th0 if th0 is not None else torch.from_numpy(case.problem.theta(N, case.dx)).cuda()
+    g0 = g0 if g0 is not None else torch.from_numpy(np.ascontiguousarray(case.problem.grad(N, case.dx))).cuda()
+    s = lb.Solver(d, N, case.nu, case.dx, case.dt, precision=precision, theta_ref=theta_ref, stream=stream)
+    with torch.cuda.stream(stream):
+        s.set_theta0(th0, g0)
+        s.step(n)
+        th, _, u = s.macros(want=("theta", "u"))
+        T = n * case.dt
+        if exact is None:
+            exact = (torch.from_numpy(case.problem.theta(N, case.dx, T)).cuda(),
+                     torch.from_numpy(np.ascontiguousarray(case.problem.u(N, case.dx, T))).cuda())
+        r = s.reduce(th, u, exact[0], exact[1])
+    s.close()
+    return {"theta_rmse": r["theta"]["rmse"],
+            "u_rmse": math.sqrt(sum(r["u%d" % a]["rmse"] ** 2 for a in range(d)) / d),
+            "u_linf": max(r["u%d" % a]["linf"] for a in range(d)),
+            "u_rel_l2": math.sqrt(sum(r["u%d" % a]["rel_l2"] ** 2 for a in range(d)) / d)}
+
+
+def run_3d(local, peaks):
+    """3D D3Q19 periodic 256^3 (the 3D Fourier family): sweep throughput and
+    %HBM for each precision, and the error against the exact solution at
+    t_end = 0.02 (256 steps)."""
+    import torch
+    from paper_2309_02825_gb300 import lb
+    torch.cuda.set_device(local)
+    case = W.fourier_3d(256)
+    stream = torch.cuda.Stream()
+    th0 = torch.from_numpy(case.problem.theta(case.N, case.dx)).cuda()
+    g0 = torch.from_numpy(np.ascontiguousarray(case.problem.grad(case.N, case.dx))).cuda()
+    exact = (torch.from_numpy(case.problem.theta(case.N, case.dx, case.t_end)).cuda(),
+             torch.from_numpy(np.ascontiguousarray(case.problem.u(case.N, case.dx, case.t_end))).cuda())
+    out = {"workload": "3D D3Q19 periodic 256^3, nu=0.01, eps=0.0512, 1.5 + 8 seeded modes, t_end=0.02 (256 steps)"}
+    for prec in ("fx64", "fp64", "fp32s"):
+        s = lb.Solver(3, case.N, case.nu, case.dx, case.dt, precision=prec, theta_ref=1.5, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            s.set_theta0(th0, g0)
+            s.step(10)
+            e0.record(stream)
+            s.step(50)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 50
+        s.close()
+        elem = 4 if prec == "fp32s" else 8
+        gbs = 2 * 19 * elem * case.nodes / (ms / 1e3) / 1e9
+        err = _run_case(case, prec, 1.5, stream, th0, g0, exact=exact)
+        out[prec] = {"sweep_ms": ms, "mlups": case.nodes / (ms / 1e3) / 1e6, "bytes_per_lu": 2 * 19 * elem,
+                     "hbm_frac": gbs / peaks["hbm_gbs"], "achieved_gbs": gbs, "error_t_end": err}
+    return out
+
+
+def run_accuracy(local):
+    """Error against the exact solution per grid size and precision, run to
+    each family's end time; CR = log2 of successive RMSE ratios."""
+    import torch
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    table = {}
+    fams = [("1d_sine", W.sine_1d, (16, 32, 64, 128), 2.0), ("2d_sine", W.sine_2d, (64, 128, 256, 512, 1024, 2048, 4096), 2.0),
+            ("3d_fourier", W.fourier_3d, (32, 64, 128, 256), 1.5)]
+    for name, fam, Ns, tref in fams:
+        for prec in ("fp64", "fx64", "fp32s"):
+            rows, prev = [], None
+            for N in Ns:
+                case = fam(N)
+                t0 = time.perf_counter()
+                e = _run_case(case, prec, tref, stream)
+                e["N"], e["steps"], e["seconds"] = N, case.nsteps, time.perf_counter() - t0
+                if prev:
+                    e["CR_u"] = math.log2(prev["u_rmse"] / e["u_rmse"])
+                    e["CR_theta"] = math.log2(prev["theta_rmse"] / e["theta_rmse"])
+                rows.append(e)
+                prev = e
+            table["%s_%s" % (name, prec)] = rows
+    return table
+
+
 # ---------------------------------------------------------------------------
 # The oracle (CPU baseline / reference arm).
 # ---------------------------------------------------------------------------
@@ -511,6 +607,10 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     world, rank, local = dist_setup(args)
+    if args.accuracy:
+        if rank == 0:
+            print(json.dumps({"accuracy": run_accuracy(local)}))
+        return 0
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -535,6 +635,9 @@ def main():
     adjoint = None
     if not args.no_adjoint:
         adjoint = run_adjoint(local)
+    sweeps3d = None
+    if not args.no_3d:
+        sweeps3d = run_3d(local, peaks)
     base = None
     if rank == 0 and not args.no_cpu_baseline:
         base = cpu_baseline(args)
@@ -567,6 +670,8 @@ def main():
             line["batched"] = batched
         if adjoint:
             line["adjoint"] = adjoint
+        if sweeps3d:
+            line["sweeps_3d"] = sweeps3d
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
