@@ -83,9 +83,12 @@ def profile_traffic(kernel_key):
     """DRAM bytes per launch from a committed ncu summary for this kernel,
     valid only while the kernel source is unchanged (same sha)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2309_02825_gb300", "csrc", "lb_kernels.cu")
+    csrc = os.path.join(ROOT, "paper_2309_02825_gb300", "csrc")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for name in ("lb_device.cuh", "lb_kernels.cu", "lb_fx.cu"):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+        sha = h.hexdigest()[:16]
         path = os.path.join(ROOT, "profiles", "traffic.txt")
         for line in open(path):
             parts = line.split()

@@ -106,9 +106,12 @@ __device__ __forceinline__ void pull_row(const T *__restrict__ row, int x0, int 
     }
 }
 
-// Gather the pre-collision f(x, n) for the V nodes of this lane.
+// Gather the pre-collision f(x, n) for the V nodes of this lane, one
+// population at a time (each shifted pull right after its load).  Used for
+// FP64 storage, whose sweep is bound by the FP64 pipe: the lower register
+// count keeps more warps resident to hide FP64 latency.
 template <class L, typename T>
-__device__ __forceinline__ void gather(const T *__restrict__ src, const Geom &g, int64_t row, int x0, int lane,
+__device__ __forceinline__ void gather_interleaved(const T *__restrict__ src, const Geom &g, int64_t row, int x0, int lane,
                                        T (&f)[L::Q][Vec<T>::V])
 {
     const int y = (int)(row % g.N1);
@@ -121,6 +124,71 @@ __device__ __forceinline__ void gather(const T *__restrict__ src, const Geom &g,
         const T *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
         pull_row<T, ex>(rp, x0, lane, g.N0, f[i]);
     });
+}
+
+// Gather in two phases: every 16-byte vector load of every population, and
+// the one halo scalar a warp edge needs, is issued before any shuffle
+// consumes a loaded value, so a warp has all q rows in flight at once.  Used
+// for the HBM-bound storage types (FP32, 64-bit fixed point).
+template <class L, typename T>
+__device__ __forceinline__ void gather_two_phase(const T *__restrict__ src, const Geom &g, int64_t row, int x0,
+                                                 int lane, T (&f)[L::Q][Vec<T>::V])
+{
+    constexpr int V = Vec<T>::V;
+    const int y = (int)(row % g.N1);
+    const int z = (int)(row / g.N1);
+    const int xb = x0 + V * lane;
+    T halo[L::Q];
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
+        const int ys = (ey == 0) ? y : wrapi(y - ey, g.N1);
+        const int zs = (ez == 0) ? z : wrapi(z - ez, g.N2);
+        const T *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
+        ld_vec(rp + xb, f[i]);
+        halo[i] = T(0);
+        if constexpr (ex == 1) {
+            if (lane == 0) halo[i] = rp[xb == 0 ? g.N0 - 1 : xb - 1];
+        } else if constexpr (ex == -1) {
+            const int x = xb + V - 1;
+            if (lane == 31 && x + 1 < g.N0) halo[i] = rp[x + 1];
+        }
+    });
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
+        if constexpr (ex == 1) {
+            T left = __shfl_up_sync(0xffffffffu, f[i][V - 1], 1);
+            if (lane == 0) left = halo[i];
+#pragma unroll
+            for (int k = V - 1; k > 0; --k) f[i][k] = f[i][k - 1];
+            f[i][0] = left;
+        } else if constexpr (ex == -1) {
+            T right = __shfl_down_sync(0xffffffffu, f[i][0], 1);
+            if (lane == 31) right = halo[i];
+#pragma unroll
+            for (int k = 0; k < V - 1; ++k) f[i][k] = f[i][k + 1];
+            f[i][V - 1] = right;
+            if (xb + V >= g.N0) {  // the node at x = N0 - 1 pulls from x = 0
+                const int ys = (ey == 0) ? y : wrapi(y - ey, g.N1);
+                const int zs = (ez == 0) ? z : wrapi(z - ez, g.N2);
+                const T *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
+#pragma unroll
+                for (int k = 0; k < V; ++k)
+                    if (xb + k + 1 == g.N0) f[i][k] = rp[0];
+            }
+        }
+    });
+}
+
+template <class L, typename T>
+__device__ __forceinline__ void gather(const T *__restrict__ src, const Geom &g, int64_t row, int x0, int lane,
+                                       T (&f)[L::Q][Vec<T>::V])
+{
+    if constexpr (std::is_same<T, double>::value)
+        gather_interleaved<L, T>(src, g, row, x0, lane, f);
+    else
+        gather_two_phase<L, T>(src, g, row, x0, lane, f);
 }
 
 // ---------------------------------------------------------------------------
@@ -229,15 +297,20 @@ __device__ __forceinline__ void collide(D3Q19, T *f, const Coll<T> &k)
 // ---------------------------------------------------------------------------
 constexpr int kSweepThreads = 256;
 
+// Threads per block of the sweep: 128 for the HBM-bound storage types
+// (more, smaller blocks balance the SMs better), 256 for FP64.
+template <typename T> __host__ __device__ constexpr int sweep_threads() { return std::is_same<T, double>::value ? 256 : 128; }
+
 // K is the collision-constant type; the matching collide() overload (float,
 // double or 64-bit fixed point) is picked by overload resolution.
 template <class L, typename T, class K>
-__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const T *__restrict__ src, T *__restrict__ dst,
-                                                              Geom g, K k)
+__global__ void __launch_bounds__(sweep_threads<T>()) sweep_kernel(const T *__restrict__ src,
+                                                                   T *__restrict__ dst, Geom g, K k)
 {
     constexpr int V = Vec<T>::V;
+    constexpr int TH = sweep_threads<T>();
     const int lane = threadIdx.x & 31;
-    const int64_t seg = (int64_t)blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
+    const int64_t seg = (int64_t)blockIdx.x * (TH / 32) + (threadIdx.x >> 5);
     if (seg >= g.nseg) return;  // warp-uniform
     const int64_t row = seg / g.seg_per_row;
     const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);

@@ -183,7 +183,9 @@ static int64_t blocks(const Geom &g) { return (g.nseg + kSweepThreads / 32 - 1) 
 
 template <class L> static cudaError_t sweep_fx_t(lb_ctx *c, const void *src, void *dst)
 {
-    sweep_kernel<L, long long, CollFx><<<(unsigned)blocks(c->geom), kSweepThreads, 0, c->stream>>>(
+    constexpr int TH = sweep_threads<long long>();
+    const unsigned nb = (unsigned)((c->geom.nseg + TH / 32 - 1) / (TH / 32));
+    sweep_kernel<L, long long, CollFx><<<nb, TH, 0, c->stream>>>(
         (const long long *)src, (long long *)dst, c->geom, make_coll_fx(c));
     return cudaGetLastError();
 }

@@ -298,7 +298,9 @@ static int64_t sweep_blocks(const Geom &g) { return (g.nseg + kSweepThreads / 32
 
 template <class L, typename T> static cudaError_t sweep_t(lb_ctx *c, const void *src, void *dst)
 {
-    sweep_kernel<L, T, Coll<T>><<<(unsigned)sweep_blocks(c->geom), kSweepThreads, 0, c->stream>>>(
+    constexpr int TH = sweep_threads<T>();
+    const unsigned nb = (unsigned)((c->geom.nseg + TH / 32 - 1) / (TH / 32));
+    sweep_kernel<L, T, Coll<T>><<<nb, TH, 0, c->stream>>>(
         (const T *)src, (T *)dst, c->geom, make_coll<T>(*c));
     return cudaGetLastError();
 }
