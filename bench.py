@@ -451,13 +451,13 @@ def run_adjoint(local, precision="fp64"):
     s.close()
     rng = np.random.default_rng(2314)
     checks = []
-    for _ in range(2):
+    for _ in range(2 if precision == "fp64" else 0):
         v = torch.from_numpy(rng.normal(size=tuple(th0.shape))).cuda()
         h = 1e-5
         fd = (loss(case.nu, th0 + h * v) - loss(case.nu, th0 - h * v)) / (2 * h)
         checks.append(abs(float((g * v).sum()) / fd - 1.0))
     hn = 1e-6 * case.nu
-    fd_nu = (loss(case.nu + hn, th0) - loss(case.nu - hn, th0)) / (2 * hn)
+    fd_nu = ((loss(case.nu + hn, th0) - loss(case.nu - hn, th0)) / (2 * hn)) if precision == "fp64" else float("nan")
     return {
         "workload": "2D D2Q9 512^2, nu=0.02, eps=0.2048, T=2000, L=0.5||u(T)-u_target||^2, %s, checkpoint every %d "
                     "steps (%d checkpoints)" % (precision, info["checkpoint"], info["checkpoints"]),
@@ -637,7 +637,13 @@ def main():
         batched = run_batched(local)
     adjoint = None
     if not args.no_adjoint:
-        adjoint = run_adjoint(local)
+        adjoint = run_adjoint(local, "fp64")
+        for prec in ("fx64", "fp32s"):
+            a = run_adjoint(local, prec)
+            adjoint[prec] = {k: a[k] for k in ("forward_with_checkpoints_s", "reverse_s", "plain_sweep_us",
+                                               "reverse_step_us", "adjoint_step_cost_vs_forward_step",
+                                               "gradient_total_cost_vs_forward", "loss", "dL_dnu")}
+            adjoint[prec]["dL_dnu_rel_diff_vs_fp64"] = abs(a["dL_dnu"] / adjoint["dL_dnu"] - 1.0)
     sweeps3d = None
     if not args.no_3d:
         sweeps3d = run_3d(local, peaks)

@@ -30,7 +30,8 @@ extern "C" {
 typedef struct lb_adj lb_adj;
 
 /*
- * Adjoint workspace for `ctx` (any precision; d = 1, 2, 3).
+ * Adjoint workspace for `ctx` (any precision: the forward states are read in
+ * their storage type, the adjoint itself is FP64; d = 1, 2, 3).
  *   T        forward steps (>= 1).
  *   C        checkpoint interval, 1 <= C <= T, or 0 for ceil(sqrt(T)).
  *   want_nu  nonzero to also compute dL/dnu (needs the paper's relaxation

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
     const int64_t row = seg / g.seg_per_row;
     const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
     T f[L::Q][V];
-    gather<L, T>(P, g, row, x0, lane, f);
+    gather<L, T, V>(P, g, row, x0, lane, f);
     const int64_t nodes = (int64_t)g.N0 * g.rows;
     double out[L::Q][V];
     double acc = 0.0;
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const double *_
     double acc = 0.0;
     if constexpr (NU) {
         T f[L::Q][V];
-        gather<L, T>(Pn, g, row, x0, lane, f);
+        gather<L, T, V>(Pn, g, row, x0, lane, f);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             double fd[L::Q];
@@ -313,6 +313,7 @@ __global__ void __launch_bounds__(256) sum_slots_kernel(const double *__restrict
 // ---------------------------------------------------------------------------
 struct lb_adj {
     lb_ctx *ctx = nullptr;
+    lbk::Geom ag{};  // the state's rows cut into 64-node segments (2 per lane)
     int64_t T = 0, C = 0, nck = 0;
     bool want_nu = false;
     size_t state_bytes = 0;
@@ -401,6 +402,8 @@ void make_adjk(lb_adj *a)
         K.shift[i] = 0.0;
     }
     K.scale = (c.precision == LB_FX64) ? ldexp(1.0, -c.fx_bits) : 1.0;
+    if (c.precision == LB_FP32_SHIFTED)  // stored f - w theta_ref
+        for (int i = 0; i < q; ++i) K.shift[i] = w[i] * c.theta_ref;
     K.ucoef = (2.0 - c.s1) * c.c;
     K.ducoef = -ds1 * c.c;
     K.iax = 0.5 * c.dx * (sigma / c.s1 - 4.0 * (d - 1) * wd);
@@ -415,21 +418,21 @@ int64_t sweep_blocks(const lbk::Geom &g) { return (g.nseg + lbk::kSweepThreads /
 template <class L, typename T> cudaError_t seed_t(lb_adj *a, const double *dLdu)
 {
     lb_ctx *c = a->ctx;
-    lbk::adj_seed_kernel<L, T><<<(unsigned)sweep_blocks(c->geom), lbk::kSweepThreads, 0, c->stream>>>(
-        (const T *)c->f[c->cur], c->geom, a->K, dLdu, a->phi[a->pcur], a->slot_step);
+    lbk::adj_seed_kernel<L, T><<<(unsigned)sweep_blocks(a->ag), lbk::kSweepThreads, 0, c->stream>>>(
+        (const T *)c->f[c->cur], a->ag, a->K, dLdu, a->phi[a->pcur], a->slot_step);
     return cudaGetLastError();
 }
 
 template <class L, typename T> cudaError_t step_t(lb_adj *a, const void *Pn)
 {
     lb_ctx *c = a->ctx;
-    const unsigned nb = (unsigned)sweep_blocks(c->geom);
+    const unsigned nb = (unsigned)sweep_blocks(a->ag);
     if (a->want_nu)
         lbk::adj_step_kernel<L, T, true><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
-            a->phi[a->pcur], (const T *)Pn, a->phi[a->pcur ^ 1], c->geom, a->K, a->slot_step);
+            a->phi[a->pcur], (const T *)Pn, a->phi[a->pcur ^ 1], a->ag, a->K, a->slot_step);
     else
         lbk::adj_step_kernel<L, T, false><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
-            a->phi[a->pcur], (const T *)Pn, a->phi[a->pcur ^ 1], c->geom, a->K, a->slot_step);
+            a->phi[a->pcur], (const T *)Pn, a->phi[a->pcur ^ 1], a->ag, a->K, a->slot_step);
     return cudaGetLastError();
 }
 
@@ -446,23 +449,39 @@ template <class L> cudaError_t init_t(lb_adj *a, double *dth0)
     return cudaGetLastError();
 }
 
+template <class L> cudaError_t seed_l(lb_adj *a, const double *dLdu)
+{
+    switch (a->ctx->precision) {
+    case LB_FX64: return seed_t<L, long long>(a, dLdu);
+    case LB_FP32_SHIFTED: return seed_t<L, float>(a, dLdu);
+    default: return seed_t<L, double>(a, dLdu);
+    }
+}
+
 cudaError_t do_seed(lb_adj *a, const double *dLdu)
 {
-    const bool fx = a->ctx->precision == LB_FX64;
     switch (a->ctx->d) {
-    case 1: return fx ? seed_t<lbk::D1Q3, long long>(a, dLdu) : seed_t<lbk::D1Q3, double>(a, dLdu);
-    case 2: return fx ? seed_t<lbk::D2Q9, long long>(a, dLdu) : seed_t<lbk::D2Q9, double>(a, dLdu);
-    default: return fx ? seed_t<lbk::D3Q19, long long>(a, dLdu) : seed_t<lbk::D3Q19, double>(a, dLdu);
+    case 1: return seed_l<lbk::D1Q3>(a, dLdu);
+    case 2: return seed_l<lbk::D2Q9>(a, dLdu);
+    default: return seed_l<lbk::D3Q19>(a, dLdu);
+    }
+}
+
+template <class L> cudaError_t step_l(lb_adj *a, const void *Pn)
+{
+    switch (a->ctx->precision) {
+    case LB_FX64: return step_t<L, long long>(a, Pn);
+    case LB_FP32_SHIFTED: return step_t<L, float>(a, Pn);
+    default: return step_t<L, double>(a, Pn);
     }
 }
 
 cudaError_t do_step(lb_adj *a, const void *Pn)
 {
-    const bool fx = a->ctx->precision == LB_FX64;
     switch (a->ctx->d) {
-    case 1: return fx ? step_t<lbk::D1Q3, long long>(a, Pn) : step_t<lbk::D1Q3, double>(a, Pn);
-    case 2: return fx ? step_t<lbk::D2Q9, long long>(a, Pn) : step_t<lbk::D2Q9, double>(a, Pn);
-    default: return fx ? step_t<lbk::D3Q19, long long>(a, Pn) : step_t<lbk::D3Q19, double>(a, Pn);
+    case 1: return step_l<lbk::D1Q3>(a, Pn);
+    case 2: return step_l<lbk::D2Q9>(a, Pn);
+    default: return step_l<lbk::D3Q19>(a, Pn);
     }
 }
 
@@ -503,10 +522,6 @@ lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_a
     if (!out) return LB_EINVAL;
     *out = nullptr;
     if (!ctx || T < 1) return LB_EINVAL;
-    if (ctx->precision == LB_FP32_SHIFTED) {
-        ctx->err = "lb_adjoint_create: the adjoint supports LB_FP64 and LB_FX64 contexts";
-        return LB_EINVAL;
-    }
     if (want_nu && !ctx->paper) {
         ctx->err = "lb_adjoint_create: dL/dnu needs the paper's relaxation set";
         return LB_EINVAL;
@@ -519,6 +534,9 @@ lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_a
     lb_adj *a = new (std::nothrow) lb_adj();
     if (!a) return LB_ENOMEM;
     a->ctx = ctx;
+    a->ag = ctx->geom;  // 64-node segments: two values per lane for every storage type
+    a->ag.seg_per_row = ctx->geom.pitch / 64;
+    a->ag.nseg = ctx->geom.rows * a->ag.seg_per_row;
     a->T = T;
     a->C = C;
     a->want_nu = want_nu != 0;
@@ -541,7 +559,7 @@ lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_a
     if (e == cudaSuccess) e = cudaMalloc(&a->th0, sizeof(double) * ctx->nodes);
     if (e == cudaSuccess) e = cudaMalloc(&a->grad, sizeof(double) * ctx->d * ctx->nodes);
     if (e == cudaSuccess) e = cudaMalloc(&a->h, sizeof(double) * ctx->d * ctx->nodes);
-    if (e == cudaSuccess) e = cudaMalloc(&a->slot_step, sizeof(double) * ctx->geom.nseg);
+    if (e == cudaSuccess) e = cudaMalloc(&a->slot_step, sizeof(double) * a->ag.nseg);
     if (e == cudaSuccess) e = cudaMalloc(&a->slot_init, sizeof(double) * a->nslot_init);
     if (e == cudaSuccess) e = cudaMalloc(&a->dsum, sizeof(double));
     a->bytes += 2 * pbytes + sizeof(double) * ctx->nodes * (1 + 2 * ctx->d);
@@ -596,7 +614,7 @@ lb_status lb_adjoint_seed(lb_adj *a, const double *dLdu)
         return afail(a, LB_ESTATE, "lb_adjoint_seed: run lb_adjoint_forward first (and do not step the context)");
     lb_ctx *c = a->ctx;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(a->slot_step, 0, sizeof(double) * c->geom.nseg, c->stream)) != cudaSuccess ||
+    if ((e = cudaMemsetAsync(a->slot_step, 0, sizeof(double) * a->ag.nseg, c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(a->slot_init, 0, sizeof(double) * a->nslot_init, c->stream)) != cudaSuccess)
         return acuda(a, e, "lb_adjoint_seed");
     a->pcur = 0;
@@ -632,7 +650,7 @@ lb_status lb_adjoint_result(lb_adj *a, double *dL_dtheta0, double *dL_dnu)
     if (e != cudaSuccess) return acuda(a, e, "lb_adjoint_result: init adjoint");
     if (dL_dnu) {
         if (!a->want_nu) return afail(a, LB_EINVAL, "lb_adjoint_result: dL/dnu was not requested");
-        lbk::sum_slots_kernel<<<1, 256, 0, c->stream>>>(a->slot_step, c->geom.nseg, a->slot_init, a->nslot_init,
+        lbk::sum_slots_kernel<<<1, 256, 0, c->stream>>>(a->slot_step, a->ag.nseg, a->slot_init, a->nslot_init,
                                                         a->dsum);
         double deps = 0.0;
         if ((e = cudaGetLastError()) != cudaSuccess ||

@@ -41,6 +41,12 @@ __device__ __forceinline__ void st_vec(float *p, const float (&a)[4])
 {
     *reinterpret_cast<float4 *>(p) = make_float4(a[0], a[1], a[2], a[3]);
 }
+__device__ __forceinline__ void ld_vec(const float *p, float (&a)[2])
+{
+    float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    a[0] = v.x;
+    a[1] = v.y;
+}
 __device__ __forceinline__ void ld_vec(const long long *p, long long (&a)[2])
 {
     longlong2 v = __ldg(reinterpret_cast<const longlong2 *>(p));
@@ -71,11 +77,9 @@ template <> __device__ __forceinline__ long long to_store<long long>(double v, d
 // lane (xb = x0 + V*lane).  Values for padding nodes are unspecified but
 // every access stays inside the row (the pitch is a multiple of 32*V).
 // Must be called by all 32 lanes of the warp together.
-template <typename T, int EX>
-__device__ __forceinline__ void pull_row(const T *__restrict__ row, int x0, int lane, int N0,
-                                         T (&out)[Vec<T>::V])
+template <typename T, int EX, int V = Vec<T>::V>
+__device__ __forceinline__ void pull_row(const T *__restrict__ row, int x0, int lane, int N0, T (&out)[V])
 {
-    constexpr int V = Vec<T>::V;
     const int xb = x0 + V * lane;
     T a[V];
     ld_vec(row + xb, a);
@@ -110,9 +114,9 @@ __device__ __forceinline__ void pull_row(const T *__restrict__ row, int x0, int 
 // population at a time (each shifted pull right after its load).  Used for
 // FP64 storage, whose sweep is bound by the FP64 pipe: the lower register
 // count keeps more warps resident to hide FP64 latency.
-template <class L, typename T>
-__device__ __forceinline__ void gather_interleaved(const T *__restrict__ src, const Geom &g, int64_t row, int x0, int lane,
-                                       T (&f)[L::Q][Vec<T>::V])
+template <class L, typename T, int V = Vec<T>::V>
+__device__ __forceinline__ void gather_interleaved(const T *__restrict__ src, const Geom &g, int64_t row, int x0,
+                                                   int lane, T (&f)[L::Q][V])
 {
     const int y = (int)(row % g.N1);
     const int z = (int)(row / g.N1);
@@ -122,7 +126,7 @@ __device__ __forceinline__ void gather_interleaved(const T *__restrict__ src, co
         const int ys = (ey == 0) ? y : wrapi(y - ey, g.N1);
         const int zs = (ez == 0) ? z : wrapi(z - ez, g.N2);
         const T *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
-        pull_row<T, ex>(rp, x0, lane, g.N0, f[i]);
+        pull_row<T, ex, V>(rp, x0, lane, g.N0, f[i]);
     });
 }
 
@@ -130,11 +134,10 @@ __device__ __forceinline__ void gather_interleaved(const T *__restrict__ src, co
 // the one halo scalar a warp edge needs, is issued before any shuffle
 // consumes a loaded value, so a warp has all q rows in flight at once.  Used
 // for the HBM-bound storage types (FP32, 64-bit fixed point).
-template <class L, typename T>
+template <class L, typename T, int V = Vec<T>::V>
 __device__ __forceinline__ void gather_two_phase(const T *__restrict__ src, const Geom &g, int64_t row, int x0,
-                                                 int lane, T (&f)[L::Q][Vec<T>::V])
+                                                 int lane, T (&f)[L::Q][V])
 {
-    constexpr int V = Vec<T>::V;
     const int y = (int)(row % g.N1);
     const int z = (int)(row / g.N1);
     const int xb = x0 + V * lane;
@@ -181,14 +184,14 @@ __device__ __forceinline__ void gather_two_phase(const T *__restrict__ src, cons
     });
 }
 
-template <class L, typename T>
+template <class L, typename T, int V = Vec<T>::V>
 __device__ __forceinline__ void gather(const T *__restrict__ src, const Geom &g, int64_t row, int x0, int lane,
-                                       T (&f)[L::Q][Vec<T>::V])
+                                       T (&f)[L::Q][V])
 {
     if constexpr (std::is_same<T, double>::value)
-        gather_interleaved<L, T>(src, g, row, x0, lane, f);
+        gather_interleaved<L, T, V>(src, g, row, x0, lane, f);
     else
-        gather_two_phase<L, T>(src, g, row, x0, lane, f);
+        gather_two_phase<L, T, V>(src, g, row, x0, lane, f);
 }
 
 // ---------------------------------------------------------------------------

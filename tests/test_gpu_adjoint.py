@@ -99,3 +99,18 @@ def test_autograd_function():
     assert float(loss.detach()) == pytest.approx(L, rel=1e-14)
     assert np.array_equal(theta0.grad.cpu().numpy(), g)
     assert float(nu_t.grad) == dnu
+
+
+@pytest.mark.parametrize("d,N,T", [(1, (100,), 37), (2, (70, 45), 23), (3, (20, 13, 9), 7)])
+def test_fp32_shifted_adjoint_tracks_fp64(d, N, T):
+    """FP32 shifted storage: the forward states carry float rounding, so the
+    gradient of the FP32 forward map differs from the FP64 one by the
+    relative size of that rounding in the velocity misfit (~1e-5 here); the
+    adjoint arithmetic itself is FP64."""
+    th0, ut, nu, dx, dt = _case(d, N, T, 60 + d)
+    L64, g64, dnu64 = _gpu_grad(d, N, nu, dx, dt, T, th0, ut, "fp64")
+    L32, g32, dnu32 = _gpu_grad(d, N, nu, dx, dt, T, th0, ut, "fp32s")
+    rel = np.max(np.abs(g32 - g64)) / np.max(np.abs(g64))
+    print("fp32s adjoint d=%d: dtheta0 rel %.2e, dnu rel %.2e, L rel %.2e" % (d, rel, abs(dnu32 / dnu64 - 1), abs(L32 / L64 - 1)))
+    assert rel <= 1e-3
+    assert dnu32 == pytest.approx(dnu64, rel=1e-3)
