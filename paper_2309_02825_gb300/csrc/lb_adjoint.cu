@@ -159,9 +159,11 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
             out[i][v] = (x < g.N0) ? s / th : 0.0;
         });
     }
-    double *dp = phi + row * g.pitch + x0 + V * lane;
+    if (x0 + V * lane < g.pitch) {  // lanes beyond the row only loaded
+        double *dp = phi + row * g.pitch + x0 + V * lane;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, out[i]);
+        for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, out[i]);
+    }
     acc = warp_sum(acc);
     if (lane == 0) slot[seg] += acc;
 }
@@ -206,9 +208,11 @@ __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const double *_
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) lam[i][v] = l[i];
     }
-    double *dp = phi_out + row * g.pitch + x0 + V * lane;
+    if (x0 + V * lane < g.pitch) {  // lanes beyond the row only loaded
+        double *dp = phi_out + row * g.pitch + x0 + V * lane;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, lam[i]);
+        for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, lam[i]);
+    }
     if constexpr (NU) {
         acc = warp_sum(acc);
         if (lane == 0) slot[seg] += acc;
@@ -535,23 +539,24 @@ lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_a
     if (!a) return LB_ENOMEM;
     a->ctx = ctx;
     a->ag = ctx->geom;  // 64-node segments: two values per lane for every storage type
-    a->ag.seg_per_row = ctx->geom.pitch / 64;
+    a->ag.seg_per_row = (ctx->geom.pitch + 63) / 64;
     a->ag.nseg = ctx->geom.rows * a->ag.seg_per_row;
     a->T = T;
     a->C = C;
     a->want_nu = want_nu != 0;
     a->state_bytes = (size_t)ctx->q * ctx->geom.slab * ctx->elem;
     cudaError_t e = cudaSuccess;
-    const size_t pbytes = (size_t)ctx->q * ctx->geom.slab * sizeof(double);
+    const size_t pbytes = ((size_t)ctx->q * ctx->geom.slab + lbk::kSlackElems) * sizeof(double);
+    const size_t sbytes = a->state_bytes + lbk::kSlackElems * ctx->elem;  // allocation incl. slack
     if (a->want_nu) {
         a->nck = (T + C - 1) / C;
         a->ck.assign(a->nck, nullptr);
         a->seg.assign(C, nullptr);
         for (auto &p : a->ck)
-            if (e == cudaSuccess) e = cudaMalloc(&p, a->state_bytes);
+            if (e == cudaSuccess) e = cudaMalloc(&p, sbytes);
         for (auto &p : a->seg)
-            if (e == cudaSuccess) e = cudaMalloc(&p, a->state_bytes);
-        a->bytes += (a->nck + C) * a->state_bytes;
+            if (e == cudaSuccess) e = cudaMalloc(&p, sbytes);
+        a->bytes += (a->nck + C) * sbytes;
     }
     for (auto &p : a->phi)
         if (e == cudaSuccess) e = cudaMalloc(&p, pbytes);

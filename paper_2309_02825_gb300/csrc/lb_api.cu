@@ -141,18 +141,10 @@ lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt, co
     // Layout.
     const int V = (precision == LB_FP32_SHIFTED) ? lbk::Vec<float>::V : lbk::Vec<double>::V;
     c->elem = (precision == LB_FP32_SHIFTED) ? 4 : 8;
-    lbk::Geom &g = c->geom;
-    g.N0 = (int)c->N[0];
-    g.N1 = (int)c->N[1];
-    g.N2 = (int)c->N[2];
-    const int segw = 32 * V;
-    g.pitch = (int)((c->N[0] + segw - 1) / segw * segw);
-    g.rows = c->N[1] * c->N[2];
-    g.slab = (int64_t)g.pitch * g.rows;
-    g.seg_per_row = g.pitch / segw;
-    g.nseg = g.rows * g.seg_per_row;
+    c->geom = lbk::make_geom(c->N[0], c->N[1], c->N[2], V);
+    const lbk::Geom &g = c->geom;
 
-    const size_t fbytes = (size_t)c->q * (size_t)g.slab * c->elem;
+    const size_t fbytes = ((size_t)c->q * (size_t)g.slab + lbk::kSlackElems) * c->elem;
     cudaError_t e;
     for (int b = 0; b < 2; ++b) {
         e = cudaMalloc(&c->f[b], fbytes);

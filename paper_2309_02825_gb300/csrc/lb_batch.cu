@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_sweep_kernel(const Ins
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) f[i][v] = n[i];
     }
+    if (x0 + V * lane >= D.g.pitch) return;  // beyond the row: loads only
     T *dp = d + row * D.g.pitch + x0 + V * lane;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * D.g.slab, f[i]);
@@ -371,16 +372,8 @@ lb_status lb_batch_create(int count, const int64_t *N, const double *nu, const d
             return LB_EINVAL;
         }
         c.elem = b->elem;
-        lbk::Geom &g = c.geom;
-        g.N0 = (int)n0;
-        g.N1 = (int)n1;
-        g.N2 = 1;
-        const int segw = 32 * V;
-        g.pitch = (int)((n0 + segw - 1) / segw * segw);
-        g.rows = n1;
-        g.slab = (int64_t)g.pitch * g.rows;
-        g.seg_per_row = g.pitch / segw;
-        g.nseg = g.rows * g.seg_per_row;
+        c.geom = lbk::make_geom(n0, n1, 1, V);
+        const lbk::Geom &g = c.geom;
         c.stream = b->stream;
         c.device = b->device;
         b->off[j] = off;
@@ -393,8 +386,9 @@ lb_status lb_batch_create(int count, const int64_t *N, const double *nu, const d
     b->total_nodes = noff;
     cudaError_t e;
     for (int k = 0; k < 2; ++k) {
-        if ((e = cudaMalloc(&b->buf[k], b->elem * (size_t)off)) != cudaSuccess ||
-            (e = cudaMemsetAsync(b->buf[k], 0, b->elem * (size_t)off, b->stream)) != cudaSuccess) {
+        const size_t bytes = b->elem * ((size_t)off + lbk::kSlackElems);
+        if ((e = cudaMalloc(&b->buf[k], bytes)) != cudaSuccess ||
+            (e = cudaMemsetAsync(b->buf[k], 0, bytes, b->stream)) != cudaSuccess) {
             free_batch(b);
             return e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA;
         }

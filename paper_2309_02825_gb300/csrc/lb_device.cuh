@@ -331,6 +331,7 @@ __global__ void __launch_bounds__(sweep_threads<T>()) sweep_kernel(const T *__re
         for (int i = 0; i < L::Q; ++i) f[i][v] = n[i];
     }
 
+    if (x0 + V * lane >= g.pitch) return;  // beyond the row: loads only
     T *dp = dst + row * g.pitch + x0 + V * lane;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, f[i]);

@@ -48,12 +48,32 @@ template <> struct Vec<long long> { using type = longlong2; static constexpr int
 // Grid geometry of one padded state array.
 struct Geom {
     int N0, N1, N2;      // sizes (N1 = N2 = 1 for missing axes)
-    int pitch;           // row pitch in elements, a multiple of 32*V
+    int pitch;           // row pitch in elements: N0 rounded up to one 16-byte vector
     int64_t slab;        // pitch*N1*N2: elements per population
     int64_t rows;        // N1*N2
-    int seg_per_row;     // pitch / (32*V)
+    int seg_per_row;     // ceil(pitch / (32*V)): warp segments per row
     int64_t nseg;        // rows * seg_per_row (one warp per segment)
 };
+
+// Lanes of a row's last segment may start at or beyond the pitch: they load
+// (harmless) values of the next row and never store.  Every state-shaped
+// allocation carries this many extra elements so those loads stay inside it.
+constexpr int64_t kSlackElems = 128;
+
+// Geometry for V values per lane (V = 16 bytes / element size).
+inline Geom make_geom(int64_t N0, int64_t N1, int64_t N2, int V)
+{
+    Geom g;
+    g.N0 = (int)N0;
+    g.N1 = (int)N1;
+    g.N2 = (int)N2;
+    g.pitch = (int)((N0 + V - 1) / V * V);
+    g.rows = N1 * N2;
+    g.slab = (int64_t)g.pitch * g.rows;
+    g.seg_per_row = (g.pitch + 32 * V - 1) / (32 * V);
+    g.nseg = g.rows * g.seg_per_row;
+    return g;
+}
 
 // Collision constants (lattice units), precomputed on the host from the
 // relaxation set.  With sigma = c_s^2/c^2 = 2 w1 + 4(d-1) wd the
