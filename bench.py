@@ -64,6 +64,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true", help="skip the batched 512-instance measurement")
     p.add_argument("--no-adjoint", action="store_true", help="skip the 512^2 adjoint measurement")
     p.add_argument("--no-3d", action="store_true", help="skip the 3D 256^3 sweep measurement")
+    p.add_argument("--no-4d", action="store_true", help="skip the 4D D4Q33 50^4 measurement")
     p.add_argument("--accuracy", action="store_true",
                    help="print the error-vs-exact convergence table (1D, 2D up to 4096^2, 3D up to 256^3) and exit")
     return p.parse_args()
@@ -529,6 +530,58 @@ def run_3d(local, peaks):
     return out
 
 
+def run_4d(local, peaks):
+    """The paper's Example 4 (D4Q33, periodic [-1,1]^4) at its finest printed
+    level: dx = 1/25 (50^4 nodes), dt = 1/250, t = 1 (250 steps), eps = 0.08.
+    Sweep throughput per precision, and the closed-node RMSE of the FX64 run
+    beside the values the paper prints in Table 4's last column."""
+    import torch
+    from paper_2309_02825_gb300 import lb
+    torch.cuda.set_device(local)
+    eps, dx, dt, steps = 0.08, 1.0 / 25, 1.0 / 250, 250
+    nu = eps * dx * dx / dt
+    N = (50,) * 4
+    prob = W.ProductSineProblem(4, nu, (1, 2, 3, 4), 2.0, 2.0, origin=-1.0)
+    stream = torch.cuda.Stream()
+    th0 = torch.from_numpy(prob.theta(N, dx)).cuda()
+    g0 = torch.from_numpy(np.ascontiguousarray(prob.grad(N, dx))).cuda()
+    nodes = 50 ** 4
+    out = {"workload": "4D D4Q33 periodic 50^4 (paper Example 4, dx=1/25, dt=1/250, eps=0.08, t=1)"}
+    for prec in ("fx64", "fp64", "fp32s"):
+        s = lb.Solver(4, N, nu, dx, dt, precision=prec, theta_ref=2.0, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            s.set_theta0(th0, g0)
+            s.step(5)
+            e0.record(stream)
+            s.step(20)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        elem = 4 if prec == "fp32s" else 8
+        gbs = 2 * 33 * elem * nodes / (ms / 1e3) / 1e9
+        entry = {"sweep_ms": ms, "mlups": nodes / (ms / 1e3) / 1e6, "bytes_per_lu": 2 * 33 * elem,
+                 "hbm_frac": gbs / peaks["hbm_gbs"]}
+        if prec == "fx64":
+            with torch.cuda.stream(stream):
+                s.set_theta0(th0, g0)
+                s.step(steps)
+                th, _, u = s.macros(want=("theta", "u"))
+            torch.cuda.synchronize()
+            closed = lambda a: np.pad(a, [(0, 1)] * a.ndim, mode="wrap")
+            rm = lambda a, b: float(np.sqrt(np.mean((closed(a) - closed(b)) ** 2)))
+            T = steps * dt
+            the, ue = prob.theta(N, dx, T), prob.u(N, dx, T)
+            thh, uh = th.cpu().numpy(), u.cpu().numpy()
+            entry["rmse_closed_nodes"] = {"theta": rm(thh, the),
+                                          **{"u_x%d" % (a + 1): rm(uh[a], ue[a]) for a in range(4)}}
+            entry["paper_table4_last_column"] = {"theta": 8.5486e-9, "u_x1": 1.5000e-9, "u_x2": 2.9646e-9,
+                                                 "u_x3": 4.2069e-9, "u_x4": 4.5931e-9}
+        s.close()
+        out[prec] = entry
+    return out
+
+
 def run_accuracy(local):
     """Error against the exact solution per grid size and precision, run to
     each family's end time; CR = log2 of successive RMSE ratios."""
@@ -647,6 +700,9 @@ def main():
     sweeps3d = None
     if not args.no_3d:
         sweeps3d = run_3d(local, peaks)
+    sweeps4d = None
+    if not args.no_4d:
+        sweeps4d = run_4d(local, peaks)
     base = None
     if rank == 0 and not args.no_cpu_baseline:
         base = cpu_baseline(args)
@@ -681,6 +737,8 @@ def main():
             line["adjoint"] = adjoint
         if sweeps3d:
             line["sweeps_3d"] = sweeps3d
+        if sweeps4d:
+            line["sweeps_4d"] = sweeps4d
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -7,7 +7,7 @@
  * velocity u is recovered through the Cole-Hopf map u = -2 nu grad(theta) /
  * theta (Eq. (transf)) from theta solving d(theta)/dt = nu lap(theta)
  * (Eq. (eq-theta)), which is advanced by the MRT-LB scheme of Sec. III.A on
- * the DdQ(1+2d^2) lattice (d = 1, 2, 3: D1Q3, D2Q9, D3Q19).
+ * the DdQ(1+2d^2) lattice (d = 1, 2, 3, 4: D1Q3, D2Q9, D3Q19, D4Q33).
  *
  * Conventions for every call:
  *  - Every call returns an lb_status; nothing aborts or throws across the
@@ -79,7 +79,7 @@ typedef struct {
 
 /*
  * Create a solver context.
- *   d        1, 2 or 3.
+ *   d        1, 2, 3 or 4.
  *   N        host array of d sizes, each >= 1 (a size of 1 makes that axis
  *            trivially periodic); N[0] <= 2^24, product <= 2^31.
  *   nu, dx, dt  viscosity, lattice spacing, time step (all > 0, finite);

@@ -526,6 +526,10 @@ lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_a
     if (!out) return LB_EINVAL;
     *out = nullptr;
     if (!ctx || T < 1) return LB_EINVAL;
+    if (ctx->d > 3) {
+        ctx->err = "lb_adjoint_create: the adjoint supports d = 1, 2, 3";
+        return LB_EINVAL;
+    }
     if (want_nu && !ctx->paper) {
         ctx->err = "lb_adjoint_create: dL/dnu needs the paper's relaxation set";
         return LB_EINVAL;

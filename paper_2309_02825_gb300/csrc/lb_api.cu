@@ -105,7 +105,7 @@ lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt, co
 {
     if (!out) return fail(nullptr, LB_EINVAL, "lb_create: out is NULL");
     *out = nullptr;
-    if (d < 1 || d > 3) return fail(nullptr, LB_EINVAL, "lb_create: d must be 1, 2 or 3");
+    if (d < 1 || d > 4) return fail(nullptr, LB_EINVAL, "lb_create: d must be 1, 2, 3 or 4");
     if (!N) return fail(nullptr, LB_EINVAL, "lb_create: N is NULL");
     if (!finite_pos(nu) || !finite_pos(dx) || !finite_pos(dt))
         return fail(nullptr, LB_EINVAL, "lb_create: nu, dx and dt must be finite and > 0");
@@ -122,7 +122,7 @@ lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt, co
     if (!c) return fail(nullptr, LB_ENOMEM, "lb_create: host allocation failed");
     c->d = d;
     c->q = 1 + 2 * d * d;
-    for (int a = 0; a < 3; ++a) c->N[a] = (a < d) ? N[a] : 1;
+    for (int a = 0; a < 4; ++a) c->N[a] = (a < d) ? N[a] : 1;
     c->nodes = nodes;
     c->precision = precision;
     c->nu = nu;
@@ -141,7 +141,7 @@ lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt, co
     // Layout.
     const int V = (precision == LB_FP32_SHIFTED) ? lbk::Vec<float>::V : lbk::Vec<double>::V;
     c->elem = (precision == LB_FP32_SHIFTED) ? 4 : 8;
-    c->geom = lbk::make_geom(c->N[0], c->N[1], c->N[2], V);
+    c->geom = lbk::make_geom(c->N[0], c->N[1], c->N[2], c->N[3], V);
     const lbk::Geom &g = c->geom;
 
     const size_t fbytes = ((size_t)c->q * (size_t)g.slab + lbk::kSlackElems) * c->elem;

@@ -360,6 +360,7 @@ lb_status lb_batch_create(int count, const int64_t *N, const double *nu, const d
         c.N[0] = n0;
         c.N[1] = n1;
         c.N[2] = 1;
+        c.N[3] = 1;
         c.nodes = n0 * n1;
         c.precision = precision;
         c.nu = nu[j];
@@ -372,7 +373,7 @@ lb_status lb_batch_create(int count, const int64_t *N, const double *nu, const d
             return LB_EINVAL;
         }
         c.elem = b->elem;
-        c.geom = lbk::make_geom(n0, n1, 1, V);
+        c.geom = lbk::make_geom(n0, n1, 1, 1, V);
         const lbk::Geom &g = c.geom;
         c.stream = b->stream;
         c.device = b->device;

@@ -110,6 +110,38 @@ __device__ __forceinline__ void pull_row(const T *__restrict__ row, int x0, int 
     }
 }
 
+// Row (y, z, w) of a flat row index, and the flat index of the row shifted
+// by -(ey, ez, ew) with periodic wrap.  For d <= 3, w = 0 and N3 = 1.
+struct RowPos {
+    int y, z, w;
+};
+template <int D> __device__ __forceinline__ RowPos row_pos(const Geom &g, int64_t row)
+{
+    RowPos r;
+    r.y = (int)(row % g.N1);
+    if constexpr (D <= 3) {
+        r.z = (int)(row / g.N1);
+        r.w = 0;
+    } else {
+        const int64_t r2 = row / g.N1;
+        r.z = (int)(r2 % g.N2);
+        r.w = (int)(r2 / g.N2);
+    }
+    return r;
+}
+template <int D, int EY, int EZ, int EW>
+__device__ __forceinline__ int64_t src_row(const Geom &g, const RowPos &r)
+{
+    const int ys = (EY == 0) ? r.y : wrapi(r.y - EY, g.N1);
+    const int zs = (EZ == 0) ? r.z : wrapi(r.z - EZ, g.N2);
+    if constexpr (D <= 3) {
+        return (int64_t)zs * g.N1 + ys;
+    } else {
+        const int ws = (EW == 0) ? r.w : wrapi(r.w - EW, g.N3);
+        return ((int64_t)ws * g.N2 + zs) * g.N1 + ys;
+    }
+}
+
 // Gather the pre-collision f(x, n) for the V nodes of this lane, one
 // population at a time (each shifted pull right after its load).  Used for
 // FP64 storage, whose sweep is bound by the FP64 pipe: the lower register
@@ -118,14 +150,11 @@ template <class L, typename T, int V = Vec<T>::V>
 __device__ __forceinline__ void gather_interleaved(const T *__restrict__ src, const Geom &g, int64_t row, int x0,
                                                    int lane, T (&f)[L::Q][V])
 {
-    const int y = (int)(row % g.N1);
-    const int z = (int)(row / g.N1);
+    const RowPos rpos = row_pos<L::D>(g, row);
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
-        const int ys = (ey == 0) ? y : wrapi(y - ey, g.N1);
-        const int zs = (ez == 0) ? z : wrapi(z - ez, g.N2);
-        const T *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
+        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2], ew = L::E[i][3];
+        const T *rp = src + (int64_t)i * g.slab + src_row<L::D, ey, ez, ew>(g, rpos) * g.pitch;
         pull_row<T, ex, V>(rp, x0, lane, g.N0, f[i]);
     });
 }
@@ -138,16 +167,13 @@ template <class L, typename T, int V = Vec<T>::V>
 __device__ __forceinline__ void gather_two_phase(const T *__restrict__ src, const Geom &g, int64_t row, int x0,
                                                  int lane, T (&f)[L::Q][V])
 {
-    const int y = (int)(row % g.N1);
-    const int z = (int)(row / g.N1);
+    const RowPos rpos = row_pos<L::D>(g, row);
     const int xb = x0 + V * lane;
     T halo[L::Q];
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
-        const int ys = (ey == 0) ? y : wrapi(y - ey, g.N1);
-        const int zs = (ez == 0) ? z : wrapi(z - ez, g.N2);
-        const T *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
+        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2], ew = L::E[i][3];
+        const T *rp = src + (int64_t)i * g.slab + src_row<L::D, ey, ez, ew>(g, rpos) * g.pitch;
         ld_vec(rp + xb, f[i]);
         halo[i] = T(0);
         if constexpr (ex == 1) {
@@ -159,7 +185,7 @@ __device__ __forceinline__ void gather_two_phase(const T *__restrict__ src, cons
     });
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
+        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2], ew = L::E[i][3];
         if constexpr (ex == 1) {
             T left = __shfl_up_sync(0xffffffffu, f[i][V - 1], 1);
             if (lane == 0) left = halo[i];
@@ -173,9 +199,7 @@ __device__ __forceinline__ void gather_two_phase(const T *__restrict__ src, cons
             for (int k = 0; k < V - 1; ++k) f[i][k] = f[i][k + 1];
             f[i][V - 1] = right;
             if (xb + V >= g.N0) {  // the node at x = N0 - 1 pulls from x = 0
-                const int ys = (ey == 0) ? y : wrapi(y - ey, g.N1);
-                const int zs = (ez == 0) ? z : wrapi(z - ez, g.N2);
-                const T *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
+                const T *rp = src + (int64_t)i * g.slab + src_row<L::D, ey, ez, ew>(g, rpos) * g.pitch;
 #pragma unroll
                 for (int k = 0; k < V; ++k)
                     if (xb + k + 1 == g.N0) f[i][k] = rp[0];
@@ -188,7 +212,8 @@ template <class L, typename T, int V = Vec<T>::V>
 __device__ __forceinline__ void gather(const T *__restrict__ src, const Geom &g, int64_t row, int x0, int lane,
                                        T (&f)[L::Q][V])
 {
-    if constexpr (std::is_same<T, double>::value)
+    // two-phase unless FP64 (FP64-pipe bound) or too many values to keep in flight
+    if constexpr (std::is_same<T, double>::value || L::Q * V > 80)
         gather_interleaved<L, T, V>(src, g, row, x0, lane, f);
     else
         gather_two_phase<L, T, V>(src, g, row, x0, lane, f);
@@ -293,6 +318,79 @@ __device__ __forceinline__ void collide(D3Q19, T *f, const Coll<T> &k)
         const T dp = fma(k.k3, yz.P, wth), dm = fma(-k.k3, yz.P, wth);
         f[15] = dp; f[17] = dp; f[16] = dm; f[18] = dm;
     }
+}
+
+// Coordinate pair p (a < b, lexicographic) of a D-dimensional lattice.
+template <int D> __host__ __device__ constexpr int pair_a(int p)
+{
+    int a = 0, n = D - 1;
+    while (p >= n) {
+        p -= n;
+        ++a;
+        --n;
+    }
+    return a;
+}
+template <int D> __host__ __device__ constexpr int pair_b(int p)
+{
+    int a = 0, n = D - 1;
+    while (p >= n) {
+        p -= n;
+        ++a;
+        --n;
+    }
+    return a + 1 + p;
+}
+
+// The same closed-form collision for any d (used for D4Q33): the pair
+// planes, axis sums and differences give theta, J_a, P_aa, P_ab.
+template <class L, typename T> __device__ __forceinline__ void collide_planes(T *f, const Coll<T> &k)
+{
+    constexpr int D = L::D, NP = D * (D - 1) / 2, B0 = 1 + 2 * D;
+    Plane<T> pl[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) pl[p] = plane(f[B0 + 4 * p], f[B0 + 4 * p + 1], f[B0 + 4 * p + 2], f[B0 + 4 * p + 3]);
+    T P[D], J[D];
+    T th = f[0];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        P[a] = f[1 + a] + f[1 + D + a];
+        J[a] = f[1 + a] - f[1 + D + a];
+        th += P[a];
+    }
+    static_for<0, NP>([&](auto Pi) {
+        constexpr int p = decltype(Pi)::value;
+        constexpr int a = pair_a<D>(p), b = pair_b<D>(p);
+        th += pl[p].F;
+        P[a] += pl[p].F;
+        P[b] += pl[p].F;
+        J[a] += pl[p].Ja;
+        J[b] += pl[p].Jb;
+    });
+    const T cth = k.cA * th, wth = k.wd * th;
+    T sumP = P[0];
+#pragma unroll
+    for (int a = 1; a < D; ++a) sumP += P[a];
+    f[0] = fma(-2 * k.k2, sumP, k.c0 * th);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const T A = fma(k.k2, P[a], cth), Bq = k.k1 * J[a];
+        f[1 + a] = A + Bq;
+        f[1 + D + a] = A - Bq;
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const T dp = fma(k.k3, pl[p].P, wth), dm = fma(-k.k3, pl[p].P, wth);
+        f[B0 + 4 * p] = dp;
+        f[B0 + 4 * p + 1] = dm;
+        f[B0 + 4 * p + 2] = dp;
+        f[B0 + 4 * p + 3] = dm;
+    }
+}
+
+template <typename T> __device__ __forceinline__ void collide(D4Q33, T *f, const Coll<T> &k)
+{
+    collide_planes<D4Q33, T>(f, k);
 }
 
 // ---------------------------------------------------------------------------

@@ -112,6 +112,52 @@ __device__ __forceinline__ void collide(D3Q19, long long *f, const CollFx &k)
     f[0] = th - 2 * (axis + diag);
 }
 
+// Any d (used for D4Q33): pair planes, exact integer moment sums, rounded
+// products, rest population = theta minus the others.
+__device__ __forceinline__ void collide(D4Q33, long long *f, const CollFx &k)
+{
+    constexpr int D = 4, NP = 6, B0 = 1 + 2 * D;
+    Plane<long long> pl[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) pl[p] = plane(f[B0 + 4 * p], f[B0 + 4 * p + 1], f[B0 + 4 * p + 2], f[B0 + 4 * p + 3]);
+    long long P[D], J[D];
+    long long th = f[0];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        P[a] = f[1 + a] + f[1 + D + a];
+        J[a] = f[1 + a] - f[1 + D + a];
+        th += P[a];
+    }
+    static_for<0, NP>([&](auto Pi) {
+        constexpr int p = decltype(Pi)::value;
+        constexpr int a = pair_a<D>(p), b = pair_b<D>(p);
+        th += pl[p].F;
+        P[a] += pl[p].F;
+        P[b] += pl[p].F;
+        J[a] += pl[p].Ja;
+        J[b] += pl[p].Jb;
+    });
+    const long long cth = mulfx(th, k.cA), wth = mulfx(th, k.wd);
+    long long rest = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const long long A = mulfx(P[a], k.k2) + cth, Bq = mulfx(J[a], k.k1);
+        f[1 + a] = A + Bq;
+        f[1 + D + a] = A - Bq;
+        rest += A;
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const long long Bq = mulfx(pl[p].P, k.k3), dp = wth + Bq, dm = wth - Bq;
+        f[B0 + 4 * p] = dp;
+        f[B0 + 4 * p + 1] = dm;
+        f[B0 + 4 * p + 2] = dp;
+        f[B0 + 4 * p + 3] = dm;
+        rest += dp + dm;
+    }
+    f[0] = th - 2 * rest;
+}
+
 // Recovery from exact integer moments, converted to FP64 once.
 template <class L>
 __global__ void __launch_bounds__(kSweepThreads) macros_fx_kernel(const long long *__restrict__ src, Geom g,
@@ -137,7 +183,7 @@ __global__ void __launch_bounds__(kSweepThreads) macros_fx_kernel(const long lon
         const int x = x0 + V * lane + v;
         if (x >= g.N0) continue;
         long long th = 0;
-        long long J[3] = {0, 0, 0};
+        long long J[4] = {0, 0, 0, 0};
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             const long long fv = f[i][v];
@@ -195,7 +241,8 @@ cudaError_t launch_sweep_fx(lb_ctx *c, const void *src, void *dst)
     switch (c->d) {
     case 1: return sweep_fx_t<D1Q3>(c, src, dst);
     case 2: return sweep_fx_t<D2Q9>(c, src, dst);
-    default: return sweep_fx_t<D3Q19>(c, src, dst);
+    case 3: return sweep_fx_t<D3Q19>(c, src, dst);
+    default: return sweep_fx_t<D4Q33>(c, src, dst);
     }
 }
 
@@ -216,7 +263,8 @@ cudaError_t launch_macros_fx(lb_ctx *c, const void *src, double *th, double *gr,
     switch (c->d) {
     case 1: return macros_fx_t<D1Q3>(c, src, th, gr, u, flag);
     case 2: return macros_fx_t<D2Q9>(c, src, th, gr, u, flag);
-    default: return macros_fx_t<D3Q19>(c, src, th, gr, u, flag);
+    case 3: return macros_fx_t<D3Q19>(c, src, th, gr, u, flag);
+    default: return macros_fx_t<D4Q33>(c, src, th, gr, u, flag);
     }
 }
 

@@ -19,24 +19,40 @@
 namespace lbk {
 
 // ---------------------------------------------------------------------------
-// Lattices DdQ(1+2d^2) for d = 1, 2, 3 in lattice units e_i = c_i / c, in
-// the order printed in Eqs. (d1q3), (d2q9) and (d3q19).
+// Lattices DdQ(1+2d^2) for d = 1..4 in lattice units e_i = c_i / c, in
+// the order printed in Eqs. (d1q3), (d2q9) and (d3q19); for d = 4 the
+// structure of Eq. (ddqq): rest, +e_p, -e_p, then for each coordinate pair
+// (a < b) the four velocities (e_a, e_b) = (1,1), (-1,1), (-1,-1), (1,-1).
+// Components beyond d are zero.
 // ---------------------------------------------------------------------------
 struct D1Q3 {
     static constexpr int D = 1, Q = 3;
-    static constexpr int E[Q][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}};
+    static constexpr int E[Q][4] = {{0, 0, 0, 0}, {1, 0, 0, 0}, {-1, 0, 0, 0}};
 };
 struct D2Q9 {
     static constexpr int D = 2, Q = 9;
-    static constexpr int E[Q][3] = {{0, 0, 0},  {1, 0, 0},  {0, 1, 0},   {-1, 0, 0}, {0, -1, 0},
-                                    {1, 1, 0},  {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+    static constexpr int E[Q][4] = {{0, 0, 0, 0}, {1, 0, 0, 0},  {0, 1, 0, 0},   {-1, 0, 0, 0}, {0, -1, 0, 0},
+                                    {1, 1, 0, 0}, {-1, 1, 0, 0}, {-1, -1, 0, 0}, {1, -1, 0, 0}};
 };
 struct D3Q19 {
     static constexpr int D = 3, Q = 19;
-    static constexpr int E[Q][3] = {
-        {0, 0, 0},   {1, 0, 0},  {0, 1, 0},   {0, 0, 1},  {-1, 0, 0}, {0, -1, 0}, {0, 0, -1},
-        {1, 1, 0},   {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {1, 0, 1},  {-1, 0, 1}, {-1, 0, -1},
-        {1, 0, -1},  {0, 1, 1},  {0, -1, 1},  {0, -1, -1}, {0, 1, -1}};
+    static constexpr int E[Q][4] = {
+        {0, 0, 0, 0},   {1, 0, 0, 0},  {0, 1, 0, 0},   {0, 0, 1, 0},   {-1, 0, 0, 0},  {0, -1, 0, 0}, {0, 0, -1, 0},
+        {1, 1, 0, 0},   {-1, 1, 0, 0}, {-1, -1, 0, 0}, {1, -1, 0, 0},  {1, 0, 1, 0},   {-1, 0, 1, 0}, {-1, 0, -1, 0},
+        {1, 0, -1, 0},  {0, 1, 1, 0},  {0, -1, 1, 0},  {0, -1, -1, 0}, {0, 1, -1, 0}};
+};
+struct D4Q33 {
+    static constexpr int D = 4, Q = 33;
+    static constexpr int E[Q][4] = {
+        {0, 0, 0, 0},
+        {1, 0, 0, 0},   {0, 1, 0, 0},   {0, 0, 1, 0},   {0, 0, 0, 1},
+        {-1, 0, 0, 0},  {0, -1, 0, 0},  {0, 0, -1, 0},  {0, 0, 0, -1},
+        {1, 1, 0, 0},   {-1, 1, 0, 0},  {-1, -1, 0, 0}, {1, -1, 0, 0},   // (x1, x2)
+        {1, 0, 1, 0},   {-1, 0, 1, 0},  {-1, 0, -1, 0}, {1, 0, -1, 0},   // (x1, x3)
+        {1, 0, 0, 1},   {-1, 0, 0, 1},  {-1, 0, 0, -1}, {1, 0, 0, -1},   // (x1, x4)
+        {0, 1, 1, 0},   {0, -1, 1, 0},  {0, -1, -1, 0}, {0, 1, -1, 0},   // (x2, x3)
+        {0, 1, 0, 1},   {0, -1, 0, 1},  {0, -1, 0, -1}, {0, 1, 0, -1},   // (x2, x4)
+        {0, 0, 1, 1},   {0, 0, -1, 1},  {0, 0, -1, -1}, {0, 0, 1, -1}};  // (x3, x4)
 };
 
 // Storage vector per thread: 16-byte loads/stores covering V consecutive x.
@@ -47,10 +63,10 @@ template <> struct Vec<long long> { using type = longlong2; static constexpr int
 
 // Grid geometry of one padded state array.
 struct Geom {
-    int N0, N1, N2;      // sizes (N1 = N2 = 1 for missing axes)
+    int N0, N1, N2, N3;  // sizes (1 for missing axes)
     int pitch;           // row pitch in elements: N0 rounded up to one 16-byte vector
     int64_t slab;        // pitch*N1*N2: elements per population
-    int64_t rows;        // N1*N2
+    int64_t rows;        // N1*N2*N3
     int seg_per_row;     // ceil(pitch / (32*V)): warp segments per row
     int64_t nseg;        // rows * seg_per_row (one warp per segment)
 };
@@ -61,14 +77,15 @@ struct Geom {
 constexpr int64_t kSlackElems = 128;
 
 // Geometry for V values per lane (V = 16 bytes / element size).
-inline Geom make_geom(int64_t N0, int64_t N1, int64_t N2, int V)
+inline Geom make_geom(int64_t N0, int64_t N1, int64_t N2, int64_t N3, int V)
 {
     Geom g;
     g.N0 = (int)N0;
     g.N1 = (int)N1;
     g.N2 = (int)N2;
+    g.N3 = (int)N3;
     g.pitch = (int)((N0 + V - 1) / V * V);
-    g.rows = N1 * N2;
+    g.rows = N1 * N2 * N3;
     g.slab = (int64_t)g.pitch * g.rows;
     g.seg_per_row = (g.pitch + 32 * V - 1) / (32 * V);
     g.nseg = g.rows * g.seg_per_row;
@@ -118,7 +135,7 @@ struct InitK {
 // ---------------------------------------------------------------------------
 struct lb_ctx {
     int d = 0, q = 0;
-    int64_t N[3] = {1, 1, 1};
+    int64_t N[4] = {1, 1, 1, 1};
     int64_t nodes = 0;
     int precision = LB_FP64;
     double nu = 0, dx = 0, dt = 0, c = 0, eps = 0, cs2 = 0, sigma = 0;

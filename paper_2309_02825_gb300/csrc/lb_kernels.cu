@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kSweepThreads) macros_kernel(const T *__restri
         const int x = x0 + V * lane + v;
         if (x >= g.N0) continue;
         double th = r.theta_ref;
-        double J[3] = {0.0, 0.0, 0.0};
+        double J[4] = {0.0, 0.0, 0.0, 0.0};
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             const double fv = (double)f[i][v];
@@ -83,7 +83,8 @@ __global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *
     const int x = (int)(node % g.N0);
     const int64_t rw = node / g.N0;
     const int y = (int)(rw % g.N1);
-    const int z = (int)(rw / g.N1);
+    const int z = (int)((rw / g.N1) % g.N2);
+    const int w = (int)(rw / ((int64_t)g.N1 * g.N2));
     {
         const double t0 = theta0[node];
         bool bad = !(t0 > 0.0) || !isfinite(t0);
@@ -91,23 +92,24 @@ __global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *
         for (int a = 0; a < L::D; ++a) bad |= !isfinite(grad[a * nodes + node]);
         if (bad) atomicOr(flag, 1);
     }
-    T *out = dst + ((int64_t)z * g.N1 + y) * g.pitch + x;
+    T *out = dst + (((int64_t)w * g.N2 + z) * g.N1 + y) * g.pitch + x;
     bool range = false;
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
+        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2], ew = L::E[i][3];
         const int xs = wrapi(x + ex, g.N0);
         const int ys = wrapi(y + ey, g.N1);
         const int zs = wrapi(z + ez, g.N2);
-        const int64_t src = ((int64_t)zs * g.N1 + ys) * g.N0 + xs;
+        const int ws = wrapi(w + ew, g.N3);
+        const int64_t src = (((int64_t)ws * g.N2 + zs) * g.N1 + ys) * g.N0 + xs;
         const double th = theta0[src];
         double val;
-        constexpr int nz = (ex != 0) + (ey != 0) + (ez != 0);
+        constexpr int nz = (ex != 0) + (ey != 0) + (ez != 0) + (ew != 0);
         if constexpr (nz == 0) {
             val = K.w0 * th;
         } else if constexpr (nz == 1) {
-            constexpr int a = (ex != 0) ? 0 : ((ey != 0) ? 1 : 2);
-            constexpr int s = (ex != 0) ? ex : ((ey != 0) ? ey : ez);
+            constexpr int a = (ex != 0) ? 0 : ((ey != 0) ? 1 : ((ez != 0) ? 2 : 3));
+            constexpr int s = (ex != 0) ? ex : ((ey != 0) ? ey : ((ez != 0) ? ez : ew));
             val = K.w1 * th - (double)s * K.iax * grad[a * nodes + src];
             val -= K.w1 * K.theta_ref;
         } else {
@@ -115,6 +117,7 @@ __global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *
             if constexpr (ex != 0) edg += (double)ex * grad[src];
             if constexpr (ey != 0) edg += (double)ey * grad[nodes + src];
             if constexpr (ez != 0) edg += (double)ez * grad[2 * nodes + src];
+            if constexpr (ew != 0) edg += (double)ew * grad[3 * nodes + src];
             val = K.wd * th - K.idg * edg;
             val -= K.wd * K.theta_ref;
         }
@@ -126,24 +129,27 @@ __global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *
 
 // Fourth-order central difference of theta along each axis (periodic).
 __global__ void fd4_kernel(const double *__restrict__ th, double *__restrict__ grad, int d, int N0, int N1,
-                           int N2, double inv12dx)
+                           int N2, int N3, double inv12dx)
 {
-    const int64_t nodes = (int64_t)N0 * N1 * N2;
+    const int64_t nodes = (int64_t)N0 * N1 * N2 * N3;
     const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= nodes) return;
-    const int x = (int)(node % N0);
-    const int64_t rw = node / N0;
-    const int y = (int)(rw % N1);
-    const int z = (int)(rw / N1);
-    const int n[3] = {N0, N1, N2};
+    int64_t rest = node;
+    const int x = (int)(rest % N0);
+    rest /= N0;
+    const int y = (int)(rest % N1);
+    rest /= N1;
+    const int z = (int)(rest % N2);
+    const int w = (int)(rest / N2);
+    const int n[4] = {N0, N1, N2, N3};
     for (int a = 0; a < d; ++a) {
         double acc = 0.0;
         const int off[4] = {2, 1, -1, -2};
         const double cof[4] = {-1.0, 8.0, -8.0, 1.0};
         for (int k = 0; k < 4; ++k) {
-            int c[3] = {x, y, z};
+            int c[4] = {x, y, z, w};
             c[a] = ((c[a] + off[k]) % n[a] + n[a]) % n[a];
-            acc += cof[k] * th[((int64_t)c[2] * N1 + c[1]) * N0 + c[0]];
+            acc += cof[k] * th[(((int64_t)c[3] * N2 + c[2]) * N1 + c[1]) * N0 + c[0]];
         }
         grad[a * nodes + node] = acc * inv12dx;
     }
@@ -312,7 +318,8 @@ cudaError_t launch_sweep(lb_ctx *c, const void *src, void *dst)
     switch (c->d) {
     case 1: return f64 ? sweep_t<D1Q3, double>(c, src, dst) : sweep_t<D1Q3, float>(c, src, dst);
     case 2: return f64 ? sweep_t<D2Q9, double>(c, src, dst) : sweep_t<D2Q9, float>(c, src, dst);
-    default: return f64 ? sweep_t<D3Q19, double>(c, src, dst) : sweep_t<D3Q19, float>(c, src, dst);
+    case 3: return f64 ? sweep_t<D3Q19, double>(c, src, dst) : sweep_t<D3Q19, float>(c, src, dst);
+    default: return f64 ? sweep_t<D4Q33, double>(c, src, dst) : sweep_t<D4Q33, float>(c, src, dst);
     }
 }
 
@@ -340,7 +347,8 @@ cudaError_t launch_macros(lb_ctx *c, const void *src, double *th, double *gr, do
     switch (c->d) {
     case 1: return f64 ? macros_t<D1Q3, double>(c, src, th, gr, u, flag) : macros_t<D1Q3, float>(c, src, th, gr, u, flag);
     case 2: return f64 ? macros_t<D2Q9, double>(c, src, th, gr, u, flag) : macros_t<D2Q9, float>(c, src, th, gr, u, flag);
-    default: return f64 ? macros_t<D3Q19, double>(c, src, th, gr, u, flag) : macros_t<D3Q19, float>(c, src, th, gr, u, flag);
+    case 3: return f64 ? macros_t<D3Q19, double>(c, src, th, gr, u, flag) : macros_t<D3Q19, float>(c, src, th, gr, u, flag);
+    default: return f64 ? macros_t<D4Q33, double>(c, src, th, gr, u, flag) : macros_t<D4Q33, float>(c, src, th, gr, u, flag);
     }
 }
 
@@ -348,7 +356,7 @@ cudaError_t launch_fd4_grad(const lb_ctx *c, const double *theta0, double *grad)
 {
     const int64_t nodes = c->nodes;
     fd4_kernel<<<(unsigned)((nodes + 255) / 256), 256, 0, c->stream>>>(
-        theta0, grad, c->d, (int)c->N[0], (int)c->N[1], (int)c->N[2], 1.0 / (12.0 * c->dx));
+        theta0, grad, c->d, (int)c->N[0], (int)c->N[1], (int)c->N[2], (int)c->N[3], 1.0 / (12.0 * c->dx));
     return cudaGetLastError();
 }
 
@@ -376,14 +384,16 @@ cudaError_t launch_init(lb_ctx *c, const double *theta0, const double *grad, int
         switch (c->d) {
         case 1: return init_t<D1Q3, long long>(c, theta0, grad, flag);
         case 2: return init_t<D2Q9, long long>(c, theta0, grad, flag);
-        default: return init_t<D3Q19, long long>(c, theta0, grad, flag);
+        case 3: return init_t<D3Q19, long long>(c, theta0, grad, flag);
+        default: return init_t<D4Q33, long long>(c, theta0, grad, flag);
         }
     }
     const bool f64 = c->precision == LB_FP64;
     switch (c->d) {
     case 1: return f64 ? init_t<D1Q3, double>(c, theta0, grad, flag) : init_t<D1Q3, float>(c, theta0, grad, flag);
     case 2: return f64 ? init_t<D2Q9, double>(c, theta0, grad, flag) : init_t<D2Q9, float>(c, theta0, grad, flag);
-    default: return f64 ? init_t<D3Q19, double>(c, theta0, grad, flag) : init_t<D3Q19, float>(c, theta0, grad, flag);
+    case 3: return f64 ? init_t<D3Q19, double>(c, theta0, grad, flag) : init_t<D3Q19, float>(c, theta0, grad, flag);
+    default: return f64 ? init_t<D4Q33, double>(c, theta0, grad, flag) : init_t<D4Q33, float>(c, theta0, grad, flag);
     }
 }
 
@@ -426,7 +436,8 @@ cudaError_t launch_norms(lb_ctx *c, const double *th, const double *u, const dou
     switch (c->d) {
     case 1: norms_kernel<1><<<nb, kRedThreads, 0, c->stream>>>(th, u, eth, eu, c->nodes, c->scratch); break;
     case 2: norms_kernel<2><<<nb, kRedThreads, 0, c->stream>>>(th, u, eth, eu, c->nodes, c->scratch); break;
-    default: norms_kernel<3><<<nb, kRedThreads, 0, c->stream>>>(th, u, eth, eu, c->nodes, c->scratch); break;
+    case 3: norms_kernel<3><<<nb, kRedThreads, 0, c->stream>>>(th, u, eth, eu, c->nodes, c->scratch); break;
+    default: norms_kernel<4><<<nb, kRedThreads, 0, c->stream>>>(th, u, eth, eu, c->nodes, c->scratch); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -42,7 +42,8 @@ def _run(d, N, nsteps, seed=21, theta_ref=1.5):
 
 
 CASES = [(1, (200,), 1), (1, (200,), 40), (2, (150, 70), 1), (2, (150, 70), 25), (2, (64, 64), 20),
-         (2, (3, 130), 6), (3, (140, 20, 9), 1), (3, (140, 20, 9), 12), (3, (5, 4, 3), 5)]
+         (2, (3, 130), 6), (3, (140, 20, 9), 1), (3, (140, 20, 9), 12), (3, (5, 4, 3), 5),
+         (4, (12, 7, 5, 4), 5)]
 
 
 @pytest.mark.parametrize("d,N,nsteps", CASES)

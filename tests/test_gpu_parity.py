@@ -83,6 +83,7 @@ CASES = [
     (2, (70, 45), 1), (2, (70, 45), 23), (2, (64, 64), 20), (2, (130, 3), 7), (2, (5, 33), 6), (2, (1, 9), 4),
     (2, (200, 17), 150),
     (3, (37, 22, 13), 1), (3, (37, 22, 13), 9), (3, (64, 16, 8), 16), (3, (3, 4, 5), 5), (3, (70, 1, 6), 4),
+    (4, (10, 8, 6, 5), 1), (4, (10, 8, 6, 5), 6), (4, (70, 3, 4, 2), 4), (4, (3, 4, 2, 5), 3),
 ]
 
 
@@ -179,7 +180,7 @@ def test_state_save_load_roundtrip():
 
 def test_invalid_inputs_are_reported():
     with pytest.raises(lb.LBError) as ei:
-        lb.Solver(4, (4, 4, 4, 4), 0.1, 0.1, 0.1)
+        lb.Solver(5, (4, 4, 4, 4, 4), 0.1, 0.1, 0.1)
     assert ei.value.status == lb.LB_EINVAL
     with pytest.raises(lb.LBError):
         lb.Solver(2, (8, 8), -1.0, 0.1, 0.1)
