@@ -67,6 +67,7 @@ def parse():
     p.add_argument("--no-4d", action="store_true", help="skip the 4D D4Q33 50^4 measurement")
     p.add_argument("--accuracy", action="store_true",
                    help="print the error-vs-exact convergence table (1D, 2D up to 4096^2, 3D up to 256^3) and exit")
+    p.add_argument("--accuracy-precisions", default="fp64,fx64,fp32s")
     return p.parse_args()
 
 
@@ -582,7 +583,7 @@ def run_4d(local, peaks):
     return out
 
 
-def run_accuracy(local):
+def run_accuracy(local, precisions=("fp64", "fx64", "fp32s")):
     """Error against the exact solution per grid size and precision, run to
     each family's end time; CR = log2 of successive RMSE ratios."""
     import torch
@@ -592,7 +593,7 @@ def run_accuracy(local):
     fams = [("1d_sine", W.sine_1d, (16, 32, 64, 128), 2.0), ("2d_sine", W.sine_2d, (64, 128, 256, 512, 1024, 2048, 4096), 2.0),
             ("3d_fourier", W.fourier_3d, (32, 64, 128, 256), 1.5)]
     for name, fam, Ns, tref in fams:
-        for prec in ("fp64", "fx64", "fp32s"):
+        for prec in precisions:
             rows, prev = [], None
             for N in Ns:
                 case = fam(N)
@@ -665,7 +666,7 @@ def main():
     world, rank, local = dist_setup(args)
     if args.accuracy:
         if rank == 0:
-            print(json.dumps({"accuracy": run_accuracy(local)}))
+            print(json.dumps({"accuracy": run_accuracy(local, tuple(args.accuracy_precisions.split(",")))}))
         return 0
     if world > 1:
         import torch

@@ -219,6 +219,13 @@ __device__ __forceinline__ void gather(const T *__restrict__ src, const Geom &g,
         gather_two_phase<L, T, V>(src, g, row, x0, lane, f);
 }
 
+// The rest population is formed as theta minus all the others when the
+// collision constants are rounded to float: the rounded c0, cA and wd do
+// not sum to exactly one, and the resulting factor (1 + O(2^-24)) on the
+// stored mass would compound step after step.  FP64 keeps the direct form
+// (one FP64 instruction fewer; its constants sum to 1 within 2^-53).
+template <typename T> constexpr bool kResidualRest = std::is_same<T, float>::value;
+
 // ---------------------------------------------------------------------------
 // Collision, in place on one node's q values.
 // ---------------------------------------------------------------------------
@@ -230,7 +237,10 @@ __device__ __forceinline__ void collide(D1Q3, T *f, const Coll<T> &k)
     const T J = f[1] - f[2];
     const T A = fma(k.k2, P, k.cA * th);
     const T B = k.k1 * J;
-    f[0] = fma(-2 * k.k2, P, k.c0 * th);
+    if constexpr (kResidualRest<T>)
+        f[0] = th - 2 * A;
+    else
+        f[0] = fma(-2 * k.k2, P, k.c0 * th);
     f[1] = A + B;
     f[2] = A - B;
 }
@@ -251,7 +261,10 @@ __device__ __forceinline__ void collide(D2Q9, T *f, const Coll<T> &k)
     const T Ay = fma(k.k2, Pyy, cth), By = k.k1 * Jy;
     const T wth = k.wd * th;
     const T dp = fma(k.k3, Pxy, wth), dm = fma(-k.k3, Pxy, wth);
-    f[0] = fma(-2 * k.k2, Pxx + Pyy, k.c0 * th);
+    if constexpr (kResidualRest<T>)
+        f[0] = th - 2 * ((Ax + Ay) + (dp + dm));
+    else
+        f[0] = fma(-2 * k.k2, Pxx + Pyy, k.c0 * th);
     f[1] = Ax + Bx;
     f[3] = Ax - Bx;
     f[2] = Ay + By;
@@ -290,34 +303,42 @@ __device__ __forceinline__ void collide(D3Q19, T *f, const Coll<T> &k)
     const T Jz = (f[3] - f[6]) + (xz.Jb + yz.Jb);
     const T cth = k.cA * th;
     const T wth = k.wd * th;
-    f[0] = fma(-2 * k.k2, (Pxx + Pyy) + Pzz, k.c0 * th);
+    T rest = T(0);
+    if constexpr (!kResidualRest<T>) f[0] = fma(-2 * k.k2, (Pxx + Pyy) + Pzz, k.c0 * th);
     {
         const T A = fma(k.k2, Pxx, cth), B = k.k1 * Jx;
         f[1] = A + B;
         f[4] = A - B;
+        rest += A;
     }
     {
         const T A = fma(k.k2, Pyy, cth), B = k.k1 * Jy;
         f[2] = A + B;
         f[5] = A - B;
+        rest += A;
     }
     {
         const T A = fma(k.k2, Pzz, cth), B = k.k1 * Jz;
         f[3] = A + B;
         f[6] = A - B;
+        rest += A;
     }
     {
         const T dp = fma(k.k3, xy.P, wth), dm = fma(-k.k3, xy.P, wth);
         f[7] = dp; f[9] = dp; f[8] = dm; f[10] = dm;
+        rest += dp + dm;
     }
     {
         const T dp = fma(k.k3, xz.P, wth), dm = fma(-k.k3, xz.P, wth);
         f[11] = dp; f[13] = dp; f[12] = dm; f[14] = dm;
+        rest += dp + dm;
     }
     {
         const T dp = fma(k.k3, yz.P, wth), dm = fma(-k.k3, yz.P, wth);
         f[15] = dp; f[17] = dp; f[16] = dm; f[18] = dm;
+        rest += dp + dm;
     }
+    if constexpr (kResidualRest<T>) f[0] = th - 2 * rest;
 }
 
 // Coordinate pair p (a < b, lexicographic) of a D-dimensional lattice.
@@ -371,12 +392,14 @@ template <class L, typename T> __device__ __forceinline__ void collide_planes(T 
     T sumP = P[0];
 #pragma unroll
     for (int a = 1; a < D; ++a) sumP += P[a];
-    f[0] = fma(-2 * k.k2, sumP, k.c0 * th);
+    T rest = T(0);
+    if constexpr (!kResidualRest<T>) f[0] = fma(-2 * k.k2, sumP, k.c0 * th);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const T A = fma(k.k2, P[a], cth), Bq = k.k1 * J[a];
         f[1 + a] = A + Bq;
         f[1 + D + a] = A - Bq;
+        rest += A;
     }
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
@@ -385,7 +408,9 @@ template <class L, typename T> __device__ __forceinline__ void collide_planes(T 
         f[B0 + 4 * p + 1] = dm;
         f[B0 + 4 * p + 2] = dp;
         f[B0 + 4 * p + 3] = dm;
+        rest += dp + dm;
     }
+    if constexpr (kResidualRest<T>) f[0] = th - 2 * rest;
 }
 
 template <typename T> __device__ __forceinline__ void collide(D4Q33, T *f, const Coll<T> &k)
