@@ -68,6 +68,8 @@ def parse():
     p.add_argument("--accuracy", action="store_true",
                    help="print the error-vs-exact convergence table (1D, 2D up to 4096^2, 3D up to 256^3) and exit")
     p.add_argument("--accuracy-precisions", default="fp64,fx64,fp32s")
+    p.add_argument("--profile-sweep", default=None, metavar="D,PREC,N,STEPS",
+                   help="run STEPS sweeps of one D-dimensional N^D grid at PREC and exit (for ncu captures)")
     return p.parse_args()
 
 
@@ -158,14 +160,32 @@ def dist_setup(args):
     return world, rank, local
 
 
-def barrier_max(t, world):
-    if world == 1:
-        return t
+def _reduce(v, op):
+    """All-reduce one float over the process group (CUDA tensor for NCCL,
+    CPU tensor for gloo)."""
     import torch
     import torch.distributed as dist
-    v = torch.tensor([t], dtype=torch.float64, device="cuda")
-    dist.all_reduce(v, op=dist.ReduceOp.MAX)
-    return float(v.item())
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
+
+
+def barrier_max(t, world):
+    """Slowest rank's time (the job finishes when the last replica does)."""
+    if world == 1:
+        return t
+    import torch.distributed as dist
+    return _reduce(t, dist.ReduceOp.MAX)
+
+
+def aggregate(units, seconds, world):
+    """Whole-job throughput of independent replicas: units summed over ranks
+    divided by the slowest rank's time."""
+    if world == 1:
+        return units / seconds
+    import torch.distributed as dist
+    return _reduce(units, dist.ReduceOp.SUM) / _reduce(seconds, dist.ReduceOp.MAX)
 
 
 # ---------------------------------------------------------------------------
@@ -233,13 +253,12 @@ def run_ours(args, precision, world, rank, local, peaks, with_e2e, label_main):
         t_end.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
-    elapsed = t_start.elapsed_time(t_end) / 1e3
-    elapsed = barrier_max(elapsed, world)
+    elapsed_local = t_start.elapsed_time(t_end) / 1e3
     sweep_ms = sum(a.elapsed_time(b) for a, b in zip(ev_s, ev_e)) / (args.steps * S)
 
     nodes = case.nodes
-    lups = nodes * S * args.steps * world
-    value = lups / elapsed / 1e6
+    value = aggregate(nodes * S * args.steps, elapsed_local, world) / 1e6
+    elapsed = barrier_max(elapsed_local, world)
     q = 9
     elem = 4 if precision == "fp32s" else 8
     bytes_lu = 2 * q * elem
@@ -318,10 +337,10 @@ def run_e2e(args, s, case, th0_h, g0_h, ex_t_h, ex_u_h, stream, world):
             one()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-    el = barrier_max(el, world)
+    value = aggregate(case.nodes * S * args.steps, el, world) / 1e6
     h2d = sum(h.numel() * h.element_size() for h in h_in)
     d2h = sum(h.numel() * h.element_size() for h in h_out)
-    return {"value": case.nodes * S * args.steps * world / el / 1e6, "unit": UNIT,
+    return {"value": value, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
@@ -364,11 +383,11 @@ def run_batched(local):
         ex_u = np.concatenate([np.ascontiguousarray(c.problem.u(c.N, c.dx, c.t_end)).ravel() for c in cases])
         err = b.errors(th, u, torch.from_numpy(ex_t).cuda(), torch.from_numpy(ex_u).cuda())
     sched = b.schedule()
-    base_steps = 100
+    base_steps = 20
     b.set_schedule(0.0, 256, False)
     t_base = timed(base_steps) * steps / base_steps
     b.set_schedule(1e18, 256, True)
-    t_flat = timed(base_steps * 2) * steps / (base_steps * 2)
+    t_flat = timed(base_steps * 10) * steps / (base_steps * 10)
     b.close()
     lu = nodes * steps
     return {
@@ -380,7 +399,7 @@ def run_batched(local):
         "autotune": choice,
         "one_launch_per_instance": {"aggregate_mlups": lu / t_base / 1e6, "instances_per_s": len(cases) / t_base,
                                     "sample_steps": base_steps},
-        "flat_one_group": {"aggregate_mlups": lu / t_flat / 1e6, "sample_steps": 2 * base_steps},
+        "flat_one_group": {"aggregate_mlups": lu / t_flat / 1e6, "sample_steps": 10 * base_steps},
         "speedup_vs_one_launch_per_instance": t_base / t_tuned,
         "u_rmse_max_over_instances": float(np.max(err[:, 1])),
         "theta_rmse_max_over_instances": float(np.max(err[:, 0])),
@@ -583,6 +602,30 @@ def run_4d(local, peaks):
     return out
 
 
+def run_profile_sweep(local, spec):
+    """Minimal, repeatable command for ncu: init + STEPS sweeps of one grid."""
+    import torch
+    from paper_2309_02825_gb300 import lb
+    torch.cuda.set_device(local)
+    d, prec, n, steps = spec.split(",")
+    d, n, steps = int(d), int(n), int(steps)
+    case = {1: W.sine_1d, 2: W.sine_2d, 3: W.fourier_3d}[d](n) if d <= 3 else None
+    if case is None:
+        dx, dt = 2.0 / n, (2.0 / n) ** 2 / 0.16
+        nu = 0.08 * dx * dx / dt
+        prob, N = W.ProductSineProblem(4, nu, (1, 2, 3, 4), 2.0, 2.0, origin=-1.0), (n,) * 4
+    else:
+        prob, N, nu, dx, dt = case.problem, case.N, case.nu, case.dx, case.dt
+    s = lb.Solver(d, N, nu, dx, dt, precision=prec, theta_ref=1.5)
+    s.set_theta0(torch.from_numpy(prob.theta(N, dx)).cuda(),
+                 torch.from_numpy(np.ascontiguousarray(prob.grad(N, dx))).cuda())
+    for _ in range(steps):
+        s.step(1)
+    torch.cuda.synchronize()
+    s.close()
+    print(json.dumps({"profile_sweep": spec, "ok": True}))
+
+
 def run_accuracy(local, precisions=("fp64", "fx64", "fp32s")):
     """Error against the exact solution per grid size and precision, run to
     each family's end time; CR = log2 of successive RMSE ratios."""
@@ -664,6 +707,9 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     world, rank, local = dist_setup(args)
+    if args.profile_sweep:
+        run_profile_sweep(local, args.profile_sweep)
+        return 0
     if args.accuracy:
         if rank == 0:
             print(json.dumps({"accuracy": run_accuracy(local, tuple(args.accuracy_precisions.split(",")))}))

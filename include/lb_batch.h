@@ -79,7 +79,8 @@ lb_status lb_batch_errors(lb_batch *b, const double *theta, const double *u, con
 
 /*
  * Autotuner: times `trial_steps` steps for each candidate (group byte budget
- * x block size) on this batch's real sizes and keeps the fastest.  Must be
+ * 48, 96, 128 MB or all instances in one group, x 128, 256 or 512 threads
+ * per block) on this batch's real sizes and keeps the fastest.  Must be
  * called before lb_batch_set_theta0 (it overwrites the state).  choice
  * (host, may be NULL) receives {budget_bytes, threads_per_block, groups,
  * microseconds per step of the winner}.  Synchronises the stream.

@@ -35,6 +35,8 @@ bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 void free_ctx(lb_ctx *c)
 {
     if (!c) return;
+    for (auto &g : c->graph)
+        if (g) cudaGraphExecDestroy(g);
     cudaFree(c->f[0]);
     cudaFree(c->f[1]);
     cudaFree(c->scratch);
@@ -56,6 +58,34 @@ struct DeviceGuard {
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
+
+constexpr int64_t kGraphSteps = 32;  // sweeps per recorded graph (even: parity unchanged)
+
+// Record kGraphSteps sweeps starting from buffer `from` on a private stream.
+cudaError_t record_sweeps(lb_ctx *c, int from)
+{
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaStream_t user = c->stream;
+    c->stream = cs;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        int p = from;
+        for (int64_t k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
+            e = lbk::launch_sweep(c, c->f[p], c->f[p ^ 1]);
+            p ^= 1;
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    c->stream = user;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph[from], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    return e;
+}
 
 }  // namespace
 
@@ -245,6 +275,19 @@ lb_status lb_step(lb_ctx *c, int64_t nsteps)
     if (nsteps < 0) return fail(c, LB_EINVAL, "lb_step: nsteps < 0");
     if (!c->initialized) return fail(c, LB_ESTATE, "lb_step: call lb_set_theta0 first");
     DeviceGuard dg(c);
+    // Long runs replay recorded 32-sweep graphs (one host call per 32 sweeps);
+    // while the caller's stream is being captured the sweeps are launched
+    // directly so that they land in the caller's graph.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
+    while (cap == cudaStreamCaptureStatusNone && nsteps >= kGraphSteps) {
+        cudaError_t e = cudaSuccess;
+        if (!c->graph[c->cur]) e = record_sweeps(c, c->cur);
+        if (e == cudaSuccess) e = cudaGraphLaunch(c->graph[c->cur], c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lb_step: graph");
+        nsteps -= kGraphSteps;
+        c->step += kGraphSteps;
+    }
     for (int64_t s = 0; s < nsteps; ++s) {
         cudaError_t e = lbk::launch_sweep(c, c->f[c->cur], c->f[c->cur ^ 1]);
         if (e != cudaSuccess) return cuda_fail(c, e, "lb_step: sweep launch");

@@ -152,6 +152,7 @@ struct lb_ctx {
     double *dout = nullptr;        // small device result area
     int *dflag = nullptr;          // device status flags
     double *gradtmp = nullptr;     // FD gradient when none is supplied
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // recorded sweeps, by starting buffer
     bool initialized = false;
     int64_t step = 0;
     int device = 0;

@@ -201,3 +201,47 @@ def test_invalid_inputs_are_reported():
     assert ei.value.status == lb.LB_ENONPOS
     with pytest.raises(ValueError):
         s.set_theta0(torch.ones(7, dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fx64", "fp32s"])
+def test_graph_replay_matches_direct_launches(precision):
+    """lb_step(70) replays two recorded 32-sweep graphs plus 6 launches; it must
+    equal 70 single-step calls bit for bit."""
+    d, N = 2, (70, 45)
+    prob, dx, dt = _problem(d, N, 13)
+    out = []
+    for chunks in ([70], [1] * 70):
+        s = lb.Solver(d, N, prob.nu, dx, dt, precision=precision, theta_ref=1.5)
+        s.set_theta0(_dev(prob.theta(N, dx)), _dev(prob.grad(N, dx)))
+        for c in chunks:
+            s.step(c)
+        assert s.nsteps == 70
+        out.append(s.macros())
+    torch.cuda.synchronize()
+    for a, b in zip(out[0], out[1]):
+        assert torch.equal(a, b)
+
+
+def test_steps_captured_into_a_caller_graph():
+    """While the caller captures its stream, lb_step launches directly so the
+    sweeps become part of the caller's CUDA graph; replaying it advances the
+    state exactly like direct stepping."""
+    d, N = 2, (64, 48)
+    prob, dx, dt = _problem(d, N, 19)
+    th0, g0 = _dev(prob.theta(N, dx)), _dev(prob.grad(N, dx))
+    ref = lb.Solver(d, N, prob.nu, dx, dt)
+    ref.set_theta0(th0, g0)
+    ref.step(40)
+    th_ref, _, u_ref = ref.macros()
+    cap = torch.cuda.Stream()
+    s = lb.Solver(d, N, prob.nu, dx, dt, stream=cap)
+    s.set_theta0(th0, g0)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cap):
+        s.step(40)  # even: the buffers return to the starting parity
+    g.replay()
+    torch.cuda.synchronize()
+    th, _, u = s.macros()
+    torch.cuda.synchronize()
+    assert torch.equal(th, th_ref) and torch.equal(u, u_ref)
