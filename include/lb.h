@@ -140,10 +140,13 @@ lb_status lb_get_step(const lb_ctx *ctx, int64_t *nsteps);
  *   theta = sum_k f_k,
  *   grad theta = -s1 sum_k c_k f^ne_k / (dt c_s^2)   (Eq. (nabla-theta)),
  *   u_a = (2 - s1) sum_k c_ka f^ne_k / sum_k f_k     (Eq. (ui-compute)).
- * All three are computed in FP64 (also for LB_FP32_SHIFTED).  Any output
- * pointer may be NULL to skip it.  Device outputs: theta (nodes), grad_theta
- * and u (d*nodes).  Asynchronous; a node with theta <= 0 or non-finite is
- * recorded and reported by the next lb_reduce as LB_ENONPOS.
+ * All three are computed in FP64 (also for LB_FP32_SHIFTED).  Each block
+ * stages its row segment of every population, with the one-node x-halo, in
+ * shared memory by bulk asynchronous copies (TMA) completing on an mbarrier.
+ * Any output pointer may be NULL to skip it.  Device outputs: theta (nodes),
+ * grad_theta and u (d*nodes).  Asynchronous; a node with theta <= 0 or
+ * non-finite is recorded and reported by the next lb_reduce as LB_ENONPOS,
+ * a staging wait that gave up (bounded at 1 s) as LB_ETIMEOUT.
  * Errors: LB_ESTATE, LB_ECUDA.
  */
 lb_status lb_macros(lb_ctx *ctx, double *theta, double *grad_theta, double *u);
@@ -215,6 +218,15 @@ lb_status lb_reduce_static(int d, int64_t nodes, const double *theta, const doub
 lb_status lb_state_layout(const lb_ctx *ctx, int64_t *pitch, int64_t *slab, int64_t *elem_bytes);
 lb_status lb_save_state(lb_ctx *ctx, void *buf);
 lb_status lb_load_state(lb_ctx *ctx, const void *buf, int64_t step);
+
+/*
+ * Self-test of the bounded waits used by the staged recovery: runs one block
+ * whose mbarrier phase is never completed and returns LB_ETIMEOUT once the
+ * bounded wait gives up after limit_s seconds (0 < limit_s <= 10), leaving
+ * the device usable; LB_OK would mean the wait was not bounded.  waited_s
+ * (host, may be NULL) receives the kernel's duration.  No paper counterpart.
+ */
+lb_status lb_selftest_staging_timeout(double limit_s, void *stream, double *waited_s);
 
 /* Message for the last failing call on ctx (or of lb_create, with ctx == NULL). */
 const char *lb_last_error(const lb_ctx *ctx);

@@ -357,6 +357,7 @@ lb_status lb_reduce(lb_ctx *c, const double *theta, const double *u, const doubl
         out[3 * v + 2] = have ? (sx > 0 ? sqrt(se / sx) : (se > 0 ? INFINITY : 0.0)) : NAN;
     }
     out[3 * (c->d + 1)] = raw[ns - 1];
+    if (flag & 4) return fail(c, LB_ETIMEOUT, "lb_macros: a shared-memory staging wait timed out");
     if (flag) return fail(c, LB_ENONPOS, "lb_macros saw theta <= 0 or non-finite");
     return LB_OK;
 }

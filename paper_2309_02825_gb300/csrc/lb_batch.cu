@@ -507,6 +507,7 @@ lb_status lb_batch_errors(lb_batch *b, const double *theta, const double *u, con
         e = cudaMemcpyAsync(&flag, b->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "lb_batch_errors");
+    if (flag & 4) return bfail(b, LB_ETIMEOUT, "lb_batch_macros: a shared-memory staging wait timed out");
     if (flag) return bfail(b, LB_ENONPOS, "lb_batch_macros saw theta <= 0");
     return LB_OK;
 }

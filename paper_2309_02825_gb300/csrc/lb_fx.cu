@@ -8,8 +8,8 @@
 // additions, each of the few products with a relaxation constant (held
 // with 62 fractional bits) is rounded to nearest once, and the rest
 // population is theta minus all others, which conserves sum theta exactly.
-// Recovery converts the exact integer moments to FP64 once, so
-// J = sum e f carries no cancellation error.
+// Recovery (lb_recover.cu) sums the exact integer moments and converts them
+// to FP64 once, so J = sum e f carries no cancellation error.
 #include "lb_device.cuh"
 
 namespace lbk {
@@ -158,58 +158,6 @@ __device__ __forceinline__ void collide(D4Q33, long long *f, const CollFx &k)
     f[0] = th - 2 * rest;
 }
 
-// Recovery from exact integer moments, converted to FP64 once.
-template <class L>
-__global__ void __launch_bounds__(kSweepThreads) macros_fx_kernel(const long long *__restrict__ src, Geom g,
-                                                                  Recov r, double inv_scale,
-                                                                  double *__restrict__ theta,
-                                                                  double *__restrict__ grad,
-                                                                  double *__restrict__ u, int *__restrict__ flag)
-{
-    constexpr int V = Vec<long long>::V;
-    const int lane = threadIdx.x & 31;
-    const int64_t seg = (int64_t)blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
-    if (seg >= g.nseg) return;
-    const int64_t row = seg / g.seg_per_row;
-    const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
-
-    long long f[L::Q][V];
-    gather<L, long long>(src, g, row, x0, lane, f);
-
-    const int64_t nodes = (int64_t)g.N0 * g.rows;
-    bool bad = false;
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        const int x = x0 + V * lane + v;
-        if (x >= g.N0) continue;
-        long long th = 0;
-        long long J[4] = {0, 0, 0, 0};
-        static_for<0, L::Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            const long long fv = f[i][v];
-            th += fv;
-            static_for<0, L::D>([&](auto A) {
-                constexpr int a = decltype(A)::value;
-                constexpr int e = L::E[i][a];
-                if constexpr (e == 1) J[a] += fv;
-                if constexpr (e == -1) J[a] -= fv;
-            });
-        });
-        const int64_t node = row * g.N0 + x;
-        const double thd = (double)th * inv_scale;
-        if (theta) theta[node] = thd;
-        if (th <= 0) bad = true;
-        const double inv = 1.0 / thd;
-#pragma unroll
-        for (int a = 0; a < L::D; ++a) {
-            const double Ja = (double)J[a] * inv_scale;
-            if (grad) grad[a * nodes + node] = r.gcoef * Ja;
-            if (u) u[a * nodes + node] = r.ucoef * Ja * inv;
-        }
-    }
-    if (bad) atomicOr(flag, 1);
-}
-
 static long long to_fx_coef(double v) { return llrint(ldexp(v, kFxCoefBits)); }
 
 static CollFx make_coll_fx(const lb_ctx *c)
@@ -224,8 +172,6 @@ static CollFx make_coll_fx(const lb_ctx *c)
     k.wd = to_fx_coef(wd);
     return k;
 }
-
-static int64_t blocks(const Geom &g) { return (g.nseg + kSweepThreads / 32 - 1) / (kSweepThreads / 32); }
 
 template <class L> static cudaError_t sweep_fx_t(lb_ctx *c, const void *src, void *dst)
 {
@@ -243,28 +189,6 @@ cudaError_t launch_sweep_fx(lb_ctx *c, const void *src, void *dst)
     case 2: return sweep_fx_t<D2Q9>(c, src, dst);
     case 3: return sweep_fx_t<D3Q19>(c, src, dst);
     default: return sweep_fx_t<D4Q33>(c, src, dst);
-    }
-}
-
-template <class L>
-static cudaError_t macros_fx_t(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
-{
-    Recov r;
-    r.ucoef = (2.0 - c->s1) * c->c;
-    r.gcoef = -c->s1 / (c->sigma * c->dx);
-    r.theta_ref = 0.0;
-    macros_fx_kernel<L><<<(unsigned)blocks(c->geom), kSweepThreads, 0, c->stream>>>(
-        (const long long *)src, c->geom, r, ldexp(1.0, -c->fx_bits), th, gr, u, flag);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_macros_fx(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
-{
-    switch (c->d) {
-    case 1: return macros_fx_t<D1Q3>(c, src, th, gr, u, flag);
-    case 2: return macros_fx_t<D2Q9>(c, src, th, gr, u, flag);
-    case 3: return macros_fx_t<D3Q19>(c, src, th, gr, u, flag);
-    default: return macros_fx_t<D4Q33>(c, src, th, gr, u, flag);
     }
 }
 

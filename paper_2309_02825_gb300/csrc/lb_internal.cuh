@@ -176,12 +176,12 @@ constexpr int kRedSlots = 16;  // doubles per block partial (>= 3*(d+1)+1)
 cudaError_t launch_fd4_grad(const lb_ctx *c, const double *theta0, double *grad);
 cudaError_t launch_init(lb_ctx *c, const double *theta0, const double *grad, int *flag);
 cudaError_t launch_sweep(lb_ctx *c, const void *src, void *dst);
+// Recovery (lb_recover.cu); flag bit 0: theta <= 0 seen, bit 2: a staging wait timed out.
 cudaError_t launch_macros(lb_ctx *c, const void *src, double *theta, double *grad, double *u, int *flag);
 cudaError_t launch_sum_state(lb_ctx *c, const void *src, double *out_dev);
 cudaError_t launch_maxabs(lb_ctx *c, const double *x, int64_t n, double *out_dev);
 // 64-bit fixed-point path (lb_fx.cu).
 cudaError_t launch_sweep_fx(lb_ctx *c, const void *src, void *dst);
-cudaError_t launch_macros_fx(lb_ctx *c, const void *src, double *theta, double *grad, double *u, int *flag);
 cudaError_t launch_norms(lb_ctx *c, const double *theta, const double *u, const double *ex_theta,
                          const double *ex_u, double *out_dev);
 

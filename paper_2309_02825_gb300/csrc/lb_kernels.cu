@@ -19,57 +19,6 @@
 namespace lbk {
 
 // ---------------------------------------------------------------------------
-// Recovery (Sec. III.C) from the pulled pre-collision f.
-// ---------------------------------------------------------------------------
-template <class L, typename T>
-__global__ void __launch_bounds__(kSweepThreads) macros_kernel(const T *__restrict__ src, Geom g, Recov r,
-                                                               double *__restrict__ theta,
-                                                               double *__restrict__ grad,
-                                                               double *__restrict__ u, int *__restrict__ flag)
-{
-    constexpr int V = Vec<T>::V;
-    const int lane = threadIdx.x & 31;
-    const int64_t seg = (int64_t)blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
-    if (seg >= g.nseg) return;
-    const int64_t row = seg / g.seg_per_row;
-    const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
-
-    T f[L::Q][V];
-    gather<L, T>(src, g, row, x0, lane, f);
-
-    const int64_t nodes = (int64_t)g.N0 * g.rows;
-    bool bad = false;
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        const int x = x0 + V * lane + v;
-        if (x >= g.N0) continue;
-        double th = r.theta_ref;
-        double J[4] = {0.0, 0.0, 0.0, 0.0};
-        static_for<0, L::Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            const double fv = (double)f[i][v];
-            th += fv;
-            static_for<0, L::D>([&](auto A) {
-                constexpr int a = decltype(A)::value;
-                constexpr int e = L::E[i][a];
-                if constexpr (e == 1) J[a] += fv;
-                if constexpr (e == -1) J[a] -= fv;
-            });
-        });
-        const int64_t node = row * g.N0 + x;
-        if (theta) theta[node] = th;
-        if (!(th > 0.0) || !isfinite(th)) bad = true;
-        const double inv = 1.0 / th;
-#pragma unroll
-        for (int a = 0; a < L::D; ++a) {
-            if (grad) grad[a * nodes + node] = r.gcoef * J[a];
-            if (u) u[a * nodes + node] = r.ucoef * J[a] * inv;
-        }
-    }
-    if (bad) atomicOr(flag, 1);
-}
-
-// ---------------------------------------------------------------------------
 // Initialisation, written in P form: P_0(y, i) = f_i(y + e_i, 0) with
 // f_i = w_i theta0 - dt [M^-1 S^-1 M Dbar f^eq]_i in closed form.
 // ---------------------------------------------------------------------------
@@ -300,7 +249,6 @@ template <typename T> Coll<T> make_coll(const lb_ctx &cc)
 template Coll<double> make_coll<double>(const lb_ctx &);
 template Coll<float> make_coll<float>(const lb_ctx &);
 
-static int64_t sweep_blocks(const Geom &g) { return (g.nseg + kSweepThreads / 32 - 1) / (kSweepThreads / 32); }
 
 template <class L, typename T> static cudaError_t sweep_t(lb_ctx *c, const void *src, void *dst)
 {
@@ -320,35 +268,6 @@ cudaError_t launch_sweep(lb_ctx *c, const void *src, void *dst)
     case 2: return f64 ? sweep_t<D2Q9, double>(c, src, dst) : sweep_t<D2Q9, float>(c, src, dst);
     case 3: return f64 ? sweep_t<D3Q19, double>(c, src, dst) : sweep_t<D3Q19, float>(c, src, dst);
     default: return f64 ? sweep_t<D4Q33, double>(c, src, dst) : sweep_t<D4Q33, float>(c, src, dst);
-    }
-}
-
-static Recov make_recov(const lb_ctx *c)
-{
-    Recov r;
-    r.ucoef = (2.0 - c->s1) * c->c;
-    r.gcoef = -c->s1 / (c->sigma * c->dx);
-    r.theta_ref = (c->precision == LB_FP32_SHIFTED) ? c->theta_ref : 0.0;
-    return r;
-}
-
-template <class L, typename T>
-static cudaError_t macros_t(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
-{
-    macros_kernel<L, T><<<(unsigned)sweep_blocks(c->geom), kSweepThreads, 0, c->stream>>>(
-        (const T *)src, c->geom, make_recov(c), th, gr, u, flag);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_macros(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
-{
-    if (c->precision == LB_FX64) return launch_macros_fx(c, src, th, gr, u, flag);
-    const bool f64 = c->precision == LB_FP64;
-    switch (c->d) {
-    case 1: return f64 ? macros_t<D1Q3, double>(c, src, th, gr, u, flag) : macros_t<D1Q3, float>(c, src, th, gr, u, flag);
-    case 2: return f64 ? macros_t<D2Q9, double>(c, src, th, gr, u, flag) : macros_t<D2Q9, float>(c, src, th, gr, u, flag);
-    case 3: return f64 ? macros_t<D3Q19, double>(c, src, th, gr, u, flag) : macros_t<D3Q19, float>(c, src, th, gr, u, flag);
-    default: return f64 ? macros_t<D4Q33, double>(c, src, th, gr, u, flag) : macros_t<D4Q33, float>(c, src, th, gr, u, flag);
     }
 }
 

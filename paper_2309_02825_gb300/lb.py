@@ -75,6 +75,7 @@ def load():
             "lb_load_state": ([vp, vp, i64], ctypes.c_int),
             "lb_last_error": ([vp], ctypes.c_char_p),
             "lb_reduce_static": ([ctypes.c_int, i64, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+            "lb_selftest_staging_timeout": ([dbl, vp, pd], ctypes.c_int),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -201,6 +202,14 @@ def lb_reduce_static(d, nodes, theta, u, exact_theta, exact_u, out, stream=None)
                               _ptr(out, "out"), _stream_handle(stream))
     if st != LB_OK:
         raise LBError(st, "lb_reduce_static")
+
+
+def lb_selftest_staging_timeout(limit_s=0.05, stream=None):
+    """(status, seconds waited) of the bounded-wait self-test (LB_ETIMEOUT expected)."""
+    lib = load()
+    w = ctypes.c_double()
+    st = lib.lb_selftest_staging_timeout(float(limit_s), _stream_handle(stream), ctypes.byref(w))
+    return st, w.value
 
 
 def lb_state_layout(ctx):
