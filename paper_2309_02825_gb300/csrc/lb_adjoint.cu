@@ -523,6 +523,7 @@ extern "C" {
 
 lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_adj **out)
 {
+    lbk::NvtxRange nvtx_range("lb_adjoint_create");
     if (!out) return LB_EINVAL;
     *out = nullptr;
     if (!ctx || T < 1) return LB_EINVAL;
@@ -590,6 +591,7 @@ lb_status lb_adjoint_destroy(lb_adj *a)
 
 lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, double *u)
 {
+    lbk::NvtxRange nvtx_range("lb_adjoint_forward");
     if (!a || !theta0) return LB_EINVAL;
     lb_ctx *c = a->ctx;
     a->forward_done = a->seeded = false;
@@ -618,6 +620,7 @@ lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, dou
 
 lb_status lb_adjoint_seed(lb_adj *a, const double *dLdu)
 {
+    lbk::NvtxRange nvtx_range("lb_adjoint_seed");
     if (!a || !dLdu) return LB_EINVAL;
     if (!a->forward_done || a->ctx->step != a->T)
         return afail(a, LB_ESTATE, "lb_adjoint_seed: run lb_adjoint_forward first (and do not step the context)");
@@ -635,6 +638,7 @@ lb_status lb_adjoint_seed(lb_adj *a, const double *dLdu)
 
 lb_status lb_adjoint_step(lb_adj *a, int64_t nsteps)
 {
+    lbk::NvtxRange nvtx_range("lb_adjoint_step");
     if (!a || nsteps < 0) return LB_EINVAL;
     if (!a->seeded) return afail(a, LB_ESTATE, "lb_adjoint_step: call lb_adjoint_seed first");
     if (a->done + nsteps > a->T) return afail(a, LB_EINVAL, "lb_adjoint_step: more reverse steps than forward");
@@ -652,6 +656,7 @@ lb_status lb_adjoint_step(lb_adj *a, int64_t nsteps)
 
 lb_status lb_adjoint_result(lb_adj *a, double *dL_dtheta0, double *dL_dnu)
 {
+    lbk::NvtxRange nvtx_range("lb_adjoint_result");
     if (!a || !dL_dtheta0) return LB_EINVAL;
     if (!a->seeded || a->done != a->T) return afail(a, LB_ESTATE, "lb_adjoint_result: reverse pass incomplete");
     lb_ctx *c = a->ctx;

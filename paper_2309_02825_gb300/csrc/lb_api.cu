@@ -133,6 +133,7 @@ extern "C" {
 lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt, const lb_relax *rs, int precision,
                     void *stream, lb_ctx **out)
 {
+    lbk::NvtxRange nvtx_range("lb_create");
     if (!out) return fail(nullptr, LB_EINVAL, "lb_create: out is NULL");
     *out = nullptr;
     if (d < 1 || d > 4) return fail(nullptr, LB_EINVAL, "lb_create: d must be 1, 2, 3 or 4");
@@ -204,6 +205,7 @@ lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt, co
 
 lb_status lb_destroy(lb_ctx *c)
 {
+    lbk::NvtxRange nvtx_range("lb_destroy");
     if (!c) return LB_OK;
     DeviceGuard dg(c);
     cudaStreamSynchronize(c->stream);
@@ -222,6 +224,7 @@ lb_status lb_get_params(const lb_ctx *c, double *out)
 
 lb_status lb_set_theta0(lb_ctx *c, const double *theta0, const double *grad)
 {
+    lbk::NvtxRange nvtx_range("lb_set_theta0");
     if (!c) return LB_EINVAL;
     if (!theta0) return fail(c, LB_EINVAL, "lb_set_theta0: theta0 is NULL");
     DeviceGuard dg(c);
@@ -271,6 +274,7 @@ lb_status lb_set_theta0(lb_ctx *c, const double *theta0, const double *grad)
 
 lb_status lb_step(lb_ctx *c, int64_t nsteps)
 {
+    lbk::NvtxRange nvtx_range("lb_step");
     if (!c) return LB_EINVAL;
     if (nsteps < 0) return fail(c, LB_EINVAL, "lb_step: nsteps < 0");
     if (!c->initialized) return fail(c, LB_ESTATE, "lb_step: call lb_set_theta0 first");
@@ -306,6 +310,7 @@ lb_status lb_get_step(const lb_ctx *c, int64_t *n)
 
 lb_status lb_macros(lb_ctx *c, double *theta, double *grad, double *u)
 {
+    lbk::NvtxRange nvtx_range("lb_macros");
     if (!c) return LB_EINVAL;
     if (!c->initialized) return fail(c, LB_ESTATE, "lb_macros: call lb_set_theta0 first");
     if (!theta && !grad && !u) return LB_OK;
@@ -317,6 +322,7 @@ lb_status lb_macros(lb_ctx *c, double *theta, double *grad, double *u)
 
 lb_status lb_sum_theta(lb_ctx *c, double *out)
 {
+    lbk::NvtxRange nvtx_range("lb_sum_theta");
     if (!c || !out) return LB_EINVAL;
     if (!c->initialized) return fail(c, LB_ESTATE, "lb_sum_theta: call lb_set_theta0 first");
     DeviceGuard dg(c);
@@ -333,6 +339,7 @@ lb_status lb_sum_theta(lb_ctx *c, double *out)
 lb_status lb_reduce(lb_ctx *c, const double *theta, const double *u, const double *ex_theta, const double *ex_u,
                     double *out)
 {
+    lbk::NvtxRange nvtx_range("lb_reduce");
     if (!c || !out) return LB_EINVAL;
     if (!theta || !ex_theta) return fail(c, LB_EINVAL, "lb_reduce: theta and exact_theta are required");
     if ((u == nullptr) != (ex_u == nullptr)) return fail(c, LB_EINVAL, "lb_reduce: u and exact_u go together");
@@ -373,6 +380,7 @@ lb_status lb_state_layout(const lb_ctx *c, int64_t *pitch, int64_t *slab, int64_
 
 lb_status lb_save_state(lb_ctx *c, void *buf)
 {
+    lbk::NvtxRange nvtx_range("lb_save_state");
     if (!c || !buf) return LB_EINVAL;
     if (!c->initialized) return fail(c, LB_ESTATE, "lb_save_state: nothing to save");
     DeviceGuard dg(c);
@@ -384,6 +392,7 @@ lb_status lb_save_state(lb_ctx *c, void *buf)
 
 lb_status lb_load_state(lb_ctx *c, const void *buf, int64_t step)
 {
+    lbk::NvtxRange nvtx_range("lb_load_state");
     if (!c || !buf || step < 0) return LB_EINVAL;
     DeviceGuard dg(c);
     cudaError_t e = cudaMemcpyAsync(c->f[c->cur], buf, (size_t)c->q * c->geom.slab * c->elem,

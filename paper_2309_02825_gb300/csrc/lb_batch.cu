@@ -331,6 +331,7 @@ extern "C" {
 lb_status lb_batch_create(int count, const int64_t *N, const double *nu, const double *dx, const double *dt,
                           const lb_relax *rs, int precision, void *stream, lb_batch **out)
 {
+    lbk::NvtxRange nvtx_range("lb_batch_create");
     if (!out) return LB_EINVAL;
     *out = nullptr;
     if (count < 1 || count > 65536 || !N || !nu || !dx || !dt) return LB_EINVAL;
@@ -438,6 +439,7 @@ lb_status lb_batch_set_theta_ref(lb_batch *b, const double *tr)
 
 lb_status lb_batch_set_theta0(lb_batch *b, const double *theta0, const double *grad0)
 {
+    lbk::NvtxRange nvtx_range("lb_batch_set_theta0");
     if (!b) return LB_EINVAL;
     if (!theta0) return bfail(b, LB_EINVAL, "lb_batch_set_theta0: theta0 is NULL");
     b->initialized = false;
@@ -470,6 +472,7 @@ lb_status lb_batch_set_theta0(lb_batch *b, const double *theta0, const double *g
 
 lb_status lb_batch_step(lb_batch *b, int64_t n)
 {
+    lbk::NvtxRange nvtx_range("lb_batch_step");
     if (!b) return LB_EINVAL;
     if (n < 0) return bfail(b, LB_EINVAL, "lb_batch_step: n < 0");
     if (!b->initialized) return bfail(b, LB_ESTATE, "lb_batch_step: call lb_batch_set_theta0 first");
@@ -480,6 +483,7 @@ lb_status lb_batch_step(lb_batch *b, int64_t n)
 
 lb_status lb_batch_macros(lb_batch *b, double *theta, double *u)
 {
+    lbk::NvtxRange nvtx_range("lb_batch_macros");
     if (!b) return LB_EINVAL;
     if (!b->initialized) return bfail(b, LB_ESTATE, "lb_batch_macros: call lb_batch_set_theta0 first");
     for (int j = 0; j < b->count; ++j) {
@@ -495,6 +499,7 @@ lb_status lb_batch_macros(lb_batch *b, double *theta, double *u)
 lb_status lb_batch_errors(lb_batch *b, const double *theta, const double *u, const double *eth, const double *eu,
                           double *out)
 {
+    lbk::NvtxRange nvtx_range("lb_batch_errors");
     if (!b || !theta || !eth || !out) return LB_EINVAL;
     if ((u == nullptr) != (eu == nullptr)) return bfail(b, LB_EINVAL, "lb_batch_errors: u and exact_u go together");
     lbk::batch_errors_kernel<<<b->count, lbk::kRedThreads, 0, b->stream>>>(b->d_node_off, theta, u, eth, eu,
@@ -514,6 +519,7 @@ lb_status lb_batch_errors(lb_batch *b, const double *theta, const double *u, con
 
 lb_status lb_batch_autotune(lb_batch *b, int trial_steps, double *choice)
 {
+    lbk::NvtxRange nvtx_range("lb_batch_autotune");
     if (!b || trial_steps < 2) return LB_EINVAL;
     // one instance per group is the naive baseline and never the fastest; it is
     // left out of the search (lb_batch_set_schedule can still select it)

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 #include <type_traits>
 
@@ -160,6 +162,15 @@ struct lb_ctx {
 };
 
 namespace lbk {
+
+// NVTX range over one ABI call (visible in Nsight timelines; no cost when no
+// tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Host-side derivation shared by every entry point (single grid and batch):
 // relaxation set (Theorem 2, Eq. (Bur-Sol), or the caller's), weights
