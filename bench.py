@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--no-adjoint", action="store_true", help="skip the 512^2 adjoint measurement")
     p.add_argument("--no-3d", action="store_true", help="skip the 3D 256^3 sweep measurement")
     p.add_argument("--no-4d", action="store_true", help="skip the 4D D4Q33 50^4 measurement")
+    p.add_argument("--no-walls", action="store_true", help="skip the mirror-wall measurements (Example 1)")
     p.add_argument("--accuracy", action="store_true",
                    help="print the error-vs-exact convergence table (1D, 2D up to 4096^2, 3D up to 256^3) and exit")
     p.add_argument("--accuracy-precisions", default="fp64,fx64,fp32s")
@@ -90,7 +91,7 @@ def profile_traffic(kernel_key):
     csrc = os.path.join(ROOT, "paper_2309_02825_gb300", "csrc")
     try:
         h = hashlib.sha256()
-        for name in ("lb_device.cuh", "lb_kernels.cu", "lb_fx.cu"):
+        for name in ("lb_internal.cuh", "lb_device.cuh", "lb_kernels.cu", "lb_fx.cu"):
             h.update(open(os.path.join(csrc, name), "rb").read())
         sha = h.hexdigest()[:16]
         path = os.path.join(ROOT, "profiles", "traffic.txt")
@@ -567,7 +568,69 @@ def run_3d(local, peaks):
         gbs = 2 * 19 * elem * case.nodes / (ms / 1e3) / 1e9
         err = _run_case(case, prec, 1.5, stream, th0, g0, exact=exact)
         out[prec] = {"sweep_ms": ms, "mlups": case.nodes / (ms / 1e3) / 1e6, "bytes_per_lu": 2 * 19 * elem,
-                     "hbm_frac": gbs / peaks["hbm_gbs"], "achieved_gbs": gbs, "error_t_end": err}
+                     "hbm_frac": gbs / peaks["hbm_gbs"], "achieved_gbs": gbs, "error_t_end": err,
+                     "traffic": profile_traffic("sweep_d3q19_%s_256" % prec)}
+    return out
+
+
+TABLE1 = {  # the paper's Table 1 (Example 1, t = 2): RMSE at levels 0..3, theta then u
+    0.5: ((7.8613e-4, 4.8926e-5, 3.0595e-6, 1.9139e-7), (1.9827e-5, 1.1821e-6, 7.2429e-8, 4.4865e-9)),
+    1.0: ((2.4232e-4, 1.5014e-5, 9.3770e-7, 5.8641e-8), (3.2184e-5, 2.0194e-6, 1.2608e-7, 7.8713e-9)),
+    1.5: ((2.3106e-4, 1.3918e-5, 8.6303e-7, 5.3874e-8), (1.0796e-4, 6.4468e-6, 3.9752e-7, 2.4739e-8)),
+    2.0: ((2.1330e-4, 1.2349e-5, 7.5838e-7, 4.7229e-8), (1.8574e-4, 1.0638e-5, 6.4967e-7, 4.0343e-8)),
+}
+
+
+def run_walls(local, peaks):
+    """Mirror walls: (1) the 2D FX64 sweep at 4096^2 with walls on both axes
+    beside the periodic one; (2) the paper's Example 1 (walls at x = 0, 1)
+    through the CUDA path, RMSE and CR per eps and level, with Table 1."""
+    import torch
+    from paper_2309_02825_gb300 import lb
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    out = {}
+    n = 4096
+    case = W.sine_2d(n)
+    N = (n, n)
+    th0 = torch.from_numpy(case.problem.theta(N, case.dx)).cuda()
+    g0 = torch.from_numpy(np.ascontiguousarray(case.problem.grad(N, case.dx))).cuda()
+    for kind in ("periodic", "mirror"):
+        s = lb.Solver(2, N, case.nu, case.dx, case.dt, precision="fx64", stream=stream, boundary=[kind, kind])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            s.set_theta0(th0, g0)
+            s.step(10)
+            e0.record(stream)
+            s.step(100)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 100
+        s.close()
+        gbs = 2 * 9 * 8 * n * n / (ms / 1e3) / 1e9
+        out["sweep_2d_4096_fx64_" + kind] = {"sweep_ms": ms, "mlups": n * n / (ms / 1e3) / 1e6,
+                                              "hbm_frac": gbs / peaks["hbm_gbs"]}
+    ex1 = {}
+    for eps in (0.5, 1.0, 1.5, 2.0):
+        rows = {"theta": [], "u": []}
+        for level in range(4):
+            c = W.wall_example1(eps, level)
+            p = c.problem
+            s = lb.Solver(1, c.N, c.nu, c.dx, c.dt, precision="fx64", stream=stream, boundary=["mirror"])
+            with torch.cuda.stream(stream):
+                s.set_theta0(torch.from_numpy(p.theta(c.N, c.dx)).cuda(),
+                             torch.from_numpy(np.ascontiguousarray(p.grad(c.N, c.dx))).cuda())
+                s.step(c.nsteps)
+                th, _, u = s.macros(want=("theta", "u"))
+            torch.cuda.synchronize()
+            T = c.t_end
+            rows["theta"].append(float(np.sqrt(np.mean((th.cpu().numpy() - p.theta(c.N, c.dx, T)) ** 2))))
+            rows["u"].append(float(np.sqrt(np.mean((u.cpu().numpy()[0] - p.u(c.N, c.dx, T)[0]) ** 2))))
+            s.close()
+        ex1[str(eps)] = {v: {"rmse": e, "cr": [math.log2(e[i] / e[i + 1]) for i in range(3)],
+                             "paper_table1": list(TABLE1[eps][k])} for k, (v, e) in enumerate(rows.items())}
+    out["example1"] = {"workload": "1D, walls at x = 0 and 1, u(x,0) = sin(pi x), t = 2, dx = 1/40/2^l, "
+                                   "dt = 1/100/4^l, fx64", "by_eps": ex1}
     return out
 
 
@@ -602,7 +665,7 @@ def run_4d(local, peaks):
         elem = 4 if prec == "fp32s" else 8
         gbs = 2 * 33 * elem * nodes / (ms / 1e3) / 1e9
         entry = {"sweep_ms": ms, "mlups": nodes / (ms / 1e3) / 1e6, "bytes_per_lu": 2 * 33 * elem,
-                 "hbm_frac": gbs / peaks["hbm_gbs"]}
+                 "hbm_frac": gbs / peaks["hbm_gbs"], "traffic": profile_traffic("sweep_d4q33_%s_50" % prec)}
         if prec == "fx64":
             with torch.cuda.stream(stream):
                 s.set_theta0(th0, g0)
@@ -784,6 +847,9 @@ def main():
     sweeps4d = None
     if not args.no_4d:
         sweeps4d = run_4d(local, peaks)
+    walls = None
+    if not args.no_walls:
+        walls = run_walls(local, peaks)
     base = None
     if rank == 0 and not args.no_cpu_baseline:
         base = cpu_baseline(args)
@@ -820,6 +886,8 @@ def main():
             line["sweeps_3d"] = sweeps3d
         if sweeps4d:
             line["sweeps_4d"] = sweeps4d
+        if walls:
+            line["walls"] = walls
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

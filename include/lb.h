@@ -106,6 +106,44 @@ lb_status lb_destroy(lb_ctx *ctx);
 lb_status lb_get_params(const lb_ctx *ctx, double *out);
 
 /*
+ * Boundary kind of one axis.  The paper's Examples 2-4 are periodic; its
+ * Example 1 (Sec. V) prescribes u = 0 at both ends of [0, 1], which under
+ * the Cole-Hopf transformation u = -2 nu grad theta / theta is the
+ * homogeneous Neumann condition d theta / dn = 0.  The paper does not state
+ * how its LB scheme imposes it; LB_MIRROR does it by specular reflection:
+ * the walls sit on the first and last node of the axis (N_a nodes span
+ * (N_a - 1) dx), and a population pulled from beyond a wall is read at the
+ * mirror image of its source node with its wall-normal velocity component
+ * negated.  The result equals, node for node, the periodic scheme on the
+ * grid doubled by even reflection across the walls, so the wall adds no
+ * error of its own (fourth order is kept), the normal component of u (and of
+ * grad theta) vanishes on wall nodes, and sum theta weighted 1/2 per wall a
+ * node lies on is conserved (exactly for LB_FX64).
+ */
+typedef enum {
+    LB_PERIODIC = 0,
+    LB_MIRROR = 1
+} lb_boundary;
+
+/*
+ * Set the boundary kind of each axis: kind is a host array of d values
+ * (LB_PERIODIC or LB_MIRROR; a new context is periodic on every axis).  A
+ * mirror axis needs N_a >= 3.  Synchronises the stream, drops recorded
+ * sweeps and leaves the context uninitialised: call lb_set_theta0 next.
+ * The initialisation reads theta0 and grad theta0 on the doubled grid:
+ * theta0 even across each wall, grad theta0's wall-normal component odd
+ * (so it is taken as zero on the wall nodes whatever the caller passes).
+ * lb_sum_theta returns the wall-weighted sum on such grids; the discrete
+ * adjoint (lb_adjoint.h) supports periodic grids only.
+ * Errors: LB_EINVAL (NULL kind, unknown kind, N_a < 3 on a mirror axis),
+ * LB_ECUDA.
+ */
+lb_status lb_set_boundary(lb_ctx *ctx, const int *kind);
+
+/* The boundary kind of each axis, written to kind[0..d-1] (host). */
+lb_status lb_get_boundary(const lb_ctx *ctx, int *kind);
+
+/*
  * Initialise the distributions from theta0 (Sec. IV: the first two terms of
  * Eq. (f-feq-o5)):  f_i(x, 0) = w_i theta0 - dt [M^-1 S^-1 M Dbar (w theta0)]_i
  * with Dbar = diag(c_i . grad).

@@ -18,7 +18,8 @@ Distributions are arrays of shape ``(q, N_{d-1}, ..., N_0)``.  Nodes sit at
 
 Parity status (each function is pinned in ``tests/test_oracle_*.py``):
 lattice, moment matrix, relaxation set, weights, initialisation, step,
-recovery and totals are all pinned; none is "parity unpinned".
+recovery, totals and the wall (mirror) model are all pinned; none is
+"parity unpinned".
 """
 
 from __future__ import annotations
@@ -255,6 +256,99 @@ class Model:
             raise MemoryError("oracle adjoint")
         p = self.params
         return float(L), g, de.value * p["dt"] / (p["dx"] * p["dx"])
+
+
+# --------------------------------------------------------------------------
+# Walls with zero normal velocity (Example 1 of Sec. V: u = 0 at both ends).
+# Under u = -2 nu grad theta / theta this is d theta / dn = 0, whose
+# solutions are the restrictions of periodic solutions that are even about
+# each wall.  The oracle therefore defines the scheme on a grid with walls as
+# the periodic scheme on the grid doubled by even reflection, restricted to
+# the original nodes: walls sit on the first and last node of a mirror axis
+# (N_a nodes span (N_a - 1) dx) and the doubled axis is periodic with
+# 2 (N_a - 1) nodes.
+# --------------------------------------------------------------------------
+
+def even_extension(a, d, mirror, vector=False):
+    """Extend a field from N_a to 2(N_a - 1) nodes on each mirror axis by
+    value(2(N_a - 1) - k) = value(k).  For a vector field (leading axis of
+    length d) the component along a reflected axis is odd: it changes sign
+    in the reflection and is zero on the wall nodes themselves."""
+    a = np.array(a, dtype=np.float64)
+    lead = 1 if vector else 0
+    for ax in range(d):
+        if not mirror[ax]:
+            continue
+        k = lead + (d - 1 - ax)  # array axis of grid axis ax (x is last)
+        n = a.shape[k]
+        if vector:
+            sl = [slice(None)] * a.ndim
+            sl[0] = ax
+            for j in (0, n - 1):
+                sl[k] = j
+                a[tuple(sl)] = 0.0
+        refl = np.flip(np.take(a, np.arange(1, n - 1), axis=k), axis=k)
+        if vector:
+            refl = refl.copy()
+            refl[ax] *= -1.0
+        a = np.concatenate([a, refl], axis=k)
+    return a
+
+
+def restrict(a, d, N, vector=False):
+    """The original N nodes of a field on the doubled grid."""
+    lead = 1 if vector else 0
+    idx = [slice(None)] * lead + [slice(0, n) for n in reversed(N)]
+    return np.ascontiguousarray(np.asarray(a)[tuple(idx)])
+
+
+class MirrorModel:
+    """The scheme on a grid whose axes ``mirror[a]`` have walls (the others
+    periodic): a periodic :class:`Model` on the doubled grid, with theta0 and
+    grad theta0 extended evenly (grad oddly along the wall normal) and the
+    recovered fields restricted.  Distributions live on the doubled grid."""
+
+    def __init__(self, d, N, mirror, nu, dx, dt, relax=None):
+        self.d = int(d)
+        self.N = tuple(int(n) for n in N)
+        self.mirror = tuple(bool(m) for m in mirror)
+        if len(self.N) != self.d or len(self.mirror) != self.d:
+            raise ValueError("N and mirror must have d entries")
+        if any(m and n < 3 for m, n in zip(self.mirror, self.N)):
+            raise ValueError("a mirror axis needs at least 3 nodes")
+        full = tuple(2 * (n - 1) if m else n for n, m in zip(self.N, self.mirror))
+        self.full = Model(self.d, full, nu, dx, dt, relax)
+        self.params, self.q = self.full.params, self.full.q
+
+    def initialize(self, theta0, grad0=None):
+        th = even_extension(theta0, self.d, self.mirror)
+        g = None if grad0 is None else even_extension(grad0, self.d, self.mirror, vector=True)
+        return self.full.initialize(th, g)
+
+    def run(self, f, nsteps):
+        return self.full.run(f, nsteps)
+
+    def recover(self, f):
+        th, g, u = self.full.recover(f)
+        return (restrict(th, self.d, self.N), restrict(g, self.d, self.N, True),
+                restrict(u, self.d, self.N, True))
+
+    def wall_weights(self):
+        """1/2 per wall a node lies on: the doubled grid holds every interior
+        node 2^k times (k mirror axes) and a wall node half as often."""
+        w = np.ones(tuple(reversed(self.N)))
+        for ax in range(self.d):
+            if self.mirror[ax]:
+                k = self.d - 1 - ax
+                sl = [slice(None)] * self.d
+                for j in (0, self.N[ax] - 1):
+                    sl[k] = j
+                    w[tuple(sl)] *= 0.5
+        return w
+
+    def total(self, f) -> float:
+        """Wall-weighted sum of theta = (sum over the doubled grid) / 2^k."""
+        return self.full.total(f) / 2.0 ** sum(self.mirror)
 
 
 # --------------------------------------------------------------------------

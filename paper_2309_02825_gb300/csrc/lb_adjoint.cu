@@ -52,7 +52,7 @@ __device__ __forceinline__ void gather_rev(const double *__restrict__ src, const
         const int ys = (ey == 0) ? y : wrapi(y + ey, g.N1);
         const int zs = (ez == 0) ? z : wrapi(z + ez, g.N2);
         const double *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
-        pull_row<double, -ex>(rp, x0, lane, g.N0, f[i]);
+        pull_row<double, -ex>(rp, x0, lane, g.N0, f[i], rp, g.N0 - 1, 0);
     });
 }
 
@@ -535,6 +535,10 @@ lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_a
         ctx->err = "lb_adjoint_create: dL/dnu needs the paper's relaxation set";
         return LB_EINVAL;
     }
+    if (ctx->geom.mirror) {
+        ctx->err = "lb_adjoint_create: the adjoint supports periodic grids only";
+        return LB_EINVAL;
+    }
     if (C == 0) C = (int64_t)ceil(sqrt((double)T));
     if (C < 1 || C > T) {
         ctx->err = "lb_adjoint_create: checkpoint interval out of range";
@@ -594,6 +598,10 @@ lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, dou
     lbk::NvtxRange nvtx_range("lb_adjoint_forward");
     if (!a || !theta0) return LB_EINVAL;
     lb_ctx *c = a->ctx;
+    if (c->geom.mirror) {
+        c->err = "lb_adjoint_forward: the adjoint supports periodic grids only";
+        return LB_EINVAL;
+    }
     a->forward_done = a->seeded = false;
     a->seg_loaded = -1;
     lb_status st = lb_set_theta0(c, theta0, nullptr);  // FD4 gradient: a function of theta0 alone

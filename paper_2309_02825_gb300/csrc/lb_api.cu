@@ -172,7 +172,8 @@ lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt, co
     // Layout.
     const int V = (precision == LB_FP32_SHIFTED) ? lbk::Vec<float>::V : lbk::Vec<double>::V;
     c->elem = (precision == LB_FP32_SHIFTED) ? 4 : 8;
-    c->geom = lbk::make_geom(c->N[0], c->N[1], c->N[2], c->N[3], V);
+    const int W = lbk::lane_width(c->d, c->elem, precision == LB_FP64);
+    c->geom = lbk::make_geom(c->N[0], c->N[1], c->N[2], c->N[3], V, W);
     const lbk::Geom &g = c->geom;
 
     const size_t fbytes = ((size_t)c->q * (size_t)g.slab + lbk::kSlackElems) * c->elem;
@@ -219,6 +220,41 @@ lb_status lb_get_params(const lb_ctx *c, double *out)
     const double v[15] = {c->eps, c->c,  c->cs2, c->s1, c->s2x, c->s22,       c->w0,       c->w1,
                           c->wd,  c->nu, c->dx,  c->dt, (double)c->q, c->theta_ref, (double)c->fx_bits};
     memcpy(out, v, sizeof v);
+    return LB_OK;
+}
+
+lb_status lb_set_boundary(lb_ctx *c, const int *kind)
+{
+    lbk::NvtxRange nvtx_range("lb_set_boundary");
+    if (!c) return LB_EINVAL;
+    if (!kind) return fail(c, LB_EINVAL, "lb_set_boundary: kind is NULL");
+    unsigned mask = 0;
+    for (int a = 0; a < c->d; ++a) {
+        if (kind[a] != LB_PERIODIC && kind[a] != LB_MIRROR)
+            return fail(c, LB_EINVAL, "lb_set_boundary: kind must be LB_PERIODIC or LB_MIRROR");
+        if (kind[a] == LB_MIRROR) {
+            if (c->N[a] < 3) return fail(c, LB_EINVAL, "lb_set_boundary: a mirror axis needs at least 3 nodes");
+            mask |= 1u << a;
+        }
+    }
+    DeviceGuard dg(c);
+    // recorded sweeps hold the old geometry; drain the stream before dropping them
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lb_set_boundary");
+    for (auto &g : c->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    c->geom.mirror = mask;
+    c->initialized = false;  // the stored state follows the old walls: initialise again
+    return LB_OK;
+}
+
+lb_status lb_get_boundary(const lb_ctx *c, int *kind)
+{
+    if (!c || !kind) return LB_EINVAL;
+    for (int a = 0; a < c->d; ++a) kind[a] = ((c->geom.mirror >> a) & 1u) ? LB_MIRROR : LB_PERIODIC;
     return LB_OK;
 }
 
@@ -331,7 +367,12 @@ lb_status lb_sum_theta(lb_ctx *c, double *out)
     if (e == cudaSuccess) e = cudaMemcpyAsync(&v, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lb_sum_theta");
-    if (c->precision == LB_FP32_SHIFTED) v += c->theta_ref * (double)c->nodes;
+    if (c->precision == LB_FP32_SHIFTED) {
+        // sum of the node weights: N_a per periodic axis, N_a - 1 per mirror axis
+        double wn = 1.0;
+        for (int a = 0; a < c->d; ++a) wn *= (double)(((c->geom.mirror >> a) & 1u) ? c->N[a] - 1 : c->N[a]);
+        v += c->theta_ref * wn;
+    }
     *out = v;
     return LB_OK;
 }

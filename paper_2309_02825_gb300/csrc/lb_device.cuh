@@ -33,6 +33,12 @@ __device__ __forceinline__ void ld_vec(const float *p, float (&a)[4])
     a[2] = v.z;
     a[3] = v.w;
 }
+template <typename T> __device__ __forceinline__ void ld_vec(const T *p, T (&a)[1]) { a[0] = __ldg(p); }
+template <typename T> __device__ __forceinline__ void st_vec(T *p, const T (&a)[1]) { *p = a[0]; }
+__device__ __forceinline__ void st_vec(float *p, const float (&a)[2])
+{
+    *reinterpret_cast<float2 *>(p) = make_float2(a[0], a[1]);
+}
 __device__ __forceinline__ void st_vec(double *p, const double (&a)[2])
 {
     *reinterpret_cast<double2 *>(p) = make_double2(a[0], a[1]);
@@ -58,6 +64,13 @@ __device__ __forceinline__ void st_vec(long long *p, const long long (&a)[2])
     *reinterpret_cast<longlong2 *>(p) = make_longlong2(a[0], a[1]);
 }
 
+// round(a * k / 2^62) for a fixed-point value a and a 62-fraction-bit constant k.
+__device__ __forceinline__ long long mulfx(long long a, long long k)
+{
+    const __int128 p = (__int128)a * (__int128)k;
+    return (long long)((p + ((__int128)1 << (kFxCoefBits - 1))) >> kFxCoefBits);
+}
+
 // Conversion of an FP64 value to the storage type (64-bit fixed point uses
 // round-to-nearest of v * 2^F).  `range` is set when a fixed-point value
 // would exceed 2^61 (4x the largest theta0), leaving the sums their headroom.
@@ -74,11 +87,15 @@ template <> __device__ __forceinline__ long long to_store<long long>(double v, d
 
 // Pull V consecutive values of one population along x with shift EX:
 // out[k] = row[(xb + k - EX) mod N0] for the valid nodes xb + k < N0 of this
-// lane (xb = x0 + V*lane).  Values for padding nodes are unspecified but
-// every access stays inside the row (the pitch is a multiple of 32*V).
+// lane (xb = x0 + V*lane).  Values for padding nodes are unspecified; loads
+// past the pitch fall into the next row or the allocation's slack.
+// The node x = 0 (EX = 1) reads wrow[wlo] and x = N0 - 1 (EX = -1) reads
+// wrow[whi]: the same row at N0 - 1 and 0 when x is periodic, the
+// x-reflected population at 1 and N0 - 2 when x has mirror walls.
 // Must be called by all 32 lanes of the warp together.
 template <typename T, int EX, int V = Vec<T>::V>
-__device__ __forceinline__ void pull_row(const T *__restrict__ row, int x0, int lane, int N0, T (&out)[V])
+__device__ __forceinline__ void pull_row(const T *__restrict__ row, int x0, int lane, int N0, T (&out)[V],
+                                         const T *__restrict__ wrow, int wlo, int whi)
 {
     const int xb = x0 + V * lane;
     T a[V];
@@ -88,7 +105,7 @@ __device__ __forceinline__ void pull_row(const T *__restrict__ row, int x0, int 
         for (int k = 0; k < V; ++k) out[k] = a[k];
     } else if constexpr (EX == 1) {
         T left = __shfl_up_sync(0xffffffffu, a[V - 1], 1);
-        if (lane == 0) left = row[xb == 0 ? N0 - 1 : xb - 1];
+        if (lane == 0) left = (row == wrow) ? row[xb == 0 ? wlo : xb - 1] : (xb == 0 ? wrow[wlo] : row[xb - 1]);
         out[0] = left;
 #pragma unroll
         for (int k = 1; k < V; ++k) out[k] = a[k - 1];
@@ -102,7 +119,7 @@ __device__ __forceinline__ void pull_row(const T *__restrict__ row, int x0, int 
             for (int k = 0; k < V; ++k) {
                 const int x = xb + k;
                 if (x + 1 == N0)
-                    out[k] = row[0];
+                    out[k] = wrow[whi];
                 else if (k == V - 1 && lane == 31 && x + 1 < N0)
                     out[k] = row[x + 1];
             }
@@ -142,20 +159,86 @@ __device__ __forceinline__ int64_t src_row(const Geom &g, const RowPos &r)
     }
 }
 
+// Source coordinate c - E on an axis of n nodes: periodic wrap, or, with
+// mirror walls on nodes 0 and n - 1, reflection of -1 to 1 and of n to
+// n - 2, recording the reflection in bit `bit` of m.
+template <int E>
+__device__ __forceinline__ int src_coord(int c, int n, bool mir, int &m, int bit)
+{
+    if constexpr (E == 0) {
+        return c;
+    } else {
+        const int s = c - E;
+        if (s >= 0 && s < n) return s;
+        if (!mir) return s < 0 ? s + n : s - n;
+        m |= bit;
+        return s < 0 ? 1 : n - 2;
+    }
+}
+
+// Where the pull f_i(x) = P_i(x - e_i) reads population I for target row r.
+// Periodic grids: the shifted row, population I.  With mirror walls the
+// doubled periodic grid (the even reflection across each wall) is folded
+// back: a source row beyond a wall is the reflected row, holding the
+// population whose velocity is reflected on that axis (pop).  popx is pop
+// reflected on x too: the population the wall node x = 0 (or N0 - 1) pulls
+// from x = 1 (or N0 - 2) when x has mirror walls.
+struct PopSrc {
+    int64_t row;
+    int pop, popx;
+};
+template <class L, int I, bool MIR>
+__device__ __forceinline__ PopSrc pop_source(const Geom &g, const RowPos &r)
+{
+    constexpr int ey = L::E[I][1], ez = L::E[I][2], ew = L::E[I][3];
+    PopSrc p;
+    if constexpr (!MIR) {
+        p.row = src_row<L::D, ey, ez, ew>(g, r);
+        p.pop = I;
+        p.popx = I;
+    } else {
+        int m = 0;
+        const int ys = src_coord<ey>(r.y, g.N1, (g.mirror >> 1) & 1u, m, 2);
+        const int zs = src_coord<ez>(r.z, g.N2, (g.mirror >> 2) & 1u, m, 4);
+        const int ws = src_coord<ew>(r.w, g.N3, (g.mirror >> 3) & 1u, m, 8);
+        p.row = ((int64_t)ws * g.N2 + zs) * g.N1 + ys;
+        p.pop = I;
+        p.popx = reflect_pop<L>(I, 1);
+        constexpr int nz = (ey != 0 ? 2 : 0) | (ez != 0 ? 4 : 0) | (ew != 0 ? 8 : 0);
+        static_for<1, 8>([&](auto Mi) {
+            constexpr int M = 2 * decltype(Mi)::value;  // subsets of the row axes y, z, w
+            if constexpr ((M & ~nz) == 0) {
+                if (m == M) {
+                    p.pop = reflect_pop<L>(I, M);
+                    p.popx = reflect_pop<L>(I, M | 1);
+                }
+            }
+        });
+    }
+    return p;
+}
+
 // Gather the pre-collision f(x, n) for the V nodes of this lane, one
 // population at a time (each shifted pull right after its load).  Used for
 // FP64 storage, whose sweep is bound by the FP64 pipe: the lower register
 // count keeps more warps resident to hide FP64 latency.
-template <class L, typename T, int V = Vec<T>::V>
+template <class L, typename T, int V = Vec<T>::V, bool MIR = false>
 __device__ __forceinline__ void gather_interleaved(const T *__restrict__ src, const Geom &g, int64_t row, int x0,
                                                    int lane, T (&f)[L::Q][V])
 {
     const RowPos rpos = row_pos<L::D>(g, row);
+    const bool mx = MIR && (g.mirror & 1u);
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2], ew = L::E[i][3];
-        const T *rp = src + (int64_t)i * g.slab + src_row<L::D, ey, ez, ew>(g, rpos) * g.pitch;
-        pull_row<T, ex, V>(rp, x0, lane, g.N0, f[i]);
+        constexpr int ex = L::E[i][0];
+        const PopSrc ps = pop_source<L, i, MIR>(g, rpos);
+        const T *rp = src + (int64_t)ps.pop * g.slab + ps.row * g.pitch;
+        if (!MIR || !mx) {
+            pull_row<T, ex, V>(rp, x0, lane, g.N0, f[i], rp, g.N0 - 1, 0);
+        } else {
+            const T *rx = src + (int64_t)ps.popx * g.slab + ps.row * g.pitch;
+            pull_row<T, ex, V>(rp, x0, lane, g.N0, f[i], rx, 1, g.N0 - 2);
+        }
     });
 }
 
@@ -163,21 +246,32 @@ __device__ __forceinline__ void gather_interleaved(const T *__restrict__ src, co
 // the one halo scalar a warp edge needs, is issued before any shuffle
 // consumes a loaded value, so a warp has all q rows in flight at once.  Used
 // for the HBM-bound storage types (FP32, 64-bit fixed point).
-template <class L, typename T, int V = Vec<T>::V>
+template <class L, typename T, int V = Vec<T>::V, bool MIR = false>
 __device__ __forceinline__ void gather_two_phase(const T *__restrict__ src, const Geom &g, int64_t row, int x0,
                                                  int lane, T (&f)[L::Q][V])
 {
     const RowPos rpos = row_pos<L::D>(g, row);
     const int xb = x0 + V * lane;
+    const bool mx = MIR && (g.mirror & 1u);
     T halo[L::Q];
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2], ew = L::E[i][3];
-        const T *rp = src + (int64_t)i * g.slab + src_row<L::D, ey, ez, ew>(g, rpos) * g.pitch;
+        constexpr int ex = L::E[i][0];
+        const PopSrc ps = pop_source<L, i, MIR>(g, rpos);
+        const T *rp = src + (int64_t)ps.pop * g.slab + ps.row * g.pitch;
         ld_vec(rp + xb, f[i]);
         halo[i] = T(0);
         if constexpr (ex == 1) {
-            if (lane == 0) halo[i] = rp[xb == 0 ? g.N0 - 1 : xb - 1];
+            if constexpr (!MIR) {
+                if (lane == 0) halo[i] = rp[xb == 0 ? g.N0 - 1 : xb - 1];
+            } else if (lane == 0) {
+                if (xb != 0)
+                    halo[i] = rp[xb - 1];
+                else if (!mx)
+                    halo[i] = rp[g.N0 - 1];
+                else
+                    halo[i] = src[(int64_t)ps.popx * g.slab + ps.row * g.pitch + 1];
+            }
         } else if constexpr (ex == -1) {
             const int x = xb + V - 1;
             if (lane == 31 && x + 1 < g.N0) halo[i] = rp[x + 1];
@@ -185,7 +279,7 @@ __device__ __forceinline__ void gather_two_phase(const T *__restrict__ src, cons
     });
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2], ew = L::E[i][3];
+        constexpr int ex = L::E[i][0];
         if constexpr (ex == 1) {
             T left = __shfl_up_sync(0xffffffffu, f[i][V - 1], 1);
             if (lane == 0) left = halo[i];
@@ -198,25 +292,29 @@ __device__ __forceinline__ void gather_two_phase(const T *__restrict__ src, cons
 #pragma unroll
             for (int k = 0; k < V - 1; ++k) f[i][k] = f[i][k + 1];
             f[i][V - 1] = right;
-            if (xb + V >= g.N0) {  // the node at x = N0 - 1 pulls from x = 0
-                const T *rp = src + (int64_t)i * g.slab + src_row<L::D, ey, ez, ew>(g, rpos) * g.pitch;
+            if (xb + V >= g.N0) {  // the node at x = N0 - 1 pulls across the row end
+                const PopSrc ps = pop_source<L, i, MIR>(g, rpos);
+                const T *wp = src + (int64_t)ps.pop * g.slab + ps.row * g.pitch;
+                if constexpr (MIR) {
+                    if (mx) wp = src + (int64_t)ps.popx * g.slab + ps.row * g.pitch + (g.N0 - 2);
+                }
 #pragma unroll
                 for (int k = 0; k < V; ++k)
-                    if (xb + k + 1 == g.N0) f[i][k] = rp[0];
+                    if (xb + k + 1 == g.N0) f[i][k] = wp[0];
             }
         }
     });
 }
 
-template <class L, typename T, int V = Vec<T>::V>
+template <class L, typename T, int V = Vec<T>::V, bool MIR = false>
 __device__ __forceinline__ void gather(const T *__restrict__ src, const Geom &g, int64_t row, int x0, int lane,
                                        T (&f)[L::Q][V])
 {
     // two-phase unless FP64 (FP64-pipe bound) or too many values to keep in flight
     if constexpr (std::is_same<T, double>::value || L::Q * V > 80)
-        gather_interleaved<L, T, V>(src, g, row, x0, lane, f);
+        gather_interleaved<L, T, V, MIR>(src, g, row, x0, lane, f);
     else
-        gather_two_phase<L, T, V>(src, g, row, x0, lane, f);
+        gather_two_phase<L, T, V, MIR>(src, g, row, x0, lane, f);
 }
 
 // The rest population is formed as theta minus all the others when the
@@ -429,11 +527,13 @@ template <typename T> __host__ __device__ constexpr int sweep_threads() { return
 
 // K is the collision-constant type; the matching collide() overload (float,
 // double or 64-bit fixed point) is picked by overload resolution.
-template <class L, typename T, class K>
+// MIR: the grid has mirror walls on some axis (g.mirror); the periodic
+// instantiation carries none of that logic.
+template <class L, typename T, class K, bool MIR = false>
 __global__ void __launch_bounds__(sweep_threads<T>()) sweep_kernel(const T *__restrict__ src,
                                                                    T *__restrict__ dst, Geom g, K k)
 {
-    constexpr int V = Vec<T>::V;
+    constexpr int V = lane_width<L, T>();
     constexpr int TH = sweep_threads<T>();
     const int lane = threadIdx.x & 31;
     const int64_t seg = (int64_t)blockIdx.x * (TH / 32) + (threadIdx.x >> 5);
@@ -442,7 +542,7 @@ __global__ void __launch_bounds__(sweep_threads<T>()) sweep_kernel(const T *__re
     const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
 
     T f[L::Q][V];
-    gather<L, T>(src, g, row, x0, lane, f);
+    gather<L, T, V, MIR>(src, g, row, x0, lane, f);
 
 #pragma unroll
     for (int v = 0; v < V; ++v) {

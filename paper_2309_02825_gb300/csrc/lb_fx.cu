@@ -14,13 +14,6 @@
 
 namespace lbk {
 
-// round(a * k / 2^62) for a fixed-point value a and a 62-fraction-bit constant k.
-__device__ __forceinline__ long long mulfx(long long a, long long k)
-{
-    const __int128 p = (__int128)a * (__int128)k;
-    return (long long)((p + ((__int128)1 << (kFxCoefBits - 1))) >> kFxCoefBits);
-}
-
 __device__ __forceinline__ void collide(D1Q3, long long *f, const CollFx &k)
 {
     const long long P = f[1] + f[2];
@@ -177,8 +170,12 @@ template <class L> static cudaError_t sweep_fx_t(lb_ctx *c, const void *src, voi
 {
     constexpr int TH = sweep_threads<long long>();
     const unsigned nb = (unsigned)((c->geom.nseg + TH / 32 - 1) / (TH / 32));
-    sweep_kernel<L, long long, CollFx><<<nb, TH, 0, c->stream>>>(
-        (const long long *)src, (long long *)dst, c->geom, make_coll_fx(c));
+    if (c->geom.mirror)
+        sweep_kernel<L, long long, CollFx, true><<<nb, TH, 0, c->stream>>>(
+            (const long long *)src, (long long *)dst, c->geom, make_coll_fx(c));
+    else
+        sweep_kernel<L, long long, CollFx><<<nb, TH, 0, c->stream>>>(
+            (const long long *)src, (long long *)dst, c->geom, make_coll_fx(c));
     return cudaGetLastError();
 }
 

@@ -63,24 +63,58 @@ template <> struct Vec<double> { using type = double2; static constexpr int V = 
 template <> struct Vec<float> { using type = float4; static constexpr int V = 4; };
 template <> struct Vec<long long> { using type = longlong2; static constexpr int V = 2; };
 
+// Values of one population a sweep lane holds (consecutive nodes along x).
+// One 16-byte vector, except in 4D: with q = 33 populations two-phase
+// gathers of one 16-byte vector per population need more registers than
+// keep enough warps resident, so the 4D sweep narrows the lane to 8 bytes
+// (one int64, two floats); FP64, bound by the FP64 pipe, keeps the vector.
+__host__ __device__ inline constexpr int lane_width(int d, int elem_bytes, bool fp64)
+{
+    return (d == 4 && !fp64) ? 8 / elem_bytes : 16 / elem_bytes;
+}
+template <class L, typename T> __host__ __device__ constexpr int lane_width()
+{
+    return lane_width(L::D, (int)sizeof(T), std::is_same<T, double>::value);
+}
+
 // Grid geometry of one padded state array.
 struct Geom {
     int N0, N1, N2, N3;  // sizes (1 for missing axes)
     int pitch;           // row pitch in elements: N0 rounded up to one 16-byte vector
     int64_t slab;        // pitch*N1*N2: elements per population
     int64_t rows;        // N1*N2*N3
-    int seg_per_row;     // ceil(pitch / (32*V)): warp segments per row
+    int seg_per_row;     // ceil(pitch / (32*W)): warp segments per row, W values a lane
     int64_t nseg;        // rows * seg_per_row (one warp per segment)
+    unsigned mirror;     // bit a: axis a has mirror walls on nodes 0 and N_a - 1 (else periodic)
 };
+
+// Index of the velocity e_i with its components on the axes of mask M
+// (bit a = axis a) negated: the population a mirror wall normal to those
+// axes reflects e_i into.  Every DdQ(1+2d^2) lattice here is closed under
+// such reflections.
+template <class L> __host__ __device__ constexpr int reflect_pop(int i, int M)
+{
+    for (int j = 0; j < L::Q; ++j) {
+        bool same = true;
+        for (int a = 0; a < 4; ++a) {
+            const int want = ((M >> a) & 1) ? -L::E[i][a] : L::E[i][a];
+            if (L::E[j][a] != want) same = false;
+        }
+        if (same) return j;
+    }
+    return -1;
+}
 
 // Lanes of a row's last segment may start at or beyond the pitch: they load
 // (harmless) values of the next row and never store.  Every state-shaped
 // allocation carries this many extra elements so those loads stay inside it.
 constexpr int64_t kSlackElems = 128;
 
-// Geometry for V values per lane (V = 16 bytes / element size).
-inline Geom make_geom(int64_t N0, int64_t N1, int64_t N2, int64_t N3, int V)
+// Geometry of a state array: V = elements per 16-byte vector (the pitch
+// unit), W = values a sweep lane holds (0: one vector).
+inline Geom make_geom(int64_t N0, int64_t N1, int64_t N2, int64_t N3, int V, int W = 0)
 {
+    if (W <= 0) W = V;
     Geom g;
     g.N0 = (int)N0;
     g.N1 = (int)N1;
@@ -89,8 +123,9 @@ inline Geom make_geom(int64_t N0, int64_t N1, int64_t N2, int64_t N3, int V)
     g.pitch = (int)((N0 + V - 1) / V * V);
     g.rows = N1 * N2 * N3;
     g.slab = (int64_t)g.pitch * g.rows;
-    g.seg_per_row = (g.pitch + 32 * V - 1) / (32 * V);
+    g.seg_per_row = (g.pitch + 32 * W - 1) / (32 * W);
     g.nseg = g.rows * g.seg_per_row;
+    g.mirror = 0;
     return g;
 }
 
@@ -128,6 +163,11 @@ struct Recov {
 struct InitK {
     double w0, w1, wd, iax, idg, theta_ref;
     double fxscale;  // 2^F for 64-bit fixed-point storage, unused otherwise
+    // 64-bit fixed point formed in integers: theta -> round(theta 2^F), a
+    // gradient component -> round(dx grad 2^F) (gscale = dx 2^F), and the
+    // constants w1, wd, iax/dx with kFxCoefBits fraction bits.
+    double gscale;
+    long long w1k, wdk, iak;
 };
 
 }  // namespace lbk

@@ -19,66 +19,154 @@
 namespace lbk {
 
 // ---------------------------------------------------------------------------
-// Initialisation, written in P form: P_0(y, i) = f_i(y + e_i, 0) with
-// f_i = w_i theta0 - dt [M^-1 S^-1 M Dbar f^eq]_i in closed form.
+// Initialisation (first two terms of Eq. (f-feq-o5), closed form):
+//   f_0 = w0 th,  f(+-e_a) = w1 th -+ iax d_a th,  f(diag e) = wd th - idg (e . grad th),
+// stored in P form, P_0(y, i) = f_i(y + e_i, 0).  One thread per node x
+// forms all q values of x once and stores f_i(x) at y = x - e_i (periodic
+// wrap).  On an axis with mirror walls a destination beyond a wall is not
+// stored (the doubled grid's ghost), and a thread next to a wall (x_a = 1
+// with e_ia = +1, or x_a = N_a - 2 with e_ia = -1) also stores f_i(x) in
+// the wall node's slot of the reflected population: that slot's source lies
+// beyond the wall, at the mirror image of x.  Every stored slot has exactly
+// one writer.  The wall-normal gradient component is odd across the wall, so
+// on a wall node it is taken as zero.
+//
+// FXI (64-bit fixed point formed in integers): theta and dx * grad theta are
+// converted to fixed point once per node, every product with a constant is
+// a rounded 64x62-bit product, and the rest population is theta minus the
+// others, so sum_i f_i(x) = round(theta0(x) 2^F) exactly.
 // ---------------------------------------------------------------------------
-template <class L, typename T>
+template <class L, typename T, bool FXI>
 __global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *__restrict__ theta0,
                             const double *__restrict__ grad, int *__restrict__ flag)
 {
+    constexpr int D = L::D, Q = L::Q;
     const int64_t nodes = (int64_t)g.N0 * g.rows;
     const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= nodes) return;
-    const int x = (int)(node % g.N0);
+    int c[4];
+    c[0] = (int)(node % g.N0);
     const int64_t rw = node / g.N0;
-    const int y = (int)(rw % g.N1);
-    const int z = (int)((rw / g.N1) % g.N2);
-    const int w = (int)(rw / ((int64_t)g.N1 * g.N2));
-    {
-        const double t0 = theta0[node];
-        bool bad = !(t0 > 0.0) || !isfinite(t0);
+    c[1] = (int)(rw % g.N1);
+    c[2] = (int)((rw / g.N1) % g.N2);
+    c[3] = (int)(rw / ((int64_t)g.N1 * g.N2));
+    const int n[4] = {g.N0, g.N1, g.N2, g.N3};
+
+    const double th = theta0[node];
+    double gr[D];
+    bool bad = !(th > 0.0) || !isfinite(th);
 #pragma unroll
-        for (int a = 0; a < L::D; ++a) bad |= !isfinite(grad[a * nodes + node]);
-        if (bad) atomicOr(flag, 1);
+    for (int a = 0; a < D; ++a) {
+        gr[a] = grad[a * nodes + node];
+        bad |= !isfinite(gr[a]);
+        if (((g.mirror >> a) & 1u) && (c[a] == 0 || c[a] == n[a] - 1)) gr[a] = 0.0;
     }
-    T *out = dst + (((int64_t)w * g.N2 + z) * g.N1 + y) * g.pitch + x;
+    if (bad) atomicOr(flag, 1);
+
+    T val[Q];
     bool range = false;
-    static_for<0, L::Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2], ew = L::E[i][3];
-        const int xs = wrapi(x + ex, g.N0);
-        const int ys = wrapi(y + ey, g.N1);
-        const int zs = wrapi(z + ez, g.N2);
-        const int ws = wrapi(w + ew, g.N3);
-        const int64_t src = (((int64_t)ws * g.N2 + zs) * g.N1 + ys) * g.N0 + xs;
-        const double th = theta0[src];
-        double val;
-        constexpr int nz = (ex != 0) + (ey != 0) + (ez != 0) + (ew != 0);
-        if constexpr (nz == 0) {
-            val = K.w0 * th;
-        } else if constexpr (nz == 1) {
-            constexpr int a = (ex != 0) ? 0 : ((ey != 0) ? 1 : ((ez != 0) ? 2 : 3));
-            constexpr int s = (ex != 0) ? ex : ((ey != 0) ? ey : ((ez != 0) ? ez : ew));
-            val = K.w1 * th - (double)s * K.iax * grad[a * nodes + src];
-            val -= K.w1 * K.theta_ref;
-        } else {
-            double edg = 0.0;
-            if constexpr (ex != 0) edg += (double)ex * grad[src];
-            if constexpr (ey != 0) edg += (double)ey * grad[nodes + src];
-            if constexpr (ez != 0) edg += (double)ez * grad[2 * nodes + src];
-            if constexpr (ew != 0) edg += (double)ew * grad[3 * nodes + src];
-            val = K.wd * th - K.idg * edg;
-            val -= K.wd * K.theta_ref;
+    if constexpr (FXI) {
+        const long long t = __double2ll_rn(th * K.fxscale);
+        long long G[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const double gs = gr[a] * K.gscale;
+            if (!(fabs(gs) < 0x1p61)) range = true;
+            G[a] = range ? 0 : __double2ll_rn(gs);
         }
-        if constexpr (nz == 0) val -= K.w0 * K.theta_ref;
-        out[(int64_t)i * g.slab] = to_store<T>(val, K.fxscale, range);
-    });
+        const long long W1 = mulfx(t, K.w1k), WD = mulfx(t, K.wdk);
+        long long rest = 0;
+        static_for<1, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int nz = (L::E[i][0] != 0) + (L::E[i][1] != 0) + (L::E[i][2] != 0) + (L::E[i][3] != 0);
+            long long v;
+            if constexpr (nz == 1) {
+                constexpr int a = (L::E[i][0] != 0) ? 0 : ((L::E[i][1] != 0) ? 1 : ((L::E[i][2] != 0) ? 2 : 3));
+                constexpr int ea = L::E[i][a];
+                const long long A = mulfx(G[a], K.iak);
+                v = (ea > 0) ? W1 - A : W1 + A;
+            } else {
+                constexpr int a = (L::E[i][0] != 0) ? 0 : ((L::E[i][1] != 0) ? 1 : 2);
+                constexpr int b = (L::E[i][3] != 0) ? 3 : ((L::E[i][2] != 0 && a < 2) ? 2 : 1);
+                constexpr int ea = L::E[i][a], eb = L::E[i][b];
+                // e . (dx grad) = +-(G_a + G_b) or +-(G_a - G_b); one rounded product per pair and sign
+                const long long P = mulfx(ea == eb ? G[a] + G[b] : G[a] - G[b], K.wdk);
+                v = (ea > 0) ? WD - P : WD + P;
+            }
+            if (!(v < (1ll << 61) && v > -(1ll << 61))) range = true;
+            val[i] = v;
+            rest += v;
+        });
+        val[0] = t - rest;
+    } else {
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2], ew = L::E[i][3];
+            constexpr int nz = (ex != 0) + (ey != 0) + (ez != 0) + (ew != 0);
+            double v;
+            if constexpr (nz == 0) {
+                v = K.w0 * th;
+                v -= K.w0 * K.theta_ref;
+            } else if constexpr (nz == 1) {
+                constexpr int a = (ex != 0) ? 0 : ((ey != 0) ? 1 : ((ez != 0) ? 2 : 3));
+                constexpr int sgn = (ex != 0) ? ex : ((ey != 0) ? ey : ((ez != 0) ? ez : ew));
+                v = K.w1 * th - (double)sgn * K.iax * gr[a];
+                v -= K.w1 * K.theta_ref;
+            } else {
+                double edg = 0.0;
+                if constexpr (ex != 0) edg += (double)ex * gr[0];
+                if constexpr (ey != 0) edg += (double)ey * gr[1];
+                if constexpr (ez != 0) edg += (double)ez * gr[2];
+                if constexpr (ew != 0) edg += (double)ew * gr[3];
+                v = K.wd * th - K.idg * edg;
+                v -= K.wd * K.theta_ref;
+            }
+            val[i] = to_store<T>(v, K.fxscale, range);
+        });
+    }
     if (range) atomicOr(flag, 2);
+
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int E0 = L::E[i][0], E1 = L::E[i][1], E2 = L::E[i][2], E3 = L::E[i][3];
+        const int ev[4] = {E0, E1, E2, E3};
+        int y[4];
+        bool ghost = false;
+        unsigned near = 0;  // axes where x is next to a wall it streams onto
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int e = ev[a];
+            int v = c[a] - e;
+            if (e != 0 && ((g.mirror >> a) & 1u)) {
+                if (v < 0 || v >= n[a]) ghost = true;
+                if ((e > 0 && c[a] == 1) || (e < 0 && c[a] == n[a] - 2)) near |= 1u << a;
+            } else if (v < 0) {
+                v += n[a];
+            } else if (v >= n[a]) {
+                v -= n[a];
+            }
+            y[a] = v;
+        }
+        if (ghost) return;
+        const int64_t at = (((int64_t)y[3] * g.N2 + y[2]) * g.N1 + y[1]) * g.pitch + y[0];
+        dst[(int64_t)i * g.slab + at] = val[i];
+        if (near) {
+            constexpr int nzm = (E0 != 0 ? 1 : 0) | (E1 != 0 ? 2 : 0) | (E2 != 0 ? 4 : 0) | (E3 != 0 ? 8 : 0);
+            static_for<1, 16>([&](auto Mi) {
+                constexpr int M = decltype(Mi)::value;
+                if constexpr ((M & ~nzm) == 0) {
+                    if ((M & ~near) == 0) dst[(int64_t)reflect_pop<L>(i, M) * g.slab + at] = val[i];
+                }
+            });
+        }
+    });
 }
 
-// Fourth-order central difference of theta along each axis (periodic).
+// Fourth-order central difference of theta along each axis: periodic, or,
+// on an axis with mirror walls (bit a of mirror), the even reflection of
+// theta across the wall nodes (theta(-k) = theta(k)).
 __global__ void fd4_kernel(const double *__restrict__ th, double *__restrict__ grad, int d, int N0, int N1,
-                           int N2, int N3, double inv12dx)
+                           int N2, int N3, unsigned mirror, double inv12dx)
 {
     const int64_t nodes = (int64_t)N0 * N1 * N2 * N3;
     const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -97,7 +185,11 @@ __global__ void fd4_kernel(const double *__restrict__ th, double *__restrict__ g
         const double cof[4] = {-1.0, 8.0, -8.0, 1.0};
         for (int k = 0; k < 4; ++k) {
             int c[4] = {x, y, z, w};
-            c[a] = ((c[a] + off[k]) % n[a] + n[a]) % n[a];
+            const int t = c[a] + off[k];
+            if ((mirror >> a) & 1u)
+                c[a] = t < 0 ? -t : (t >= n[a] ? 2 * (n[a] - 1) - t : t);
+            else
+                c[a] = (t % n[a] + n[a]) % n[a];
             acc += cof[k] * th[(((int64_t)c[3] * N2 + c[2]) * N1 + c[1]) * N0 + c[0]];
         }
         grad[a * nodes + node] = acc * inv12dx;
@@ -139,7 +231,24 @@ __device__ __forceinline__ void block_reduce_store(Acc<NS> &a, const int (&op)[N
     }
 }
 
-// Sum of the stored state over populations and valid nodes.
+// Weight of a node in the conserved total: 1/2 per mirror wall it lies on
+// (the doubled periodic grid holds interior nodes twice, wall nodes once).
+__device__ __forceinline__ double wall_weight(const Geom &g, int x, int64_t row)
+{
+    double wt = 1.0;
+    if ((g.mirror & 1u) && (x == 0 || x == g.N0 - 1)) wt *= 0.5;
+    const int y = (int)(row % g.N1);
+    const int64_t r2 = row / g.N1;
+    const int z = (int)(r2 % g.N2);
+    const int w = (int)(r2 / g.N2);
+    if ((g.mirror & 2u) && (y == 0 || y == g.N1 - 1)) wt *= 0.5;
+    if ((g.mirror & 4u) && (z == 0 || z == g.N2 - 1)) wt *= 0.5;
+    if ((g.mirror & 8u) && (w == 0 || w == g.N3 - 1)) wt *= 0.5;
+    return wt;
+}
+
+// Sum of the stored state over populations and valid nodes (weighted by
+// wall_weight when the grid has mirror walls).
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) sum_state_kernel(const T *__restrict__ src, Geom g, int q,
                                                                 double scale, double *__restrict__ partial)
@@ -150,7 +259,8 @@ __global__ void __launch_bounds__(kRedThreads) sum_state_kernel(const T *__restr
          t += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(t % g.N0);
         const int64_t rr = t / g.N0;  // population * rows + row
-        a.v[0] += (double)src[rr * g.pitch + x] * scale;
+        const double v = (double)src[rr * g.pitch + x] * scale;
+        a.v[0] += g.mirror ? v * wall_weight(g, x, rr % g.rows) : v;
     }
     const int op[1] = {0};
     block_reduce_store<1>(a, op, partial + (int64_t)blockIdx.x * kRedSlots);
@@ -254,8 +364,12 @@ template <class L, typename T> static cudaError_t sweep_t(lb_ctx *c, const void 
 {
     constexpr int TH = sweep_threads<T>();
     const unsigned nb = (unsigned)((c->geom.nseg + TH / 32 - 1) / (TH / 32));
-    sweep_kernel<L, T, Coll<T>><<<nb, TH, 0, c->stream>>>(
-        (const T *)src, (T *)dst, c->geom, make_coll<T>(*c));
+    if (c->geom.mirror)
+        sweep_kernel<L, T, Coll<T>, true><<<nb, TH, 0, c->stream>>>(
+            (const T *)src, (T *)dst, c->geom, make_coll<T>(*c));
+    else
+        sweep_kernel<L, T, Coll<T>><<<nb, TH, 0, c->stream>>>(
+            (const T *)src, (T *)dst, c->geom, make_coll<T>(*c));
     return cudaGetLastError();
 }
 
@@ -275,7 +389,8 @@ cudaError_t launch_fd4_grad(const lb_ctx *c, const double *theta0, double *grad)
 {
     const int64_t nodes = c->nodes;
     fd4_kernel<<<(unsigned)((nodes + 255) / 256), 256, 0, c->stream>>>(
-        theta0, grad, c->d, (int)c->N[0], (int)c->N[1], (int)c->N[2], (int)c->N[3], 1.0 / (12.0 * c->dx));
+        theta0, grad, c->d, (int)c->N[0], (int)c->N[1], (int)c->N[2], (int)c->N[3], c->geom.mirror,
+        1.0 / (12.0 * c->dx));
     return cudaGetLastError();
 }
 
@@ -292,8 +407,23 @@ static cudaError_t init_t(lb_ctx *c, const double *theta0, const double *grad, i
     K.idg = wd * c->dx;
     K.theta_ref = (c->precision == LB_FP32_SHIFTED) ? c->theta_ref : 0.0;
     K.fxscale = ldexp(1.0, c->fx_bits);
-    init_kernel<L, T><<<(unsigned)((c->nodes + 255) / 256), 256, 0, c->stream>>>(
-        (T *)c->f[c->cur], c->geom, K, theta0, grad, flag);
+    K.gscale = c->dx * K.fxscale;
+    const unsigned nb = (unsigned)((c->nodes + 255) / 256);
+    if constexpr (std::is_same<T, long long>::value) {
+        // integer formation needs every constant inside the 62-bit range and
+        // a total weight that keeps the rest population's sum below 2^61
+        const double ia = K.iax / c->dx;
+        const double wmass = fabs(c->w0) + 2.0 * d * fabs(c->w1) + 2.0 * d * (d - 1.0) * fabs(wd);
+        if (fabs(ia) < 1.5 && fabs(c->w1) < 1.0 && fabs(wd) < 1.0 && wmass <= 4.0) {
+            K.w1k = llrint(ldexp(c->w1, kFxCoefBits));
+            K.wdk = llrint(ldexp(wd, kFxCoefBits));
+            K.iak = llrint(ldexp(ia, kFxCoefBits));
+            init_kernel<L, T, true><<<nb, 256, 0, c->stream>>>((T *)c->f[c->cur], c->geom, K, theta0, grad, flag);
+            return cudaGetLastError();
+        }
+    }
+    K.w1k = K.wdk = K.iak = 0;
+    init_kernel<L, T, false><<<nb, 256, 0, c->stream>>>((T *)c->f[c->cur], c->geom, K, theta0, grad, flag);
     return cudaGetLastError();
 }
 

@@ -9,6 +9,9 @@
 // N0 - 1, x = N0 - 1 pulling from 0) read a scalar from global memory.
 // Then theta = sum f, J = sum e f (exact integer sums for 64-bit fixed
 // point), grad theta = -s1 J / (sigma dx) and u = (2 - s1) c J / theta.
+// With mirror walls (MIR) a row or population beyond a wall is read from its
+// reflection (pop_source), and the wall nodes of x read x = 1 and N0 - 2 of
+// the x-reflected population instead of the periodic wrap.
 // The mbarrier wait is bounded: on timeout the block records an error flag,
 // waits (again bounded) for its own copies and returns.
 #include <math.h>
@@ -64,7 +67,7 @@ template <> struct RecAcc<long long> {
     using type = long long;  // exact integer moment sums
 };
 
-template <class L, typename T>
+template <class L, typename T, bool MIR>
 __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ src, Geom g, Recov r, double scale,
                                                        double *__restrict__ theta, double *__restrict__ grad,
                                                        double *__restrict__ u, int *__restrict__ flag)
@@ -96,8 +99,8 @@ __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ sr
                      : "memory");
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            constexpr int ey = L::E[i][1], ez = L::E[i][2], ew = L::E[i][3];
-            const T *gsrc = src + (int64_t)i * g.slab + src_row<L::D, ey, ez, ew>(g, rpos) * g.pitch + xs;
+            const PopSrc ps = pop_source<L, i, MIR>(g, rpos);
+            const T *gsrc = src + (int64_t)ps.pop * g.slab + ps.row * g.pitch + xs;
             const uint32_t dst = smem_u32(tile + i * TW + (xs - x0 + H));
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -117,14 +120,17 @@ __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ sr
     A th = 0, J[4] = {0, 0, 0, 0};
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2], ew = L::E[i][3];
+        constexpr int ex = L::E[i][0];
         const int sx = x - ex;
         T v;
         if (sx >= 0 && sx < g.N0) {
             v = tile[i * TW + (sx - x0 + H)];
-        } else {  // periodic wrap of the row: a scalar from the other end
-            const T *rowp = src + (int64_t)i * g.slab + src_row<L::D, ey, ez, ew>(g, rpos) * g.pitch;
-            v = rowp[sx < 0 ? g.N0 - 1 : 0];
+        } else {  // across the row end: a scalar from the other end, or the x-reflection
+            const PopSrc ps = pop_source<L, i, MIR>(g, rpos);
+            if (MIR && (g.mirror & 1u))
+                v = src[(int64_t)ps.popx * g.slab + ps.row * g.pitch + (sx < 0 ? 1 : g.N0 - 2)];
+            else
+                v = src[(int64_t)ps.pop * g.slab + ps.row * g.pitch + (sx < 0 ? g.N0 - 1 : 0)];
         }
         const A fv = (A)v;
         th += fv;
@@ -149,13 +155,14 @@ __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ sr
     }
 }
 
-template <class L, typename T>
+template <class L, typename T, bool MIR>
 static cudaError_t recover_t(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
 {
     constexpr int H = 16 / (int)sizeof(T);
     const size_t smem = (size_t)L::Q * (kTile + 2 * H) * sizeof(T);
     // up to 68 KB (D4Q33, 8-byte storage): allow more than the default 48 KB
-    cudaError_t e = cudaFuncSetAttribute(recover_kernel<L, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(recover_kernel<L, T, MIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     Recov r;
     r.ucoef = (2.0 - c->s1) * c->c;
@@ -163,18 +170,24 @@ static cudaError_t recover_t(lb_ctx *c, const void *src, double *th, double *gr,
     r.theta_ref = (c->precision == LB_FP32_SHIFTED) ? c->theta_ref : 0.0;
     const double scale = (c->precision == LB_FX64) ? ldexp(1.0, -c->fx_bits) : 1.0;
     const int64_t blocks = c->geom.rows * ((c->geom.N0 + kTile - 1) / kTile);
-    recover_kernel<L, T><<<(unsigned)blocks, kTile, smem, c->stream>>>((const T *)src, c->geom, r, scale, th, gr, u,
-                                                                        flag);
+    recover_kernel<L, T, MIR><<<(unsigned)blocks, kTile, smem, c->stream>>>((const T *)src, c->geom, r, scale, th,
+                                                                             gr, u, flag);
     return cudaGetLastError();
+}
+
+template <class L, bool MIR>
+static cudaError_t recover_m(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
+{
+    switch (c->precision) {
+    case LB_FX64: return recover_t<L, long long, MIR>(c, src, th, gr, u, flag);
+    case LB_FP32_SHIFTED: return recover_t<L, float, MIR>(c, src, th, gr, u, flag);
+    default: return recover_t<L, double, MIR>(c, src, th, gr, u, flag);
+    }
 }
 
 template <class L> static cudaError_t recover_l(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
 {
-    switch (c->precision) {
-    case LB_FX64: return recover_t<L, long long>(c, src, th, gr, u, flag);
-    case LB_FP32_SHIFTED: return recover_t<L, float>(c, src, th, gr, u, flag);
-    default: return recover_t<L, double>(c, src, th, gr, u, flag);
-    }
+    return c->geom.mirror ? recover_m<L, true>(c, src, th, gr, u, flag) : recover_m<L, false>(c, src, th, gr, u, flag);
 }
 
 // Self-test of the bounded wait: a barrier that nothing completes.

@@ -24,6 +24,7 @@ from . import build as _build
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ESTATE, LB_ETIMEOUT, LB_ENONPOS = range(7)
 LB_FP64, LB_FP32_SHIFTED, LB_FX64 = 0, 1, 2
+LB_PERIODIC, LB_MIRROR = 0, 1
 _STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ESTATE",
            5: "LB_ETIMEOUT", 6: "LB_ENONPOS"}
 
@@ -65,6 +66,8 @@ def load():
             "lb_destroy": ([vp], ctypes.c_int),
             "lb_get_params": ([vp, pd], ctypes.c_int),
             "lb_set_theta0": ([vp, vp, vp], ctypes.c_int),
+            "lb_set_boundary": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "lb_get_boundary": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "lb_step": ([vp, i64], ctypes.c_int),
             "lb_get_step": ([vp, p64], ctypes.c_int),
             "lb_macros": ([vp, vp, vp, vp], ctypes.c_int),
@@ -144,6 +147,22 @@ def lb_get_params(ctx):
     keys = ("eps", "c", "cs2", "s1", "s2x", "s22", "w0", "w1", "wd", "nu", "dx", "dt", "q", "theta_ref",
             "fx_bits")
     return dict(zip(keys, list(buf)))
+
+
+def lb_set_boundary(ctx, kinds):
+    """kinds: one LB_PERIODIC / LB_MIRROR (or "periodic" / "mirror") per axis."""
+    lib = load()
+    names = {"periodic": LB_PERIODIC, "mirror": LB_MIRROR}
+    vals = [names[k] if isinstance(k, str) else int(k) for k in kinds]
+    arr = (ctypes.c_int * max(1, len(vals)))(*vals)
+    _check(lib, ctx, lib.lb_set_boundary(ctx, arr), "lb_set_boundary")
+
+
+def lb_get_boundary(ctx, d):
+    lib = load()
+    arr = (ctypes.c_int * 4)()
+    _check(lib, ctx, lib.lb_get_boundary(ctx, arr), "lb_get_boundary")
+    return ["mirror" if arr[a] == LB_MIRROR else "periodic" for a in range(d)]
 
 
 def lb_set_theta0(ctx, theta0, grad_theta0=None, nodes=None, d=None):
@@ -235,15 +254,18 @@ def lb_load_state(ctx, buf, step):
 # --------------------------------------------------------------------------
 
 class Solver:
-    """One periodic MRT-LB solver context on the current CUDA device.
+    """One MRT-LB solver context on the current CUDA device.
 
     ``relax`` = None uses Theorem 2's relaxation set; a dict with s1, s2x,
     s22, w1, wd overrides it.  ``precision`` is "fp64" or "fp32s" (FP32
     shifted storage around ``theta_ref``) or "fx64" (64-bit fixed-point
-    storage with exact integer moment sums).
+    storage with exact integer moment sums).  ``boundary`` gives each axis
+    "periodic" (default) or "mirror" (walls on the first and last node,
+    d theta/dn = 0, i.e. zero normal velocity).
     """
 
-    def __init__(self, d, N, nu, dx, dt, relax=None, precision="fp64", theta_ref=0.0, stream=None):
+    def __init__(self, d, N, nu, dx, dt, relax=None, precision="fp64", theta_ref=0.0, stream=None,
+                 boundary=None):
         if not torch.cuda.is_available():
             raise RuntimeError("the MRT-LB solver needs a CUDA GPU; no CPU fallback exists")
         self.d = int(d)
@@ -260,6 +282,11 @@ class Solver:
         self.stream = stream
         self._lib = load()
         self.ctx = lb_create(self.d, self.N, nu, dx, dt, rel, self.precision, stream)
+        if boundary is not None:
+            if len(boundary) != self.d:
+                raise ValueError("boundary must have d entries")
+            lb_set_boundary(self.ctx, boundary)
+        self.boundary = lb_get_boundary(self.ctx, self.d)
         self.params = lb_get_params(self.ctx)
 
     def close(self):

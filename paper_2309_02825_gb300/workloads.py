@@ -150,6 +150,108 @@ class ProductSineProblem:
         return cole_hopf_u(self.nu, self.theta(N, dx, t), self.grad(N, dx, t))
 
 
+@dataclass
+class ProductWaveProblem:
+    """theta = (A + exp(-nu pi^2 |kappa|^2 t) prod_a w_a(pi kappa_a x_a)) / B
+    with w_a = cos or sin per axis ("cos" on an axis with walls at x = 0 and
+    x = (N_a - 1) dx = L_a: d theta/dn = 0 there for integer kappa_a L_a)."""
+
+    d: int
+    nu: float
+    kappa: tuple
+    waves: tuple
+    A: float = 2.0
+    B: float = 1.0
+
+    @property
+    def rate(self):
+        return self.nu * math.pi ** 2 * sum(k * k for k in self.kappa)
+
+    def _parts(self, N, dx):
+        X = grid(N, dx)
+        W, dW = [], []
+        for a in range(self.d):
+            k = math.pi * self.kappa[a]
+            if self.waves[a] == "cos":
+                W.append(np.cos(k * X[a]))
+                dW.append(-k * np.sin(k * X[a]))
+            else:
+                W.append(np.sin(k * X[a]))
+                dW.append(k * np.cos(k * X[a]))
+        return W, dW
+
+    def theta(self, N, dx, t=0.0):
+        W, _ = self._parts(N, dx)
+        prod = np.ones(tuple(reversed(N)))
+        for a in range(self.d):
+            prod = prod * W[a]
+        return (self.A + math.exp(-self.rate * t) * prod) / self.B
+
+    def grad(self, N, dx, t=0.0):
+        W, dW = self._parts(N, dx)
+        out = np.zeros((self.d,) + tuple(reversed(N)))
+        dec = math.exp(-self.rate * t) / self.B
+        for a in range(self.d):
+            term = np.ones(tuple(reversed(N)))
+            for b in range(self.d):
+                term = term * (dW[b] if b == a else W[b])
+            out[a] = dec * term
+        return out
+
+    def u(self, N, dx, t=0.0):
+        return cole_hopf_u(self.nu, self.theta(N, dx, t), self.grad(N, dx, t))
+
+
+def bessel_i_all(z, nmax, quad=1024):
+    """I_0(z) .. I_nmax(z) from I_n(z) = (1/pi) int_0^pi exp(z cos s) cos(n s) ds,
+    by the trapezoid rule over the full period (exponentially accurate for
+    this periodic analytic integrand once quad >> z + nmax)."""
+    s = 2.0 * math.pi * np.arange(quad) / quad
+    spec = np.fft.rfft(np.exp(z * np.cos(s)))
+    return spec.real[: nmax + 1] / quad
+
+
+@dataclass
+class WallBesselProblem:
+    """Example 1 (Sec. V): 1D, u(x, 0) = sin(pi x) on [0, 1] with u = 0 at
+    x = 0 and x = 1.  Its Cole-Hopf transform is
+    theta(x, t) = a_0 + 2 sum_{n >= 1} a_n exp(-n^2 pi^2 nu t) cos(n pi x),
+    a_n = I_n(1/(2 pi nu)) (modified Bessel functions of the first kind), and
+    theta(x, 0) = exp(cos(pi x)/(2 pi nu)).  Nodes x_j = j dx, j = 0..N-1,
+    with (N - 1) dx = 1."""
+
+    nu: float
+    nmax: int = 96
+
+    def _coef(self):
+        return bessel_i_all(1.0 / (2.0 * math.pi * self.nu), self.nmax)
+
+    def _x(self, N, dx):
+        return dx * np.arange(N[0], dtype=np.float64)
+
+    def theta(self, N, dx, t=0.0):
+        x = self._x(N, dx)
+        if t == 0.0:  # closed form (the series cancels heavily where theta is small)
+            return np.exp(np.cos(math.pi * x) / (2.0 * math.pi * self.nu))
+        a = self._coef()
+        n = np.arange(1, self.nmax + 1)
+        w = a[1:] * np.exp(-(n * math.pi) ** 2 * self.nu * t)
+        return a[0] + 2.0 * (w @ np.cos(math.pi * np.outer(n, x)))
+
+    def grad(self, N, dx, t=0.0):
+        x = self._x(N, dx)
+        if t == 0.0:
+            th = np.exp(np.cos(math.pi * x) / (2.0 * math.pi * self.nu))
+            return (-np.sin(math.pi * x) / (2.0 * self.nu) * th)[None, :]
+        a = self._coef()
+        n = np.arange(1, self.nmax + 1)
+        w = a[1:] * np.exp(-(n * math.pi) ** 2 * self.nu * t) * n * math.pi
+        return (-2.0 * (w @ np.sin(math.pi * np.outer(n, x))))[None, :]
+
+    def u(self, N, dx, t=0.0):
+        return cole_hopf_u(self.nu, self.theta(N, dx, t), self.grad(N, dx, t))
+
+
 # --------------------------------------------------------------------------
 # The standard workloads (sizes, eps, steps).  eps = nu*dt/dx^2 is fixed per
 # family so that t_end is an integer number of steps at every N.
@@ -227,6 +329,18 @@ def paper_example(d, eps, level=0):
     steps = int(round(2.0 / dt))
     return Case("paper_ex%d_eps%g_l%d" % (d, eps, level), d, (n,) * d, nu, dx, dt, steps,
                 ProductSineProblem(d, nu, kappa, 2.0, 2.0))
+
+
+def wall_example1(eps, level=0):
+    """The paper's Example 1 (1D, walls at x = 0 and x = 1, t = 2) at
+    refinement `level`: dx = 1/40 / 2^level, dt = 1/100 / 4^level,
+    nu = eps dx^2 / dt; N = 1/dx + 1 nodes (both wall nodes included)."""
+    dx = 1.0 / 40 / 2 ** level
+    dt = 1.0 / 100 / 4 ** level
+    nu = eps * dx * dx / dt
+    n = int(round(1.0 / dx)) + 1
+    steps = int(round(2.0 / dt))
+    return Case("wall_ex1_eps%g_l%d" % (eps, level), 1, (n,), nu, dx, dt, steps, WallBesselProblem(nu))
 
 
 def batched_2d(count=512, seed=2312, nsteps=2000):

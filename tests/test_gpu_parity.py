@@ -121,6 +121,34 @@ def test_sum_theta_conserved_and_matches_oracle(d, N):
     assert abs(total - prob.theta(N, dx).sum()) <= 1e-12 * abs(total)
 
 
+@pytest.mark.parametrize("d,N", [(1, (77,)), (2, (70, 45)), (3, (24, 10, 7)), (4, (9, 6, 5, 4))])
+def test_fx64_initial_mass_is_rounded_theta0(d, N):
+    """The fixed-point initialisation forms the rest population as theta
+    minus the others, so the stored state sums to sum_x round(theta0 2^F)
+    exactly (compared modulo 2^64, as the int64 sums wrap)."""
+    prob, dx, dt = _problem(d, N, 11)
+    s = lb.Solver(d, N, prob.nu, dx, dt, precision="fx64")
+    th0 = prob.theta(N, dx)
+    s.set_theta0(_dev(th0), _dev(prob.grad(N, dx)))
+    F = lb.lb_get_params(s.ctx)["fx_bits"]
+    pitch, _, _ = s.state_layout()
+    q = int(s.params["q"])
+    st = s.save_state().view(torch.int64).view(q, -1, pitch)[..., : N[0]]
+    got = int(st.sum().item()) % 2 ** 64
+    want = int(np.rint(th0 * 2.0 ** F).astype(np.int64).sum()) % 2 ** 64
+    assert got == want
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fx64"])
+def test_init_constants_beyond_fixed_point_range(precision):
+    """s1 = 0.1 makes the initialisation's gradient constant (sigma/s1 - ...)/2
+    exceed the fixed-point range: FX64 then forms the values in FP64 and
+    rounds them, and still meets the FP64 bar."""
+    relax = {"s1": 0.1, "s2x": 0.7, "s22": 1.1, "w1": 0.12, "wd": 0.02}
+    ref, got, _, m = _run_both(2, (40, 30), 7, relax=relax, precision=precision)
+    _check_fp64(ref, got, m, 7)
+
+
 @pytest.mark.parametrize("d,N", [(1, (77,)), (2, (70, 45)), (3, (24, 10, 7))])
 def test_fx64_conserves_sum_exactly(d, N):
     """Fixed point: the rest population is theta minus the others, so the
@@ -201,6 +229,13 @@ def test_invalid_inputs_are_reported():
     assert ei.value.status == lb.LB_ENONPOS
     with pytest.raises(ValueError):
         s.set_theta0(torch.ones(7, dtype=torch.float64, device="cuda"))
+    # fixed point: a gradient too steep for the fixed-point range
+    fx = lb.Solver(2, (8, 8), 0.02, 1 / 8, 0.01, precision="fx64")
+    steep = torch.zeros((2, 8, 8), dtype=torch.float64, device="cuda")
+    steep[0, 2, 2] = 1e30
+    with pytest.raises(lb.LBError) as ei:
+        fx.set_theta0(torch.ones((8, 8), dtype=torch.float64, device="cuda"), steep)
+    assert ei.value.status == lb.LB_EINVAL
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fx64", "fp32s"])
