@@ -362,8 +362,23 @@ def run_e2e(args, s, case, th0_h, g0_h, ex_t_h, ex_u_h, stream, world):
     value = aggregate(case.nodes * S * args.steps, el, world) / 1e6
     h2d_b = sum(h.numel() * h.element_size() for h in h_in)
     d2h_b = sum(t.numel() * t.element_size() for t in h_out[0])
+    # copy rates on their own (outside the timed region): the first upload and
+    # the last download of the timed run cannot overlap any compute
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    with torch.cuda.stream(cs):
+        e0.record(cs)
+        for h, dv in zip(h_in, d_in[0]):
+            dv.copy_(h, non_blocking=True)
+        e1.record(cs)
+        h_out[0][0].copy_(d_out[0][0], non_blocking=True)
+        h_out[0][1].copy_(d_out[0][1], non_blocking=True)
+        e2.record(cs)
+    torch.cuda.synchronize()
+    h2d_ms, d2h_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
     return {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
-            "overlap": "copies double-buffered on a second stream"}
+            "overlap": "copies double-buffered on a second stream",
+            "copy_rates": {"h2d_gbs": h2d_b / h2d_ms / 1e6, "d2h_gbs": d2h_b / d2h_ms / 1e6,
+                           "unoverlapped_ms_per_run": h2d_ms + d2h_ms, "steps": args.steps}}
 
 
 def run_batched(local):
@@ -687,7 +702,8 @@ def run_4d(local, peaks):
 
 
 def run_profile_sweep(local, spec):
-    """Minimal, repeatable command for ncu: init + STEPS sweeps of one grid."""
+    """Minimal, repeatable command for ncu: init + STEPS sweeps of one grid,
+    then one recovery and one state sum."""
     import torch
     from paper_2309_02825_gb300 import lb
     torch.cuda.set_device(local)
@@ -705,6 +721,8 @@ def run_profile_sweep(local, spec):
                  torch.from_numpy(np.ascontiguousarray(prob.grad(N, dx))).cuda())
     for _ in range(steps):
         s.step(1)
+    s.macros(want=("theta", "u"))
+    s.sum_theta()
     torch.cuda.synchronize()
     s.close()
     print(json.dumps({"profile_sweep": spec, "ok": True}))

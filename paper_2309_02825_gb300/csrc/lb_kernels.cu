@@ -231,12 +231,13 @@ __device__ __forceinline__ void block_reduce_store(Acc<NS> &a, const int (&op)[N
     }
 }
 
-// Weight of a node in the conserved total: 1/2 per mirror wall it lies on
-// (the doubled periodic grid holds interior nodes twice, wall nodes once).
-__device__ __forceinline__ double wall_weight(const Geom &g, int x, int64_t row)
+// Weight of a row of nodes in the conserved total: 1/2 per mirror wall of
+// the y, z, w axes the row lies on (the doubled periodic grid holds interior
+// nodes twice, wall nodes once); the x walls halve the row's first and last
+// node.
+__device__ __forceinline__ double row_wall_weight(const Geom &g, int64_t row)
 {
     double wt = 1.0;
-    if ((g.mirror & 1u) && (x == 0 || x == g.N0 - 1)) wt *= 0.5;
     const int y = (int)(row % g.N1);
     const int64_t r2 = row / g.N1;
     const int z = (int)(r2 % g.N2);
@@ -247,21 +248,54 @@ __device__ __forceinline__ double wall_weight(const Geom &g, int x, int64_t row)
     return wt;
 }
 
+template <typename T> struct SumAcc {
+    using type = double;
+};
+template <> struct SumAcc<long long> {
+    using type = __int128;  // exact: fixed-point values add without rounding
+};
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(__int128 v)
+{
+    const long long hi = (long long)(v >> 64);
+    const unsigned long long lo = (unsigned long long)v;
+    return (double)hi * 0x1p64 + (double)lo;
+}
+
 // Sum of the stored state over populations and valid nodes (weighted by
-// wall_weight when the grid has mirror walls).
+// the wall weights when the grid has mirror walls): one warp per row of
+// one population, aligned 16-byte vector loads along the row.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) sum_state_kernel(const T *__restrict__ src, Geom g, int q,
                                                                 double scale, double *__restrict__ partial)
 {
-    Acc<1> a{{0.0}};
-    const int64_t total = (int64_t)q * g.rows * g.N0;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(t % g.N0);
-        const int64_t rr = t / g.N0;  // population * rows + row
-        const double v = (double)src[rr * g.pitch + x] * scale;
-        a.v[0] += g.mirror ? v * wall_weight(g, x, rr % g.rows) : v;
+    constexpr int V = Vec<T>::V;
+    typename SumAcc<T>::type acc = 0;
+    double accw = 0.0;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nrows = (int64_t)q * g.rows;
+    for (int64_t r = warp; r < nrows; r += nwarps) {
+        const T *rowp = src + r * g.pitch;
+        const double rw = g.mirror ? row_wall_weight(g, r % g.rows) : 1.0;
+        for (int x0 = lane * V; x0 < g.N0; x0 += 32 * V) {
+            T a[V];
+            ld_vec(rowp + x0, a);
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                const int x = x0 + k;
+                if (x >= g.N0) continue;
+                if (!g.mirror) {
+                    acc += a[k];
+                } else {
+                    const double xw = ((g.mirror & 1u) && (x == 0 || x == g.N0 - 1)) ? 0.5 : 1.0;
+                    accw += (double)a[k] * (rw * xw);
+                }
+            }
+        }
     }
+    Acc<1> a{{(to_double(acc) + accw) * scale}};
     const int op[1] = {0};
     block_reduce_store<1>(a, op, partial + (int64_t)blockIdx.x * kRedSlots);
 }
