@@ -9,8 +9,10 @@
 // with Lt = c0 l0 + cA sum_axis l + wd sum_diag l, Laa = k2 (l_{+a} + l_{-a}
 // - 2 l0), Ja = k1 (l_{+a} - l_{-a}), Lab = k3 sum_{diag(a,b)} sa sb l,
 //   (K^T l)_j = Lt + sum_a e_ja^2 Laa + sum_a e_ja Ja + sum_{a<b} e_ja e_jb Lab.
-// (dK/deps) f is the forward collision formula evaluated with the
-// eps-derivatives of its constants (it is linear in them).
+// The collision is linear in its constants, so lambda . (dK/deps) f is the
+// same bilinear form with the eps-derivatives of the constants: the lambda
+// channels of K^T (l0, l_{+a} +- l_{-a}, the plane sums) against the
+// moments of f (theta, J_a, P_aa, P_ab), a handful of products per node.
 #include <math.h>
 #include <string.h>
 
@@ -31,6 +33,7 @@ struct AdjK {
     Coll<double> kd;  // their eps-derivatives
     double scale;     // stored value -> f: f_i = v * scale + shift[i]
     double shift[kAdjQ];
+    double mshift_th, mshift_paa;  // the shift's moments: theta_ref and sigma theta_ref
     double ucoef, ducoef;                      // (2 - s1) c and d/deps
     double w[kAdjQ], dw[kAdjQ];                // weights and d/deps
     double iax, idg, diax, didg;               // initialisation operator and d/deps
@@ -56,48 +59,105 @@ __device__ __forceinline__ void gather_rev(const double *__restrict__ src, const
     });
 }
 
-// In-place K^T on one node's q adjoint values.
-template <class L> __device__ __forceinline__ void apply_KT(double *l, const Coll<double> &k)
+// Moments of one node's distributions in the accumulation type of the
+// storage (exact int64 sums for fixed point): theta, J_a, P_aa, P_ab.
+template <class L, typename A> struct NodeMoments {
+    static constexpr int D = L::D, NP = D * (D - 1) / 2 > 0 ? D * (D - 1) / 2 : 1;
+    A th, J[D], Paa[D], Pab[NP];
+};
+template <class L, typename A> __device__ __forceinline__ NodeMoments<L, A> node_moments(const A *f)
 {
-    double sax = 0.0, sdg = 0.0;
-    double Laa[3] = {0, 0, 0}, Ja[3] = {0, 0, 0}, Lab[3] = {0, 0, 0};  // pairs xy, xz, yz
-    static_for<1, L::Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
-        constexpr int nz = (ex != 0) + (ey != 0) + (ez != 0);
-        if constexpr (nz == 1) {
-            constexpr int a = (ex != 0) ? 0 : ((ey != 0) ? 1 : 2);
-            constexpr int s = (ex != 0) ? ex : ((ey != 0) ? ey : ez);
-            sax += l[i];
-            Laa[a] += l[i];
-            Ja[a] += s * l[i];
-        } else {
-            constexpr int p = (ez == 0) ? 0 : ((ey == 0) ? 1 : 2);
-            constexpr int ss = ex * ey + ex * ez + ey * ez;  // sa*sb of the nonzero pair
-            sdg += l[i];
-            Lab[p] += ss * l[i];
-        }
-    });
-    const double Lt = fma(k.c0, l[0], fma(k.cA, sax, k.wd * sdg));
+    constexpr int D = L::D, NP = D * (D - 1) / 2, B0 = 1 + 2 * D;
+    NodeMoments<L, A> m;
+    m.th = f[0];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        Laa[a] = k.k2 * (Laa[a] - 2.0 * l[0]);
-        Ja[a] = k.k1 * Ja[a];
-        Lab[a] = k.k3 * Lab[a];
+    for (int a = 0; a < D; ++a) {
+        m.Paa[a] = f[1 + a] + f[1 + D + a];
+        m.J[a] = f[1 + a] - f[1 + D + a];
+        m.th += m.Paa[a];
+    }
+    static_for<0, NP>([&](auto Pi) {
+        constexpr int p = decltype(Pi)::value;
+        constexpr int a = pair_a<D>(p), b = pair_b<D>(p);
+        const Plane<A> pl = plane(f[B0 + 4 * p], f[B0 + 4 * p + 1], f[B0 + 4 * p + 2], f[B0 + 4 * p + 3]);
+        m.th += pl.F;
+        m.Paa[a] += pl.F;
+        m.Paa[b] += pl.F;
+        m.J[a] += pl.Ja;
+        m.J[b] += pl.Jb;
+        m.Pab[p] = pl.P;
+    });
+    return m;
+}
+
+// One node of the reverse step: l <- K^T l in place (shared sub-sums, as
+// in the forward collision); with NU, also returns lambda . (dK/deps) f for
+// the node's pre-collision f (stored values fv: f = fv scale + shift).
+template <class L, typename T, bool NU>
+__device__ __forceinline__ double adj_node(double *l, const T *fv, const AdjK &K)
+{
+    constexpr int D = L::D, NP = D * (D - 1) / 2, B0 = 1 + 2 * D;
+    const double l0 = l[0];
+    double s[D], dd[D], F[NP > 0 ? NP : 1], P[NP > 0 ? NP : 1];
+    double sax = 0.0, sdg = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        s[a] = l[1 + a] + l[1 + D + a];
+        dd[a] = l[1 + a] - l[1 + D + a];
+        sax += s[a];
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const Plane<double> pl = plane(l[B0 + 4 * p], l[B0 + 4 * p + 1], l[B0 + 4 * p + 2], l[B0 + 4 * p + 3]);
+        F[p] = pl.F;
+        P[p] = pl.P;
+        sdg += pl.F;
+    }
+    double eterm = 0.0;
+    if constexpr (NU) {
+        const NodeMoments<L, T> m = node_moments<L, T>(fv);
+        // f moments in FP64: theta = sum f, P_aa gains sigma theta_ref from the
+        // FP32 storage shift (w theta_ref has no J or P_ab part)
+        const double th = (double)m.th * K.scale + K.mshift_th;
+        const Coll<double> &kd = K.kd;
+        eterm = th * fma(kd.c0, l0, fma(kd.cA, sax, kd.wd * sdg));
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const double Paa = (double)m.Paa[a] * K.scale + K.mshift_paa;
+            eterm = fma(Paa, kd.k2 * (s[a] - 2.0 * l0), eterm);
+            eterm = fma((double)m.J[a] * K.scale, kd.k1 * dd[a], eterm);
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) eterm = fma((double)m.Pab[p] * K.scale, kd.k3 * P[p], eterm);
+    }
+    const Coll<double> &k = K.k;
+    const double Lt = fma(k.c0, l0, fma(k.cA, sax, k.wd * sdg));
+    double LP[D], LJ[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        LP[a] = k.k2 * (s[a] - 2.0 * l0);
+        LJ[a] = k.k1 * dd[a];
     }
     l[0] = Lt;
-    static_for<1, L::Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
-        double v = Lt;
-        if constexpr (ex != 0) v += Laa[0] + ex * Ja[0];
-        if constexpr (ey != 0) v += Laa[1] + ey * Ja[1];
-        if constexpr (ez != 0) v += Laa[2] + ez * Ja[2];
-        if constexpr (ex != 0 && ey != 0) v += ex * ey * Lab[0];
-        if constexpr (ex != 0 && ez != 0) v += ex * ez * Lab[1];
-        if constexpr (ey != 0 && ez != 0) v += ey * ez * Lab[2];
-        l[i] = v;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const double base = Lt + LP[a];
+        l[1 + a] = base + LJ[a];
+        l[1 + D + a] = base - LJ[a];
+    }
+    static_for<0, NP>([&](auto Pi) {
+        constexpr int p = decltype(Pi)::value;
+        constexpr int a = pair_a<D>(p), b = pair_b<D>(p);
+        const double X = Lt + (LP[a] + LP[b]);
+        const double U = LJ[a] + LJ[b], W = LJ[a] - LJ[b];
+        const double lab = k.k3 * P[p];
+        const double Xp = X + lab, Xm = X - lab;
+        l[B0 + 4 * p] = Xp + U;      // (+1, +1)
+        l[B0 + 4 * p + 1] = Xm - W;  // (-1, +1)
+        l[B0 + 4 * p + 2] = Xp - U;  // (-1, -1)
+        l[B0 + 4 * p + 3] = Xm + W;  // (+1, -1)
     });
+    return eterm;
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -184,27 +244,19 @@ __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const double *_
     double lam[L::Q][V];
     gather_rev<L>(phi_in, g, row, x0, lane, lam);
     double acc = 0.0;
-    if constexpr (NU) {
-        T f[L::Q][V];
-        gather<L, T, V>(Pn, g, row, x0, lane, f);
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            double fd[L::Q];
-#pragma unroll
-            for (int i = 0; i < L::Q; ++i) fd[i] = to_f(f[i][v], K.scale) + K.shift[i];
-            collide(L{}, fd, K.kd);
-            double s = 0.0;
-#pragma unroll
-            for (int i = 0; i < L::Q; ++i) s = fma(lam[i][v], fd[i], s);
-            if (x0 + V * lane + v < g.N0) acc += s;
-        }
-    }
+    T f[L::Q][V];
+    if constexpr (NU) gather<L, T, V>(Pn, g, row, x0, lane, f);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         double l[L::Q];
+        T fv[L::Q];
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) l[i] = lam[i][v];
-        apply_KT<L>(l, K.k);
+        for (int i = 0; i < L::Q; ++i) {
+            l[i] = lam[i][v];
+            if constexpr (NU) fv[i] = f[i][v];
+        }
+        const double e = adj_node<L, T, NU>(l, fv, K);
+        if (NU && x0 + V * lane + v < g.N0) acc += e;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) lam[i][v] = l[i];
     }
@@ -406,8 +458,12 @@ void make_adjk(lb_adj *a)
         K.shift[i] = 0.0;
     }
     K.scale = (c.precision == LB_FX64) ? ldexp(1.0, -c.fx_bits) : 1.0;
-    if (c.precision == LB_FP32_SHIFTED)  // stored f - w theta_ref
+    K.mshift_th = K.mshift_paa = 0.0;
+    if (c.precision == LB_FP32_SHIFTED) {  // stored f - w theta_ref
         for (int i = 0; i < q; ++i) K.shift[i] = w[i] * c.theta_ref;
+        K.mshift_th = c.theta_ref;
+        K.mshift_paa = sigma * c.theta_ref;
+    }
     K.ucoef = (2.0 - c.s1) * c.c;
     K.ducoef = -ds1 * c.c;
     K.iax = 0.5 * c.dx * (sigma / c.s1 - 4.0 * (d - 1) * wd);
