@@ -92,3 +92,88 @@ def test_fullsize_fp32_shifted(case, ref):
     # stored values are O(1): float rounding of a handful of operations per step
     assert worst["theta"] <= 1e-6 and worst["u"] <= 1e-4, worst
     assert abs(total - t0) <= 1e-6 * t0
+
+
+def _mirror_index(k, n):
+    """Node of the evenly doubled axis (period 2(n-1)) folded back into
+    0..n-1, and the sign of the wall-normal gradient component there."""
+    p = 2 * (n - 1)
+    j = np.mod(k, p)
+    refl = j > n - 1
+    return np.where(refl, p - j, j), np.where(refl, -1.0, 1.0)
+
+
+def _patch_walls(field, center, half, mirror, vector=False):
+    """Patch of side 2*half+1 around `center` on the grid doubled by even
+    reflection across the walls of each mirror axis (periodic elsewhere);
+    for a vector field the wall-normal component is odd (zero on the wall)."""
+    d = len(center)
+    lead = 1 if vector else 0
+    out = np.array(field, dtype=np.float64)
+    if vector:
+        for a in range(d):
+            if mirror[a]:
+                n = field.shape[lead + d - 1 - a]
+                sl = [slice(None)] * out.ndim
+                sl[0] = a
+                for j in (0, n - 1):
+                    sl[lead + d - 1 - a] = j
+                    out[tuple(sl)] = 0.0
+    for a in range(d):
+        ax = lead + (d - 1 - a)
+        n = field.shape[ax]
+        k = np.arange(center[a] - half, center[a] + half + 1)
+        if mirror[a]:
+            idx, sgn = _mirror_index(k, n)
+            out = np.take(out, idx, axis=ax)
+            if vector:
+                shape = [1] * out.ndim
+                shape[ax] = len(k)
+                out[a] = out[a] * sgn.reshape(shape[1:])
+        else:
+            out = np.take(out, k % n, axis=ax)
+    return out
+
+
+def _check_walls(case, mirror, precision, nsteps):
+    N, d = case.N, case.d
+    th0 = case.problem.theta(N, case.dx)
+    g0 = np.ascontiguousarray(case.problem.grad(N, case.dx))
+    kinds = ["mirror" if m else "periodic" for m in mirror]
+    s = lb.Solver(d, N, case.nu, case.dx, case.dt, precision=precision, boundary=kinds)
+    s.set_theta0(torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda())
+    s.step(nsteps)
+    th, _, u = s.macros()
+    th, u = th.cpu().numpy(), u.cpu().numpy()
+    s.close()
+    half = nsteps + 1
+    P = 2 * half + 1
+    m = O.Model(d, [P] * d, case.nu, case.dx, case.dt)
+    rng = np.random.default_rng(98)
+    worst = {"theta": 0.0, "u": 0.0}
+    scale_t, scale_u = float(np.max(np.abs(th))), float(np.max(np.abs(u)))
+    pts = _samples(N, rng) + [tuple([1] + [n - 2 for n in N[1:]]), tuple([N[0] - 2] + [1] * (d - 1))]
+    for c in pts:
+        pt = _patch_walls(th0, c, half, mirror)
+        pg = _patch_walls(g0, c, half, mirror, vector=True)
+        tho, _, uo = m.recover(m.run(m.initialize(pt, pg), nsteps))
+        mid = (half,) * d
+        got_t = th[tuple(reversed(c))]
+        got_u = u[(slice(None),) + tuple(reversed(c))]
+        worst["theta"] = max(worst["theta"], abs(got_t - tho[mid]) / scale_t)
+        worst["u"] = max(worst["u"], float(np.max(np.abs(got_u - uo[(slice(None),) + mid])) / scale_u))
+    return worst
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fx64"])
+def test_fullsize_2d_4096_walls(precision):
+    """4096^2 with walls on both axes (corners included among the samples)."""
+    worst = _check_walls(W.sine_2d(4096), (True, True), precision, 3)
+    assert worst["theta"] <= 1e-12 and worst["u"] <= 1e-12, worst
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fx64"])
+def test_fullsize_3d_256_walls(precision):
+    """256^3 with walls on x and z, periodic y."""
+    worst = _check_walls(W.fourier_3d(256), (True, False, True), precision, 2)
+    assert worst["theta"] <= 1e-12 and worst["u"] <= 1e-12, worst

@@ -37,3 +37,35 @@ def test_oracle_adjoint_matches_finite_differences(d, N, T):
     hn = 1e-6 * nu
     fd_nu = (O.Model(d, N, nu + hn, dx, dt).loss(th0, ut, T) - O.Model(d, N, nu - hn, dx, dt).loss(th0, ut, T)) / (2 * hn)
     assert dnu == pytest.approx(fd_nu, rel=2e-6)
+
+
+@pytest.mark.parametrize("d,N,T", [(1, (6,), 7), (2, (5, 4), 4)])
+def test_oracle_adjoint_matches_dense_jacobian(d, N, T):
+    """Exact check without finite-difference truncation: theta0 -> f_T is
+    linear (initialisation with the FD4 gradient, then T linear steps), so
+    its columns are forward runs of unit vectors; u = (2 - s1) c J / theta is
+    then differentiated by hand, giving dL/dtheta0 to rounding."""
+    th0, ut, nu, dx, dt = _case(d, N, T, 41 + d)
+    m = O.Model(d, N, nu, dx, dt)
+    _, g, _ = m.adjoint(th0, ut, T)
+    e = m.matrices()["e"]  # (q, d) lattice velocities
+    p = m.params
+    ucoef = (2.0 - p["s1"]) * p["c"]
+
+    def moments(f):
+        th = f.sum(axis=0)
+        J = np.stack([np.tensordot(e[:, a], f, axes=(0, 0)) for a in range(d)])
+        return th, J
+
+    fT = m.run(m.initialize(th0), T)
+    th, J = moments(fT)
+    u = ucoef * J / th[None]
+    r = u - ut
+    dense = np.zeros(th0.size)
+    for j in range(th0.size):
+        ej = np.zeros(th0.size)
+        ej[j] = 1.0
+        dth, dJ = moments(m.run(m.initialize(ej.reshape(th0.shape)), T))
+        du = ucoef * (dJ * th[None] - J * dth[None]) / (th[None] ** 2)
+        dense[j] = np.sum(r * du)
+    assert np.max(np.abs(g.ravel() - dense)) <= 1e-12 * np.max(np.abs(dense))
