@@ -10,7 +10,7 @@
  *   dL/dtheta0 (one value per node) and dL/dnu (through eps = nu dt/dx^2 and
  *   the relaxation set of Theorem 2, Eq. (Bur-Sol); dx and dt fixed).
  * Reverse step: phi_n(x) = K^T [phi_{n+1}(x + e_i)_i]_i (reversed streaming,
- * transposed collision, FP64), plus the eps-derivative term
+ * transposed collision), plus the eps-derivative term
  * lambda_{n+1} . (dK/deps) f_n(x), which needs the forward states f_n: they
  * are kept as checkpoints every C steps and recomputed one segment at a
  * time (C = ceil(sqrt(T)) stores about 2 sqrt(T) states).
@@ -30,15 +30,19 @@ extern "C" {
 typedef struct lb_adj lb_adj;
 
 /*
- * Adjoint workspace for `ctx` (any precision: the forward states are read in
- * their storage type, the adjoint itself is FP64; d = 1, 2, 3).
+ * Adjoint workspace for `ctx` (any precision; d = 1, 2, 3; periodic grids).
+ * The forward states are read in their storage type.  The reverse pass
+ * computes in FP64 for LB_FP64 and LB_FX64 contexts and in FP32 for
+ * LB_FP32_SHIFTED contexts (whose forward map is FP32-accurate); the seed,
+ * the initialisation adjoint and the dL/dnu accumulation are FP64 always.
  *   T        forward steps (>= 1).
  *   C        checkpoint interval, 1 <= C <= T, or 0 for ceil(sqrt(T)).
  *   want_nu  nonzero to also compute dL/dnu (needs the paper's relaxation
  *            set; keeps checkpoints and recomputes segments); zero computes
  *            dL/dtheta0 only and keeps no forward states.
- * Allocates ceil(T/C) + C state copies (want_nu) and two FP64 adjoint
- * fields.  The context must outlive the workspace.
+ * Allocates ceil(T/C) + C state copies (want_nu) and two adjoint fields
+ * (FP64, or FP32 for LB_FP32_SHIFTED).  The context must outlive the
+ * workspace.
  * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA.
  */
 lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_adj **out);

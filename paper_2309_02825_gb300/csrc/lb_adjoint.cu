@@ -31,6 +31,7 @@ constexpr int kAdjQ = 19;
 struct AdjK {
     Coll<double> k;   // collision constants
     Coll<double> kd;  // their eps-derivatives
+    Coll<float> kf, kdf;  // the same in float, for the FP32 reverse pass of FP32-shifted states
     double scale;     // stored value -> f: f_i = v * scale + shift[i]
     double shift[kAdjQ];
     double mshift_th, mshift_paa;  // the shift's moments: theta_ref and sigma theta_ref
@@ -43,9 +44,9 @@ struct AdjK {
 template <typename T> __device__ __forceinline__ double to_f(T v, double scale) { return (double)v * scale; }
 
 // Reverse pull: out[k] = phi(x + e_i) for the V nodes of this lane.
-template <class L>
-__device__ __forceinline__ void gather_rev(const double *__restrict__ src, const Geom &g, int64_t row, int x0,
-                                           int lane, double (&f)[L::Q][2])
+template <class L, typename A>
+__device__ __forceinline__ void gather_rev(const A *__restrict__ src, const Geom &g, int64_t row, int x0, int lane,
+                                           A (&f)[L::Q][2])
 {
     const int y = (int)(row % g.N1);
     const int z = (int)(row / g.N1);
@@ -54,8 +55,8 @@ __device__ __forceinline__ void gather_rev(const double *__restrict__ src, const
         constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
         const int ys = (ey == 0) ? y : wrapi(y + ey, g.N1);
         const int zs = (ez == 0) ? z : wrapi(z + ez, g.N2);
-        const double *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
-        pull_row<double, -ex>(rp, x0, lane, g.N0, f[i], rp, g.N0 - 1, 0);
+        const A *rp = src + (int64_t)i * g.slab + ((int64_t)zs * g.N1 + ys) * g.pitch;
+        pull_row<A, -ex, 2>(rp, x0, lane, g.N0, f[i], rp, g.N0 - 1, 0);
     });
 }
 
@@ -90,16 +91,28 @@ template <class L, typename A> __device__ __forceinline__ NodeMoments<L, A> node
     return m;
 }
 
+// Fused multiply-add in the adjoint's own type (fmaf keeps float arithmetic in float).
+__device__ __forceinline__ float fma_a(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_a(double a, double b, double c) { return fma(a, b, c); }
+
+template <typename A> __device__ __forceinline__ const Coll<A> &coll_k(const AdjK &K);
+template <> __device__ __forceinline__ const Coll<double> &coll_k<double>(const AdjK &K) { return K.k; }
+template <> __device__ __forceinline__ const Coll<float> &coll_k<float>(const AdjK &K) { return K.kf; }
+template <typename A> __device__ __forceinline__ const Coll<A> &coll_kd(const AdjK &K);
+template <> __device__ __forceinline__ const Coll<double> &coll_kd<double>(const AdjK &K) { return K.kd; }
+template <> __device__ __forceinline__ const Coll<float> &coll_kd<float>(const AdjK &K) { return K.kdf; }
+
 // One node of the reverse step: l <- K^T l in place (shared sub-sums, as
 // in the forward collision); with NU, also returns lambda . (dK/deps) f for
 // the node's pre-collision f (stored values fv: f = fv scale + shift).
-template <class L, typename T, bool NU>
-__device__ __forceinline__ double adj_node(double *l, const T *fv, const AdjK &K)
+// A is the adjoint's arithmetic: double, or float for FP32-shifted states.
+template <class L, typename T, bool NU, typename A>
+__device__ __forceinline__ double adj_node(A *l, const T *fv, const AdjK &K)
 {
     constexpr int D = L::D, NP = D * (D - 1) / 2, B0 = 1 + 2 * D;
-    const double l0 = l[0];
-    double s[D], dd[D], F[NP > 0 ? NP : 1], P[NP > 0 ? NP : 1];
-    double sax = 0.0, sdg = 0.0;
+    const A l0 = l[0];
+    A s[D], dd[D], P[NP > 0 ? NP : 1];
+    A sax = 0, sdg = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         s[a] = l[1 + a] + l[1 + D + a];
@@ -108,56 +121,73 @@ __device__ __forceinline__ double adj_node(double *l, const T *fv, const AdjK &K
     }
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        const Plane<double> pl = plane(l[B0 + 4 * p], l[B0 + 4 * p + 1], l[B0 + 4 * p + 2], l[B0 + 4 * p + 3]);
-        F[p] = pl.F;
+        const Plane<A> pl = plane(l[B0 + 4 * p], l[B0 + 4 * p + 1], l[B0 + 4 * p + 2], l[B0 + 4 * p + 3]);
         P[p] = pl.P;
         sdg += pl.F;
     }
-    double eterm = 0.0;
+    A eterm = 0;
     if constexpr (NU) {
         const NodeMoments<L, T> m = node_moments<L, T>(fv);
-        // f moments in FP64: theta = sum f, P_aa gains sigma theta_ref from the
-        // FP32 storage shift (w theta_ref has no J or P_ab part)
-        const double th = (double)m.th * K.scale + K.mshift_th;
-        const Coll<double> &kd = K.kd;
-        eterm = th * fma(kd.c0, l0, fma(kd.cA, sax, kd.wd * sdg));
+        // f moments: theta = sum f, P_aa gains sigma theta_ref from the FP32
+        // storage shift (w theta_ref has no J or P_ab part)
+        A th, Paa[D], J[D], Pab[NP > 0 ? NP : 1];
+        if constexpr (std::is_same<A, float>::value && std::is_same<T, float>::value) {
+            th = m.th + (float)K.mshift_th;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                Paa[a] = m.Paa[a] + (float)K.mshift_paa;
+                J[a] = m.J[a];
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p) Pab[p] = m.Pab[p];
+        } else {
+            th = (A)((double)m.th * K.scale + K.mshift_th);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                Paa[a] = (A)((double)m.Paa[a] * K.scale + K.mshift_paa);
+                J[a] = (A)((double)m.J[a] * K.scale);
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p) Pab[p] = (A)((double)m.Pab[p] * K.scale);
+        }
+        const Coll<A> &kd = coll_kd<A>(K);
+        eterm = th * fma_a(kd.c0, l0, fma_a(kd.cA, sax, kd.wd * sdg));
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            const double Paa = (double)m.Paa[a] * K.scale + K.mshift_paa;
-            eterm = fma(Paa, kd.k2 * (s[a] - 2.0 * l0), eterm);
-            eterm = fma((double)m.J[a] * K.scale, kd.k1 * dd[a], eterm);
+            eterm = fma_a(Paa[a], kd.k2 * (s[a] - (A)2 * l0), eterm);
+            eterm = fma_a(J[a], kd.k1 * dd[a], eterm);
         }
 #pragma unroll
-        for (int p = 0; p < NP; ++p) eterm = fma((double)m.Pab[p] * K.scale, kd.k3 * P[p], eterm);
+        for (int p = 0; p < NP; ++p) eterm = fma_a(Pab[p], kd.k3 * P[p], eterm);
     }
-    const Coll<double> &k = K.k;
-    const double Lt = fma(k.c0, l0, fma(k.cA, sax, k.wd * sdg));
-    double LP[D], LJ[D];
+    const Coll<A> &k = coll_k<A>(K);
+    const A Lt = fma_a(k.c0, l0, fma_a(k.cA, sax, k.wd * sdg));
+    A LP[D], LJ[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        LP[a] = k.k2 * (s[a] - 2.0 * l0);
+        LP[a] = k.k2 * (s[a] - (A)2 * l0);
         LJ[a] = k.k1 * dd[a];
     }
     l[0] = Lt;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const double base = Lt + LP[a];
+        const A base = Lt + LP[a];
         l[1 + a] = base + LJ[a];
         l[1 + D + a] = base - LJ[a];
     }
     static_for<0, NP>([&](auto Pi) {
         constexpr int p = decltype(Pi)::value;
         constexpr int a = pair_a<D>(p), b = pair_b<D>(p);
-        const double X = Lt + (LP[a] + LP[b]);
-        const double U = LJ[a] + LJ[b], W = LJ[a] - LJ[b];
-        const double lab = k.k3 * P[p];
-        const double Xp = X + lab, Xm = X - lab;
+        const A X = Lt + (LP[a] + LP[b]);
+        const A U = LJ[a] + LJ[b], W = LJ[a] - LJ[b];
+        const A lab = k.k3 * P[p];
+        const A Xp = X + lab, Xm = X - lab;
         l[B0 + 4 * p] = Xp + U;      // (+1, +1)
         l[B0 + 4 * p + 1] = Xm - W;  // (-1, +1)
         l[B0 + 4 * p + 2] = Xp - U;  // (-1, -1)
         l[B0 + 4 * p + 3] = Xm + W;  // (+1, -1)
     });
-    return eterm;
+    return (double)eterm;
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -168,10 +198,10 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 // phi_T = dL/df_T through u_a = ucoef J_a / theta; eps-term of the recovery.
-template <class L, typename T>
+template <class L, typename T, typename A>
 __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__restrict__ P, Geom g, AdjK K,
                                                                  const double *__restrict__ dLdu,
-                                                                 double *__restrict__ phi, double *__restrict__ slot)
+                                                                 A *__restrict__ phi, double *__restrict__ slot)
 {
     constexpr int V = 2;
     const int lane = threadIdx.x & 31;
@@ -220,20 +250,24 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
         });
     }
     if (x0 + V * lane < g.pitch) {  // lanes beyond the row only loaded
-        double *dp = phi + row * g.pitch + x0 + V * lane;
+        A *dp = phi + row * g.pitch + x0 + V * lane;
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, out[i]);
+        for (int i = 0; i < L::Q; ++i) {
+            A o[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) o[v] = (A)out[i][v];
+            st_vec(dp + (int64_t)i * g.slab, o);
+        }
     }
     acc = warp_sum(acc);
     if (lane == 0) slot[seg] += acc;
 }
 
 // One reverse step: phi_out = K^T lambda(phi_in); eps-term if NU.
-template <class L, typename T, bool NU>
-__global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const double *__restrict__ phi_in,
-                                                                 const T *__restrict__ Pn,
-                                                                 double *__restrict__ phi_out, Geom g, AdjK K,
-                                                                 double *__restrict__ slot)
+template <class L, typename T, bool NU, typename A>
+__global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const A *__restrict__ phi_in,
+                                                                 const T *__restrict__ Pn, A *__restrict__ phi_out,
+                                                                 Geom g, AdjK K, double *__restrict__ slot)
 {
     constexpr int V = 2;
     const int lane = threadIdx.x & 31;
@@ -241,27 +275,27 @@ __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const double *_
     if (seg >= g.nseg) return;
     const int64_t row = seg / g.seg_per_row;
     const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
-    double lam[L::Q][V];
-    gather_rev<L>(phi_in, g, row, x0, lane, lam);
+    A lam[L::Q][V];
+    gather_rev<L, A>(phi_in, g, row, x0, lane, lam);
     double acc = 0.0;
     T f[L::Q][V];
     if constexpr (NU) gather<L, T, V>(Pn, g, row, x0, lane, f);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        double l[L::Q];
+        A l[L::Q];
         T fv[L::Q];
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
             l[i] = lam[i][v];
             if constexpr (NU) fv[i] = f[i][v];
         }
-        const double e = adj_node<L, T, NU>(l, fv, K);
+        const double e = adj_node<L, T, NU, A>(l, fv, K);
         if (NU && x0 + V * lane + v < g.N0) acc += e;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) lam[i][v] = l[i];
     }
     if (x0 + V * lane < g.pitch) {  // lanes beyond the row only loaded
-        double *dp = phi_out + row * g.pitch + x0 + V * lane;
+        A *dp = phi_out + row * g.pitch + x0 + V * lane;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, lam[i]);
     }
@@ -274,8 +308,8 @@ __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const double *_
 // Adjoint of the initialisation f_i = w_i theta0 - sum_a A_ia d_a theta0:
 // dtheta0 = sum_i w_i phi_i, h_a = -sum_i A_ia phi_i (fed to G^T), and the
 // eps-term sum_i phi_i (w_i' theta0 - sum_a A'_ia d_a theta0).
-template <class L>
-__global__ void adj_init_kernel(const double *__restrict__ phi, Geom g, AdjK K, const double *__restrict__ th0,
+template <class L, typename A>
+__global__ void adj_init_kernel(const A *__restrict__ phi, Geom g, AdjK K, const double *__restrict__ th0,
                                 const double *__restrict__ grad, double *__restrict__ dth0,
                                 double *__restrict__ h, double *__restrict__ slot)
 {
@@ -285,7 +319,7 @@ __global__ void adj_init_kernel(const double *__restrict__ phi, Geom g, AdjK K, 
     if (n < nodes) {
         const int x = (int)(n % g.N0);
         const int64_t rw = n / g.N0;
-        const double *p = phi + rw * g.pitch + x;
+        const A *p = phi + rw * g.pitch + x;
         const double t0 = th0[n];
         double gr[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -295,7 +329,7 @@ __global__ void adj_init_kernel(const double *__restrict__ phi, Geom g, AdjK K, 
             constexpr int i = decltype(I)::value;
             constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
             constexpr int nz = (ex != 0) + (ey != 0) + (ez != 0);
-            const double ph = p[(int64_t)i * g.slab];
+            const double ph = (double)p[(int64_t)i * g.slab];
             s = fma(K.w[i], ph, s);
             double dfi = K.dw[i] * t0;
             if constexpr (nz == 1) {
@@ -376,7 +410,7 @@ struct lb_adj {
     std::vector<void *> ck;   // checkpoints P_{kC}
     std::vector<void *> seg;  // recomputed segment P_{kC + m}
     int64_t seg_loaded = -1;
-    double *phi[2] = {nullptr, nullptr};
+    void *phi[2] = {nullptr, nullptr};  // adjoint fields: float for FP32-shifted states, else double
     int pcur = 0;
     double *th0 = nullptr, *grad = nullptr, *h = nullptr;
     double *slot_step = nullptr, *slot_init = nullptr, *dsum = nullptr;
@@ -444,6 +478,8 @@ void make_adjk(lb_adj *a)
     K.kd.c0 = -d * (ds2x * sigma + c.s2x * dsigma) + 2.0 * d * (d - 1) * dwd;
     K.kd.cA = (ds2x * sigma + c.s2x * dsigma) / 2.0 - 2.0 * (d - 1) * dwd;
     K.kd.wd = dwd;
+    K.kf = lbk::make_coll<float>(c);
+    K.kdf = {(float)K.kd.k1, (float)K.kd.k2, (float)K.kd.k3, (float)K.kd.c0, (float)K.kd.cA, (float)K.kd.wd};
     const int q = c.q;
     double w[lbk::kAdjQ], dw[lbk::kAdjQ];
     w[0] = c.w0;
@@ -475,24 +511,31 @@ void make_adjk(lb_adj *a)
 
 int64_t sweep_blocks(const lbk::Geom &g) { return (g.nseg + lbk::kSweepThreads / 32 - 1) / (lbk::kSweepThreads / 32); }
 
+// The adjoint's arithmetic for a storage type: float for FP32-shifted states
+// (whose forward map is only FP32-accurate), double otherwise.
+template <typename T> using AdjT = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+
 template <class L, typename T> cudaError_t seed_t(lb_adj *a, const double *dLdu)
 {
     lb_ctx *c = a->ctx;
-    lbk::adj_seed_kernel<L, T><<<(unsigned)sweep_blocks(a->ag), lbk::kSweepThreads, 0, c->stream>>>(
-        (const T *)c->f[c->cur], a->ag, a->K, dLdu, a->phi[a->pcur], a->slot_step);
+    lbk::adj_seed_kernel<L, T, AdjT<T>><<<(unsigned)sweep_blocks(a->ag), lbk::kSweepThreads, 0, c->stream>>>(
+        (const T *)c->f[c->cur], a->ag, a->K, dLdu, (AdjT<T> *)a->phi[a->pcur], a->slot_step);
     return cudaGetLastError();
 }
 
 template <class L, typename T> cudaError_t step_t(lb_adj *a, const void *Pn)
 {
+    using A = AdjT<T>;
     lb_ctx *c = a->ctx;
     const unsigned nb = (unsigned)sweep_blocks(a->ag);
+    const A *in = (const A *)a->phi[a->pcur];
+    A *out = (A *)a->phi[a->pcur ^ 1];
     if (a->want_nu)
-        lbk::adj_step_kernel<L, T, true><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
-            a->phi[a->pcur], (const T *)Pn, a->phi[a->pcur ^ 1], a->ag, a->K, a->slot_step);
+        lbk::adj_step_kernel<L, T, true, A><<<nb, lbk::kSweepThreads, 0, c->stream>>>(in, (const T *)Pn, out, a->ag,
+                                                                                      a->K, a->slot_step);
     else
-        lbk::adj_step_kernel<L, T, false><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
-            a->phi[a->pcur], (const T *)Pn, a->phi[a->pcur ^ 1], a->ag, a->K, a->slot_step);
+        lbk::adj_step_kernel<L, T, false, A><<<nb, lbk::kSweepThreads, 0, c->stream>>>(in, (const T *)Pn, out, a->ag,
+                                                                                       a->K, a->slot_step);
     return cudaGetLastError();
 }
 
@@ -500,8 +543,12 @@ template <class L> cudaError_t init_t(lb_adj *a, double *dth0)
 {
     lb_ctx *c = a->ctx;
     const unsigned nb = (unsigned)((c->nodes + 255) / 256);
-    lbk::adj_init_kernel<L><<<nb, 256, 0, c->stream>>>(a->phi[a->pcur], c->geom, a->K, a->th0, a->grad, dth0, a->h,
-                                                       a->slot_init);
+    if (c->precision == LB_FP32_SHIFTED)
+        lbk::adj_init_kernel<L, float><<<nb, 256, 0, c->stream>>>((const float *)a->phi[a->pcur], c->geom, a->K,
+                                                                  a->th0, a->grad, dth0, a->h, a->slot_init);
+    else
+        lbk::adj_init_kernel<L, double><<<nb, 256, 0, c->stream>>>((const double *)a->phi[a->pcur], c->geom, a->K,
+                                                                   a->th0, a->grad, dth0, a->h, a->slot_init);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     lbk::adj_fd4t_kernel<<<nb, 256, 0, c->stream>>>(a->h, dth0, c->d, (int)c->N[0], (int)c->N[1], (int)c->N[2],
@@ -611,7 +658,8 @@ lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_a
     a->want_nu = want_nu != 0;
     a->state_bytes = (size_t)ctx->q * ctx->geom.slab * ctx->elem;
     cudaError_t e = cudaSuccess;
-    const size_t pbytes = ((size_t)ctx->q * ctx->geom.slab + lbk::kSlackElems) * sizeof(double);
+    const size_t aelem = (ctx->precision == LB_FP32_SHIFTED) ? sizeof(float) : sizeof(double);
+    const size_t pbytes = ((size_t)ctx->q * ctx->geom.slab + lbk::kSlackElems) * aelem;
     const size_t sbytes = a->state_bytes + lbk::kSlackElems * ctx->elem;  // allocation incl. slack
     if (a->want_nu) {
         a->nck = (T + C - 1) / C;
