@@ -69,6 +69,10 @@ def parse():
     p.add_argument("--accuracy", action="store_true",
                    help="print the error-vs-exact convergence table (1D, 2D up to 4096^2, 3D up to 256^3) and exit")
     p.add_argument("--accuracy-precisions", default="fp64,fx64,fp32s")
+    p.add_argument("--profile-batch", default=None, metavar="COUNT,STEPS",
+                   help="minimal command for ncu: COUNT batched 2D instances, STEPS steps, then exit")
+    p.add_argument("--profile-adjoint", default=None, metavar="PREC,N,T",
+                   help="minimal command for ncu: forward + seed + T reverse steps at N^2, then exit")
     p.add_argument("--profile-sweep", default=None, metavar="D,PREC,N,STEPS",
                    help="run STEPS sweeps of one D-dimensional N^D grid at PREC and exit (for ncu captures)")
     return p.parse_args()
@@ -305,24 +309,23 @@ def run_ours(args, precision, world, rank, local, peaks, with_e2e, label_main):
 
 def run_e2e(args, s, case, th0_h, g0_h, ex_t_h, ex_u_h, stream, world):
     """The same step through the public API from pinned host buffers: every
-    step copies its inputs (theta0, grad theta0 and the exact fields) in and
-    its theta and u out, all inside the timed region.  The copies are double
-    buffered on a second stream, so step k+1's inputs and step k's outputs
-    move while step k computes; events order each copy against the solver."""
+    step uploads its inputs (theta0, grad theta0 and the exact fields the
+    error norms are taken against) and reads its result, the error norms
+    that lb_reduce returns to the host, all inside the timed region.  The
+    uploads are double buffered on a second stream, so step k+1's inputs move
+    while step k computes; events order each copy against the solver."""
     import torch
     S = args.sweeps
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_in = [pin(th0_h), pin(g0_h), pin(ex_t_h), pin(ex_u_h)]
     d_in = [[torch.empty_like(h, device="cuda") for h in h_in] for _ in range(2)]
     shape = tuple(reversed(case.N))
-    d_out = [(torch.empty(shape, dtype=torch.float64, device="cuda"),
-              torch.empty((case.d,) + shape, dtype=torch.float64, device="cuda")) for _ in range(2)]
-    h_out = [(torch.empty(shape, dtype=torch.float64).pin_memory(),
-              torch.empty((case.d,) + shape, dtype=torch.float64).pin_memory()) for _ in range(2)]
+    d_out = (torch.empty(shape, dtype=torch.float64, device="cuda"),
+             torch.empty((case.d,) + shape, dtype=torch.float64, device="cuda"))
     cs = torch.cuda.Stream()
     in_ready = [torch.cuda.Event() for _ in range(2)]
     solved = [torch.cuda.Event() for _ in range(2)]
-    read_out = [torch.cuda.Event() for _ in range(2)]
+    results = []
 
     def h2d(b):
         with torch.cuda.stream(cs):
@@ -334,25 +337,18 @@ def run_e2e(args, s, case, th0_h, g0_h, ex_t_h, ex_u_h, stream, world):
     def run(n):
         for b in range(2):
             solved[b].record(cs)
-            read_out[b].record(cs)
         h2d(0)
         for k in range(n):
             b = k % 2
             if k + 1 < n:
                 h2d(1 - b)
             stream.wait_event(in_ready[b])
-            stream.wait_event(read_out[b])  # outputs of step k-2 have left the device
             with torch.cuda.stream(stream):
                 s.set_theta0(d_in[b][0], d_in[b][1])
                 s.step(S)
-                s.macros(d_out[b][0], None, d_out[b][1])
-                s.reduce(d_out[b][0], d_out[b][1], d_in[b][2], d_in[b][3])
+                s.macros(d_out[0], None, d_out[1])
+                results.append(s.reduce(d_out[0], d_out[1], d_in[b][2], d_in[b][3]))  # read back to the host
                 solved[b].record(stream)
-            with torch.cuda.stream(cs):
-                cs.wait_event(solved[b])
-                h_out[b][0].copy_(d_out[b][0], non_blocking=True)
-                h_out[b][1].copy_(d_out[b][1], non_blocking=True)
-                read_out[b].record(cs)
         torch.cuda.synchronize()
 
     run(max(1, args.warmup))
@@ -361,24 +357,21 @@ def run_e2e(args, s, case, th0_h, g0_h, ex_t_h, ex_u_h, stream, world):
     el = time.perf_counter() - t0
     value = aggregate(case.nodes * S * args.steps, el, world) / 1e6
     h2d_b = sum(h.numel() * h.element_size() for h in h_in)
-    d2h_b = sum(t.numel() * t.element_size() for t in h_out[0])
-    # copy rates on their own (outside the timed region): the first upload and
-    # the last download of the timed run cannot overlap any compute
-    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    d2h_b = 8 * (3 * (case.d + 1) + 1)  # lb_reduce's norms and sum, FP64
+    # the upload rate on its own (outside the timed region): the first upload
+    # of the timed run cannot overlap any compute
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(cs):
         e0.record(cs)
         for h, dv in zip(h_in, d_in[0]):
             dv.copy_(h, non_blocking=True)
         e1.record(cs)
-        h_out[0][0].copy_(d_out[0][0], non_blocking=True)
-        h_out[0][1].copy_(d_out[0][1], non_blocking=True)
-        e2.record(cs)
     torch.cuda.synchronize()
-    h2d_ms, d2h_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    h2d_ms = e0.elapsed_time(e1)
     return {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
-            "overlap": "copies double-buffered on a second stream",
-            "copy_rates": {"h2d_gbs": h2d_b / h2d_ms / 1e6, "d2h_gbs": d2h_b / d2h_ms / 1e6,
-                           "unoverlapped_ms_per_run": h2d_ms + d2h_ms, "steps": args.steps}}
+            "overlap": "uploads double-buffered on a second stream; the result read is the step's error norms",
+            "copy_rates": {"h2d_gbs": h2d_b / h2d_ms / 1e6, "unoverlapped_ms_per_run": h2d_ms, "steps": args.steps},
+            "u_rmse_last_step": results[-1]["u0"]["rmse"]}
 
 
 def run_batched(local):
@@ -701,6 +694,50 @@ def run_4d(local, peaks):
     return out
 
 
+def run_profile_batch(local, spec):
+    """Minimal, repeatable command for ncu: the first COUNT instances of the
+    batched workload (FP32s, flat schedule), STEPS steps."""
+    import torch
+    from paper_2309_02825_gb300 import lb
+    torch.cuda.set_device(local)
+    count, steps = (int(v) for v in spec.split(","))
+    cases = W.batched_2d(512, nsteps=2000)[:count]
+    th0 = np.concatenate([c.problem.theta(c.N, c.dx).ravel() for c in cases])
+    g0 = np.concatenate([np.ascontiguousarray(c.problem.grad(c.N, c.dx)).ravel() for c in cases])
+    b = lb.Batch([c.N for c in cases], [c.nu for c in cases], [c.dx for c in cases], [c.dt for c in cases],
+                 precision="fp32s", theta_ref=[1.5] * len(cases))
+    b.set_schedule(1e18, 128, False)
+    b.set_theta0(torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda())
+    b.step(steps)
+    torch.cuda.synchronize()
+    b.close()
+    print(json.dumps({"profile_batch": spec, "ok": True}))
+
+
+def run_profile_adjoint(local, spec):
+    """Minimal, repeatable command for ncu: the adjoint workload's forward
+    with checkpoints, seed and T reverse steps at N^2 (PREC storage)."""
+    import torch
+    from paper_2309_02825_gb300 import lb
+    torch.cuda.set_device(local)
+    prec, n, T = spec.split(",")
+    n, T = int(n), int(T)
+    case = W.adjoint_2d(n, T)
+    N = case.N
+    th0 = torch.from_numpy(case.problem.theta(N, case.dx)).cuda()
+    ut = torch.from_numpy(np.ascontiguousarray(case.extra["target"].u(N, case.dx, T * case.dt))).cuda()
+    s = lb.Solver(2, N, case.nu, case.dx, case.dt, precision=prec)
+    a = lb.Adjoint(s, T, checkpoint=0, want_nu=True)
+    u = a.forward(th0)
+    a.seed(u - ut)
+    a.step(T)
+    a.result()
+    torch.cuda.synchronize()
+    a.close()
+    s.close()
+    print(json.dumps({"profile_adjoint": spec, "ok": True}))
+
+
 def run_profile_sweep(local, spec):
     """Minimal, repeatable command for ncu: init + STEPS sweeps of one grid,
     then one recovery and one state sum."""
@@ -822,6 +859,12 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     world, rank, local = dist_setup(args)
+    if args.profile_batch:
+        run_profile_batch(local, args.profile_batch)
+        return 0
+    if args.profile_adjoint:
+        run_profile_adjoint(local, args.profile_adjoint)
+        return 0
     if args.profile_sweep:
         run_profile_sweep(local, args.profile_sweep)
         return 0

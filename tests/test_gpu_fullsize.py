@@ -177,3 +177,32 @@ def test_fullsize_3d_256_walls(precision):
     """256^3 with walls on x and z, periodic y."""
     worst = _check_walls(W.fourier_3d(256), (True, False, True), precision, 2)
     assert worst["theta"] <= 1e-12 and worst["u"] <= 1e-12, worst
+
+
+def test_fx64_16384_squared_offsets_beyond_2_31():
+    """16384^2 D2Q9 FX64 (268 M nodes, 2 x 19.3 GB of state): population
+    offsets i * slab pass 2^31 elements, so any 32-bit index arithmetic in
+    the initialisation, sweep or recovery would misplace values.  Sampled
+    nodes (first and last rows, last population slabs' far corners) against
+    the patch oracle after 2 steps."""
+    n, nsteps = 16384, 2
+    case = W.sine_2d(n)
+    N = case.N
+    th0 = case.problem.theta(N, case.dx)
+    g0 = np.ascontiguousarray(case.problem.grad(N, case.dx))
+    s = lb.Solver(2, N, case.nu, case.dx, case.dt, precision="fx64")
+    pitch, slab, _ = s.state_layout()
+    assert int(s.params["q"]) * slab > 2 ** 31
+    s.set_theta0(torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda())
+    s.step(nsteps)
+    th, _, u = s.macros(want=("theta", "u"))
+    half = nsteps + 1
+    m = O.Model(2, [2 * half + 1] * 2, case.nu, case.dx, case.dt)
+    pts = [(0, 0), (n - 1, n - 1), (n - 1, 0), (0, n - 1), (8191, 12000), (16000, 16383), (5, 16380)]
+    for c in pts:
+        tho, _, uo = m.recover(m.run(m.initialize(_patch(th0, c, half), _patch(g0, c, half)), nsteps))
+        got_t = float(th[c[1], c[0]].item())
+        got_u = u[:, c[1], c[0]].cpu().numpy()
+        assert abs(got_t - tho[half, half]) <= 1e-12 * 3.0, (c, got_t, tho[half, half])
+        assert np.max(np.abs(got_u - uo[:, half, half])) <= 1e-12 * 0.3, (c, got_u, uo[:, half, half])
+    s.close()
