@@ -88,16 +88,26 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+def kernel_source_sha():
+    """sha256 (16 hex digits) of the sweep kernels' sources with comments and
+    whitespace removed, so that only a change of code voids a capture."""
+    import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_2309_02825_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("lb_internal.cuh", "lb_device.cuh", "lb_kernels.cu", "lb_fx.cu"):
+        text = open(os.path.join(csrc, name)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()[:16]
+
+
 def profile_traffic(kernel_key):
     """DRAM bytes per launch from a committed ncu summary for this kernel,
     valid only while the kernel source is unchanged (same sha)."""
-    import hashlib
-    csrc = os.path.join(ROOT, "paper_2309_02825_gb300", "csrc")
     try:
-        h = hashlib.sha256()
-        for name in ("lb_internal.cuh", "lb_device.cuh", "lb_kernels.cu", "lb_fx.cu"):
-            h.update(open(os.path.join(csrc, name), "rb").read())
-        sha = h.hexdigest()[:16]
+        sha = kernel_source_sha()
         path = os.path.join(ROOT, "profiles", "traffic.txt")
         for line in open(path):
             parts = line.split()

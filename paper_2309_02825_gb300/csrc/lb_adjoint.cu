@@ -35,6 +35,7 @@ struct AdjK {
     double scale;     // stored value -> f: f_i = v * scale + shift[i]
     double shift[kAdjQ];
     double mshift_th, mshift_paa;  // the shift's moments: theta_ref and sigma theta_ref
+    float mshift_th_f, mshift_paa_f;
     double ucoef, ducoef;                      // (2 - s1) c and d/deps
     double w[kAdjQ], dw[kAdjQ];                // weights and d/deps
     double iax, idg, diax, didg;               // initialisation operator and d/deps
@@ -107,7 +108,7 @@ template <> __device__ __forceinline__ const Coll<float> &coll_kd<float>(const A
 // the node's pre-collision f (stored values fv: f = fv scale + shift).
 // A is the adjoint's arithmetic: double, or float for FP32-shifted states.
 template <class L, typename T, bool NU, typename A>
-__device__ __forceinline__ double adj_node(A *l, const T *fv, const AdjK &K)
+__device__ __forceinline__ A adj_node(A *l, const T *fv, const AdjK &K)
 {
     constexpr int D = L::D, NP = D * (D - 1) / 2, B0 = 1 + 2 * D;
     const A l0 = l[0];
@@ -132,10 +133,10 @@ __device__ __forceinline__ double adj_node(A *l, const T *fv, const AdjK &K)
         // storage shift (w theta_ref has no J or P_ab part)
         A th, Paa[D], J[D], Pab[NP > 0 ? NP : 1];
         if constexpr (std::is_same<A, float>::value && std::is_same<T, float>::value) {
-            th = m.th + (float)K.mshift_th;
+            th = m.th + K.mshift_th_f;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                Paa[a] = m.Paa[a] + (float)K.mshift_paa;
+                Paa[a] = m.Paa[a] + K.mshift_paa_f;
                 J[a] = m.J[a];
             }
 #pragma unroll
@@ -187,10 +188,10 @@ __device__ __forceinline__ double adj_node(A *l, const T *fv, const AdjK &K)
         l[B0 + 4 * p + 2] = Xp - U;  // (-1, -1)
         l[B0 + 4 * p + 3] = Xm + W;  // (+1, -1)
     });
-    return (double)eterm;
+    return eterm;
 }
 
-__device__ __forceinline__ double warp_sum(double v)
+template <typename A> __device__ __forceinline__ A warp_sum(A v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const A *__rest
     const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
     A lam[L::Q][V];
     gather_rev<L, A>(phi_in, g, row, x0, lane, lam);
-    double acc = 0.0;
+    A acc = 0;  // this lane's dL/deps terms, in the adjoint's arithmetic
     T f[L::Q][V];
     if constexpr (NU) gather<L, T, V>(Pn, g, row, x0, lane, f);
 #pragma unroll
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const A *__rest
             l[i] = lam[i][v];
             if constexpr (NU) fv[i] = f[i][v];
         }
-        const double e = adj_node<L, T, NU, A>(l, fv, K);
+        const A e = adj_node<L, T, NU, A>(l, fv, K);
         if (NU && x0 + V * lane + v < g.N0) acc += e;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) lam[i][v] = l[i];
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const A *__rest
     }
     if constexpr (NU) {
         acc = warp_sum(acc);
-        if (lane == 0) slot[seg] += acc;
+        if (lane == 0) slot[seg] += (double)acc;
     }
 }
 
@@ -500,6 +501,8 @@ void make_adjk(lb_adj *a)
         K.mshift_th = c.theta_ref;
         K.mshift_paa = sigma * c.theta_ref;
     }
+    K.mshift_th_f = (float)K.mshift_th;
+    K.mshift_paa_f = (float)K.mshift_paa;
     K.ucoef = (2.0 - c.s1) * c.c;
     K.ducoef = -ds1 * c.c;
     K.iax = 0.5 * c.dx * (sigma / c.s1 - 4.0 * (d - 1) * wd);

@@ -1,7 +1,10 @@
-// Device-side building blocks shared by the sweep, recovery and fixed-point
-// kernels: compile-time loops, periodic wrap, 16-byte vector access, the
-// shifted pull of one population along x, and the closed-form moment-space
-// collision for D1Q3, D2Q9 and D3Q19 (Eq. (distribution-f)).
+// Device-side building blocks shared by the sweep, recovery, fixed-point,
+// batched and adjoint kernels: compile-time loops, periodic wrap, vector
+// access, the 64x62-bit fixed-point product, the shifted pull of one
+// population along x, where a pull reads from on periodic and mirror-wall
+// grids (pop_source), the two gather orders, and the closed-form
+// moment-space collision for D1Q3, D2Q9, D3Q19 and D4Q33
+// (Eq. (distribution-f)) with the sweep kernel built from them.
 #pragma once
 
 #include "lb_internal.cuh"

@@ -152,7 +152,8 @@ constexpr int kFxCoefBits = 62;
 
 // Recovery constants (Sec. III.C): u_a = ucoef * J_a / theta with
 // ucoef = (2 - s1) c; grad_a = gcoef * J_a with gcoef = -s1 / (sigma dx);
-// J_a = sum_k e_ka f_k.
+// J_a = sum_k e_ka f_k, summed in storage units (both constants carry the
+// storage scale, 2^-F for 64-bit fixed point, 1 otherwise).
 struct Recov {
     double ucoef, gcoef, theta_ref;
 };

@@ -276,21 +276,27 @@ __global__ void __launch_bounds__(kRedThreads) sum_state_kernel(const T *__restr
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nrows = (int64_t)q * g.rows;
+    constexpr int U = 4;  // vectors in flight per lane
     for (int64_t r = warp; r < nrows; r += nwarps) {
         const T *rowp = src + r * g.pitch;
         const double rw = g.mirror ? row_wall_weight(g, r % g.rows) : 1.0;
-        for (int x0 = lane * V; x0 < g.N0; x0 += 32 * V) {
-            T a[V];
-            ld_vec(rowp + x0, a);
+        for (int x0 = lane * V; x0 < g.N0; x0 += U * 32 * V) {
+            T a[U][V];
 #pragma unroll
-            for (int k = 0; k < V; ++k) {
-                const int x = x0 + k;
-                if (x >= g.N0) continue;
-                if (!g.mirror) {
-                    acc += a[k];
-                } else {
-                    const double xw = ((g.mirror & 1u) && (x == 0 || x == g.N0 - 1)) ? 0.5 : 1.0;
-                    accw += (double)a[k] * (rw * xw);
+            for (int j = 0; j < U; ++j)
+                if (x0 + j * 32 * V < g.N0) ld_vec(rowp + x0 + j * 32 * V, a[j]);
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const int x = x0 + j * 32 * V + k;
+                    if (x >= g.N0) continue;
+                    if (!g.mirror) {
+                        acc += a[j][k];
+                    } else {
+                        const double xw = ((g.mirror & 1u) && (x == 0 || x == g.N0 - 1)) ? 0.5 : 1.0;
+                        accw += (double)a[j][k] * (rw * xw);
+                    }
                 }
             }
         }
@@ -313,25 +319,33 @@ __global__ void __launch_bounds__(kRedThreads) norms_kernel(const double *__rest
     Acc<NS> a;
 #pragma unroll
     for (int k = 0; k < NS; ++k) a.v[k] = 0.0;
+    // max |err| on the integer pipes: for non-negative doubles the bit
+    // patterns order like the values (a NaN error shows in the RMSE sums)
+    long long mx[D + 1];
+#pragma unroll
+    for (int c = 0; c <= D; ++c) mx[c] = 0;
+    constexpr long long kAbs = 0x7fffffffffffffffll;
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < nodes;
          n += (int64_t)gridDim.x * blockDim.x) {
         const double t = th[n], te = eth[n];
         const double e = t - te;
-        a.v[0] += e * e;
-        a.v[1] = fmax(a.v[1], fabs(e));
-        a.v[2] += te * te;
+        a.v[0] = fma(e, e, a.v[0]);
+        mx[0] = max(mx[0], __double_as_longlong(e) & kAbs);
+        a.v[2] = fma(te, te, a.v[2]);
         a.v[NS - 1] += t;
         if (u) {
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 const double uv = u[c * nodes + n], ue = eu[c * nodes + n];
                 const double eu2 = uv - ue;
-                a.v[3 * (c + 1) + 0] += eu2 * eu2;
-                a.v[3 * (c + 1) + 1] = fmax(a.v[3 * (c + 1) + 1], fabs(eu2));
-                a.v[3 * (c + 1) + 2] += ue * ue;
+                a.v[3 * (c + 1) + 0] = fma(eu2, eu2, a.v[3 * (c + 1) + 0]);
+                mx[c + 1] = max(mx[c + 1], __double_as_longlong(eu2) & kAbs);
+                a.v[3 * (c + 1) + 2] = fma(ue, ue, a.v[3 * (c + 1) + 2]);
             }
         }
     }
+#pragma unroll
+    for (int c = 0; c <= D; ++c) a.v[3 * c + 1] = __longlong_as_double(mx[c]);
     int op[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) op[k] = (k < NS - 1 && k % 3 == 1) ? 1 : 0;

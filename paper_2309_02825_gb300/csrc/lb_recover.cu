@@ -146,12 +146,12 @@ __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ sr
     const double thd = (double)th * scale + r.theta_ref;
     if (theta) theta[node] = thd;
     if (!(thd > 0.0) || !isfinite(thd)) atomicOr(flag, 1);
-    const double inv = 1.0 / thd;
+    const double cu = r.ucoef / thd;  // the storage scale is folded into ucoef and gcoef
 #pragma unroll
     for (int a = 0; a < L::D; ++a) {
-        const double Ja = (double)J[a] * scale;
+        const double Ja = (double)J[a];
         if (grad) grad[a * nodes + node] = r.gcoef * Ja;
-        if (u) u[a * nodes + node] = r.ucoef * Ja * inv;
+        if (u) u[a * nodes + node] = cu * Ja;
     }
 }
 
@@ -165,10 +165,11 @@ static cudaError_t recover_t(lb_ctx *c, const void *src, double *th, double *gr,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     Recov r;
-    r.ucoef = (2.0 - c->s1) * c->c;
-    r.gcoef = -c->s1 / (c->sigma * c->dx);
-    r.theta_ref = (c->precision == LB_FP32_SHIFTED) ? c->theta_ref : 0.0;
     const double scale = (c->precision == LB_FX64) ? ldexp(1.0, -c->fx_bits) : 1.0;
+    // J is summed in storage units: the scale (a power of two, exact) goes into the constants
+    r.ucoef = (2.0 - c->s1) * c->c * scale;
+    r.gcoef = -c->s1 / (c->sigma * c->dx) * scale;
+    r.theta_ref = (c->precision == LB_FP32_SHIFTED) ? c->theta_ref : 0.0;
     const int64_t blocks = c->geom.rows * ((c->geom.N0 + kTile - 1) / kTile);
     recover_kernel<L, T, MIR><<<(unsigned)blocks, kTile, smem, c->stream>>>((const T *)src, c->geom, r, scale, th,
                                                                              gr, u, flag);
