@@ -32,16 +32,22 @@ typedef struct lb_adj lb_adj;
 /*
  * Adjoint workspace for `ctx` (any precision; d = 1, 2, 3; periodic grids).
  * The forward states are read in their storage type.  The reverse pass
- * computes in FP64 for LB_FP64 and LB_FX64 contexts and in FP32 for
- * LB_FP32_SHIFTED contexts (whose forward map is FP32-accurate); the seed,
- * the initialisation adjoint and the dL/dnu accumulation are FP64 always.
+ * computes in FP64 for LB_FP64 contexts, in FP32 for LB_FP32_SHIFTED contexts
+ * (whose forward map is FP32-accurate), and for LB_FX64 contexts in 64-bit
+ * fixed point: the adjoint field is held as round(phi 2^G), G chosen from
+ * the seed so that max|phi_T| 2^G < 2^56, K^T is formed from exact integer
+ * sums and rounded 62-bit products, and the dL/dnu term from exact 128-bit
+ * dot products (FP64 instead when the collision constants are too large for
+ * that range: see lb_adjoint.cu).
+ * The seed, the initialisation adjoint and the dL/dnu accumulation are FP64
+ * always.
  *   T        forward steps (>= 1).
  *   C        checkpoint interval, 1 <= C <= T, or 0 for ceil(sqrt(T)).
  *   want_nu  nonzero to also compute dL/dnu (needs the paper's relaxation
  *            set; keeps checkpoints and recomputes segments); zero computes
  *            dL/dtheta0 only and keeps no forward states.
  * Allocates ceil(T/C) + C state copies (want_nu) and two adjoint fields
- * (FP64, or FP32 for LB_FP32_SHIFTED).  The context must outlive the
+ * (8 bytes per value, 4 for LB_FP32_SHIFTED).  The context must outlive the
  * workspace.
  * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA.
  */
@@ -67,7 +73,9 @@ lb_status lb_adjoint_step(lb_adj *a, int64_t nsteps);
 /*
  * After T reverse steps: dL/dtheta0 (device, nodes) and, if requested at
  * creation, dL/dnu (host, 1 value; NULL to skip).  Synchronises the stream.
- * Errors: LB_ESTATE if the reverse pass is incomplete.
+ * Errors: LB_ESTATE if the reverse pass is incomplete; LB_EINVAL if a
+ * fixed-point adjoint field left |value| < 2^59 (not seen in practice: the
+ * field grows by less than 1.3x over a reverse pass, against 8x of headroom).
  */
 lb_status lb_adjoint_result(lb_adj *a, double *dL_dtheta0, double *dL_dnu);
 

@@ -36,6 +36,13 @@ struct AdjK {
     double shift[kAdjQ];
     double mshift_th, mshift_paa;  // the shift's moments: theta_ref and sigma theta_ref
     float mshift_th_f, mshift_paa_f;
+    // Fixed-point reverse pass (64-bit fixed-point states): the adjoint fields
+    // hold round(phi 2^G); aunit = 2^-G.  K^T uses the collision constants with
+    // kFxCoefBits fraction bits (c0k .. wdk); the eps-term uses the FP64
+    // eps-derivatives scaled by 2^-(F+G) (kdx), F the state's fraction bits.
+    long long c0k, cAk, wdk, k1k, k2k, k3k;
+    double aunit;
+    Coll<double> kdx;
     double ucoef, ducoef;                      // (2 - s1) c and d/deps
     double w[kAdjQ], dw[kAdjQ];                // weights and d/deps
     double iax, idg, diax, didg;               // initialisation operator and d/deps
@@ -191,6 +198,97 @@ __device__ __forceinline__ A adj_node(A *l, const T *fv, const AdjK &K)
     return eterm;
 }
 
+__device__ __forceinline__ double i128_to_double(__int128 v)
+{
+    const long long hi = (long long)(v >> 64);
+    const unsigned long long lo = (unsigned long long)v;
+    return fma((double)hi, 0x1p64, (double)lo);
+}
+
+// The node update of the fixed-point reverse pass (64-bit fixed-point states):
+// K^T from exact integer channel sums and rounded 64x62-bit products; with
+// NU, lambda . (dK/deps) f as exact 128-bit dot products of the integer
+// channels with the state's integer moments, converted once each.  Sets
+// `range` when an output leaves |v| < 2^59 (the fields start below 2^56).
+template <class L, bool NU>
+__device__ __forceinline__ double adj_node_fx(long long *l, const long long *fv, const AdjK &K, bool &range)
+{
+    constexpr int D = L::D, NP = D * (D - 1) / 2, B0 = 1 + 2 * D;
+    const long long l0 = l[0];
+    long long s2[D], dd[D], P[NP > 0 ? NP : 1];  // s2 = l_{+a} + l_{-a} - 2 l0
+    long long sax = 0, sdg = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const long long sa = l[1 + a] + l[1 + D + a];
+        sax += sa;
+        s2[a] = sa - 2 * l0;
+        dd[a] = l[1 + a] - l[1 + D + a];
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const Plane<long long> pl = plane(l[B0 + 4 * p], l[B0 + 4 * p + 1], l[B0 + 4 * p + 2], l[B0 + 4 * p + 3]);
+        P[p] = pl.P;
+        sdg += pl.F;
+    }
+    double eterm = 0.0;
+    if constexpr (NU) {
+        const NodeMoments<L, long long> m = node_moments<L, long long>(fv);
+        __int128 S2 = 0, S1 = 0, S3 = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            S2 += (__int128)m.Paa[a] * s2[a];
+            S1 += (__int128)m.J[a] * dd[a];
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) S3 += (__int128)m.Pab[p] * P[p];
+        const Coll<double> &kd = K.kdx;
+        const double lt = fma(kd.c0, (double)l0, fma(kd.cA, (double)sax, kd.wd * (double)sdg));
+        eterm = fma((double)m.th, lt, fma(kd.k2, i128_to_double(S2), fma(kd.k1, i128_to_double(S1),
+                                                                           kd.k3 * i128_to_double(S3))));
+    }
+    const long long Lt = mulfx(l0, K.c0k) + mulfx(sax, K.cAk) + mulfx(sdg, K.wdk);
+    long long LP[D], LJ[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        LP[a] = mulfx(s2[a], K.k2k);
+        LJ[a] = mulfx(dd[a], K.k1k);
+    }
+    l[0] = Lt;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const long long base = Lt + LP[a];
+        l[1 + a] = base + LJ[a];
+        l[1 + D + a] = base - LJ[a];
+    }
+    static_for<0, NP>([&](auto Pi) {
+        constexpr int p = decltype(Pi)::value;
+        constexpr int a = pair_a<D>(p), b = pair_b<D>(p);
+        const long long X = Lt + (LP[a] + LP[b]);
+        const long long U = LJ[a] + LJ[b], W = LJ[a] - LJ[b];
+        const long long lab = mulfx(P[p], K.k3k);
+        const long long Xp = X + lab, Xm = X - lab;
+        l[B0 + 4 * p] = Xp + U;      // (+1, +1)
+        l[B0 + 4 * p + 1] = Xm - W;  // (-1, +1)
+        l[B0 + 4 * p + 2] = Xp - U;  // (-1, -1)
+        l[B0 + 4 * p + 3] = Xm + W;  // (+1, -1)
+    });
+    constexpr long long kLim = 1ll << 59;  // next step's channel sums (<= 12 terms) stay below 2^63
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) range |= !(l[i] < kLim && l[i] > -kLim);
+    return eterm;
+}
+
+// Sum type of a lane's eps-terms: the adjoint's own type, FP64 for fixed point.
+template <typename A> using EpsAcc = typename std::conditional<std::is_same<A, long long>::value, double, A>::type;
+
+// FP64 seed values -> fixed point round(v * 2^G).
+__global__ void to_fixed_kernel(const double *__restrict__ src, long long *__restrict__ dst, int64_t n,
+                                double scale)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __double2ll_rn(src[i] * scale);
+}
+
 template <typename A> __device__ __forceinline__ A warp_sum(A v)
 {
 #pragma unroll
@@ -268,7 +366,8 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
 template <class L, typename T, bool NU, typename A>
 __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const A *__restrict__ phi_in,
                                                                  const T *__restrict__ Pn, A *__restrict__ phi_out,
-                                                                 Geom g, AdjK K, double *__restrict__ slot)
+                                                                 Geom g, AdjK K, double *__restrict__ slot,
+                                                                 int *__restrict__ flag)
 {
     constexpr int V = 2;
     const int lane = threadIdx.x & 31;
@@ -278,7 +377,8 @@ __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const A *__rest
     const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
     A lam[L::Q][V];
     gather_rev<L, A>(phi_in, g, row, x0, lane, lam);
-    A acc = 0;  // this lane's dL/deps terms, in the adjoint's arithmetic
+    EpsAcc<A> acc = 0;  // this lane's dL/deps terms
+    bool range = false;
     T f[L::Q][V];
     if constexpr (NU) gather<L, T, V>(Pn, g, row, x0, lane, f);
 #pragma unroll
@@ -290,7 +390,11 @@ __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const A *__rest
             l[i] = lam[i][v];
             if constexpr (NU) fv[i] = f[i][v];
         }
-        const A e = adj_node<L, T, NU, A>(l, fv, K);
+        EpsAcc<A> e;
+        if constexpr (std::is_same<A, long long>::value)
+            e = adj_node_fx<L, NU>(l, fv, K, range);
+        else
+            e = adj_node<L, T, NU, A>(l, fv, K);
         if (NU && x0 + V * lane + v < g.N0) acc += e;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) lam[i][v] = l[i];
@@ -299,6 +403,9 @@ __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const A *__rest
         A *dp = phi_out + row * g.pitch + x0 + V * lane;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, lam[i]);
+    }
+    if constexpr (std::is_same<A, long long>::value) {
+        if (range) atomicOr(flag, 1);
     }
     if constexpr (NU) {
         acc = warp_sum(acc);
@@ -330,7 +437,8 @@ __global__ void adj_init_kernel(const A *__restrict__ phi, Geom g, AdjK K, const
             constexpr int i = decltype(I)::value;
             constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2];
             constexpr int nz = (ex != 0) + (ey != 0) + (ez != 0);
-            const double ph = (double)p[(int64_t)i * g.slab];
+            const double ph = std::is_same<A, long long>::value ? (double)p[(int64_t)i * g.slab] * K.aunit
+                                                               : (double)p[(int64_t)i * g.slab];
             s = fma(K.w[i], ph, s);
             double dfi = K.dw[i] * t0;
             if constexpr (nz == 1) {
@@ -411,7 +519,9 @@ struct lb_adj {
     std::vector<void *> ck;   // checkpoints P_{kC}
     std::vector<void *> seg;  // recomputed segment P_{kC + m}
     int64_t seg_loaded = -1;
-    void *phi[2] = {nullptr, nullptr};  // adjoint fields: float for FP32-shifted states, else double
+    void *phi[2] = {nullptr, nullptr};  // adjoint fields: float (FP32s), int64 fixed point (fx), else double
+    bool fx = false;                     // fixed-point reverse pass (64-bit fixed-point states)
+    int *dflag = nullptr;                // fixed-point range flag
     int pcur = 0;
     double *th0 = nullptr, *grad = nullptr, *h = nullptr;
     double *slot_step = nullptr, *slot_init = nullptr, *dsum = nullptr;
@@ -449,6 +559,7 @@ void free_adj(lb_adj *a)
     cudaFree(a->slot_step);
     cudaFree(a->slot_init);
     cudaFree(a->dsum);
+    cudaFree(a->dflag);
     delete a;
 }
 
@@ -480,6 +591,15 @@ void make_adjk(lb_adj *a)
     K.kd.cA = (ds2x * sigma + c.s2x * dsigma) / 2.0 - 2.0 * (d - 1) * dwd;
     K.kd.wd = dwd;
     K.kf = lbk::make_coll<float>(c);
+    const auto fxk = [](double v) { return llrint(ldexp(v, lbk::kFxCoefBits)); };
+    K.c0k = fxk(K.k.c0);
+    K.cAk = fxk(K.k.cA);
+    K.wdk = fxk(K.k.wd);
+    K.k1k = fxk(K.k.k1);
+    K.k2k = fxk(K.k.k2);
+    K.k3k = fxk(K.k.k3);
+    K.aunit = 1.0;
+    K.kdx = K.kd;
     K.kdf = {(float)K.kd.k1, (float)K.kd.k2, (float)K.kd.k3, (float)K.kd.c0, (float)K.kd.cA, (float)K.kd.wd};
     const int q = c.q;
     double w[lbk::kAdjQ], dw[lbk::kAdjQ];
@@ -515,30 +635,82 @@ void make_adjk(lb_adj *a)
 int64_t sweep_blocks(const lbk::Geom &g) { return (g.nseg + lbk::kSweepThreads / 32 - 1) / (lbk::kSweepThreads / 32); }
 
 // The adjoint's arithmetic for a storage type: float for FP32-shifted states
-// (whose forward map is only FP32-accurate), double otherwise.
+// (whose forward map is only FP32-accurate), double otherwise; fixed-point
+// states use the integer reverse pass (a->fx) when its constants fit.
 template <typename T> using AdjT = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+
+// Constants of the fixed-point reverse pass once the adjoint scale 2^G is known.
+void set_fx_scale(lb_adj *a, int G)
+{
+    lbk::AdjK &K = a->K;
+    K.aunit = ldexp(1.0, -G);
+    const int sh = -(a->ctx->fx_bits + G);
+    K.kdx = {ldexp(K.kd.k1, sh), ldexp(K.kd.k2, sh), ldexp(K.kd.k3, sh),
+             ldexp(K.kd.c0, sh), ldexp(K.kd.cA, sh), ldexp(K.kd.wd, sh)};
+}
 
 template <class L, typename T> cudaError_t seed_t(lb_adj *a, const double *dLdu)
 {
     lb_ctx *c = a->ctx;
-    lbk::adj_seed_kernel<L, T, AdjT<T>><<<(unsigned)sweep_blocks(a->ag), lbk::kSweepThreads, 0, c->stream>>>(
-        (const T *)c->f[c->cur], a->ag, a->K, dLdu, (AdjT<T> *)a->phi[a->pcur], a->slot_step);
+    const unsigned nb = (unsigned)sweep_blocks(a->ag);
+    if constexpr (std::is_same<T, long long>::value) {
+        if (a->fx) {
+            // FP64 seed into the other field, then round(phi 2^G) with max|phi| 2^G < 2^56:
+            // seven bits of headroom for the channel sums and the (measured, < 1.3x) growth
+            double *tmp = (double *)a->phi[a->pcur ^ 1];
+            lbk::adj_seed_kernel<L, T, double><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
+                (const T *)c->f[c->cur], a->ag, a->K, dLdu, tmp, a->slot_step);
+            cudaError_t e = cudaGetLastError();
+            const int64_t n = (int64_t)c->q * a->ag.slab;
+            double mx = 0.0;
+            if (e == cudaSuccess) e = lbk::launch_maxabs(c, tmp, n, c->dout);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&mx, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return e;
+            int ex = 0;
+            if (mx > 0.0) frexp(mx, &ex);
+            const int G = 56 - ex;
+            set_fx_scale(a, G);
+            lbk::to_fixed_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, c->stream>>>(
+                tmp, (long long *)a->phi[a->pcur], n, ldexp(1.0, G));
+            return cudaGetLastError();
+        }
+    }
+    using A = AdjT<T>;
+    lbk::adj_seed_kernel<L, T, A><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
+        (const T *)c->f[c->cur], a->ag, a->K, dLdu, (A *)a->phi[a->pcur], a->slot_step);
     return cudaGetLastError();
 }
 
-template <class L, typename T> cudaError_t step_t(lb_adj *a, const void *Pn)
+template <class L, typename T, typename A> cudaError_t step_a(lb_adj *a, const void *Pn)
 {
-    using A = AdjT<T>;
     lb_ctx *c = a->ctx;
     const unsigned nb = (unsigned)sweep_blocks(a->ag);
     const A *in = (const A *)a->phi[a->pcur];
     A *out = (A *)a->phi[a->pcur ^ 1];
     if (a->want_nu)
         lbk::adj_step_kernel<L, T, true, A><<<nb, lbk::kSweepThreads, 0, c->stream>>>(in, (const T *)Pn, out, a->ag,
-                                                                                      a->K, a->slot_step);
+                                                                                      a->K, a->slot_step, a->dflag);
     else
         lbk::adj_step_kernel<L, T, false, A><<<nb, lbk::kSweepThreads, 0, c->stream>>>(in, (const T *)Pn, out, a->ag,
-                                                                                       a->K, a->slot_step);
+                                                                                       a->K, a->slot_step, a->dflag);
+    return cudaGetLastError();
+}
+
+template <class L, typename T> cudaError_t step_t(lb_adj *a, const void *Pn)
+{
+    if constexpr (std::is_same<T, long long>::value) {
+        if (a->fx) return step_a<L, T, long long>(a, Pn);
+    }
+    return step_a<L, T, AdjT<T>>(a, Pn);
+}
+
+template <class L, typename A> cudaError_t init_a(lb_adj *a, double *dth0)
+{
+    lb_ctx *c = a->ctx;
+    const unsigned nb = (unsigned)((c->nodes + 255) / 256);
+    lbk::adj_init_kernel<L, A><<<nb, 256, 0, c->stream>>>((const A *)a->phi[a->pcur], c->geom, a->K, a->th0, a->grad,
+                                                          dth0, a->h, a->slot_init);
     return cudaGetLastError();
 }
 
@@ -546,13 +718,13 @@ template <class L> cudaError_t init_t(lb_adj *a, double *dth0)
 {
     lb_ctx *c = a->ctx;
     const unsigned nb = (unsigned)((c->nodes + 255) / 256);
+    cudaError_t e;
     if (c->precision == LB_FP32_SHIFTED)
-        lbk::adj_init_kernel<L, float><<<nb, 256, 0, c->stream>>>((const float *)a->phi[a->pcur], c->geom, a->K,
-                                                                  a->th0, a->grad, dth0, a->h, a->slot_init);
+        e = init_a<L, float>(a, dth0);
+    else if (a->fx)
+        e = init_a<L, long long>(a, dth0);
     else
-        lbk::adj_init_kernel<L, double><<<nb, 256, 0, c->stream>>>((const double *)a->phi[a->pcur], c->geom, a->K,
-                                                                   a->th0, a->grad, dth0, a->h, a->slot_init);
-    cudaError_t e = cudaGetLastError();
+        e = init_a<L, double>(a, dth0);
     if (e != cudaSuccess) return e;
     lbk::adj_fd4t_kernel<<<nb, 256, 0, c->stream>>>(a->h, dth0, c->d, (int)c->N[0], (int)c->N[1], (int)c->N[2],
                                                     a->K.inv12dx);
@@ -659,6 +831,20 @@ lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_a
     a->T = T;
     a->C = C;
     a->want_nu = want_nu != 0;
+    {
+        // The integer reverse pass holds the constants with 62 fraction bits
+        // (each inside (-2, 2)) and keeps every field below 2^59 (checked per
+        // store).  An output of K^T is then bounded by
+        // (|c0| + 2d|cA| + 4P|wd| + 8|k2| + 4|k1| + 4|k3|) 2^59, P = d(d-1)/2
+        // planes, which must stay below 2^63; otherwise the pass runs in FP64.
+        const lbk::Coll<double> kc = lbk::make_coll<double>(*ctx);
+        const double d = ctx->d, planes = d * (d - 1) / 2;
+        const double bound = fabs(kc.c0) + 2 * d * fabs(kc.cA) + 4 * planes * fabs(kc.wd) + 8 * fabs(kc.k2) +
+                             4 * fabs(kc.k1) + 4 * fabs(kc.k3);
+        const double lim = 1.999;
+        a->fx = ctx->precision == LB_FX64 && bound < 15.0 && fabs(kc.c0) < lim && fabs(kc.cA) < lim &&
+                fabs(kc.wd) < lim && fabs(kc.k1) < lim && fabs(kc.k2) < lim && fabs(kc.k3) < lim;
+    }
     a->state_bytes = (size_t)ctx->q * ctx->geom.slab * ctx->elem;
     cudaError_t e = cudaSuccess;
     const size_t aelem = (ctx->precision == LB_FP32_SHIFTED) ? sizeof(float) : sizeof(double);
@@ -683,6 +869,7 @@ lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_a
     if (e == cudaSuccess) e = cudaMalloc(&a->slot_step, sizeof(double) * a->ag.nseg);
     if (e == cudaSuccess) e = cudaMalloc(&a->slot_init, sizeof(double) * a->nslot_init);
     if (e == cudaSuccess) e = cudaMalloc(&a->dsum, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&a->dflag, sizeof(int));
     a->bytes += 2 * pbytes + sizeof(double) * ctx->nodes * (1 + 2 * ctx->d);
     if (e != cudaSuccess) {
         free_adj(a);
@@ -742,7 +929,8 @@ lb_status lb_adjoint_seed(lb_adj *a, const double *dLdu)
     lb_ctx *c = a->ctx;
     cudaError_t e;
     if ((e = cudaMemsetAsync(a->slot_step, 0, sizeof(double) * a->ag.nseg, c->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(a->slot_init, 0, sizeof(double) * a->nslot_init, c->stream)) != cudaSuccess)
+        (e = cudaMemsetAsync(a->slot_init, 0, sizeof(double) * a->nslot_init, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(a->dflag, 0, sizeof(int), c->stream)) != cudaSuccess)
         return acuda(a, e, "lb_adjoint_seed");
     a->pcur = 0;
     if ((e = do_seed(a, dLdu)) != cudaSuccess) return acuda(a, e, "lb_adjoint_seed: launch");
@@ -777,6 +965,14 @@ lb_status lb_adjoint_result(lb_adj *a, double *dL_dtheta0, double *dL_dnu)
     lb_ctx *c = a->ctx;
     cudaError_t e = do_init(a, dL_dtheta0);
     if (e != cudaSuccess) return acuda(a, e, "lb_adjoint_result: init adjoint");
+    if (a->fx) {
+        int flag = 0;
+        if ((e = cudaMemcpyAsync(&flag, a->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+            return acuda(a, e, "lb_adjoint_result");
+        if (flag)
+            return afail(a, LB_EINVAL, "lb_adjoint_result: the fixed-point adjoint field left its range");
+    }
     if (dL_dnu) {
         if (!a->want_nu) return afail(a, LB_EINVAL, "lb_adjoint_result: dL/dnu was not requested");
         lbk::sum_slots_kernel<<<1, 256, 0, c->stream>>>(a->slot_step, a->ag.nseg, a->slot_init, a->nslot_init,

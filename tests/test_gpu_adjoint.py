@@ -103,10 +103,9 @@ def test_autograd_function():
 
 @pytest.mark.parametrize("d,N,T", [(1, (100,), 37), (2, (70, 45), 23), (3, (20, 13, 9), 7)])
 def test_fp32_shifted_adjoint_tracks_fp64(d, N, T):
-    """FP32 shifted storage: the forward states carry float rounding, so the
-    gradient of the FP32 forward map differs from the FP64 one by the
-    relative size of that rounding in the velocity misfit (~1e-5 here); the
-    adjoint arithmetic itself is FP64."""
+    """FP32 shifted storage: the forward states carry float rounding and the
+    reverse pass computes in FP32, so the gradient differs from the FP64 one
+    by float rounding relative to the velocity misfit (~1e-5 here)."""
     th0, ut, nu, dx, dt = _case(d, N, T, 60 + d)
     L64, g64, dnu64 = _gpu_grad(d, N, nu, dx, dt, T, th0, ut, "fp64")
     L32, g32, dnu32 = _gpu_grad(d, N, nu, dx, dt, T, th0, ut, "fp32s")
@@ -114,3 +113,23 @@ def test_fp32_shifted_adjoint_tracks_fp64(d, N, T):
     print("fp32s adjoint d=%d: dtheta0 rel %.2e, dnu rel %.2e, L rel %.2e" % (d, rel, abs(dnu32 / dnu64 - 1), abs(L32 / L64 - 1)))
     assert rel <= 1e-3
     assert dnu32 == pytest.approx(dnu64, rel=1e-3)
+
+
+@pytest.mark.parametrize("d,N,T", [(1, (100,), 37), (2, (70, 45), 23), (3, (20, 13, 9), 7)])
+def test_fx64_theta0_gradient_without_nu(d, N, T):
+    """Fixed-point states, dL/dtheta0 only: the reverse pass is then entirely
+    integer (K^T on round(phi 2^G)); it must meet the same bar against the
+    oracle as the FP64 adjoint."""
+    th0, ut, nu, dx, dt = _case(d, N, T, 70 + d)
+    m = O.Model(d, N, nu, dx, dt)
+    _, go, _ = m.adjoint(th0, ut, T)
+    s = lb.Solver(d, N, nu, dx, dt, precision="fx64")
+    a = lb.Adjoint(s, T, want_nu=False)
+    u = a.forward(torch.from_numpy(th0).cuda())
+    a.seed((u - torch.from_numpy(ut).cuda()).contiguous())
+    a.step(T)
+    g, _ = a.result()
+    g = g.cpu().numpy()
+    rel = np.max(np.abs(g - go)) / np.max(np.abs(go))
+    print("fx64 theta0-only adjoint d=%d: rel %.2e" % (d, rel))
+    assert rel <= 1e-9
