@@ -169,6 +169,7 @@ struct InitK {
     // constants w1, wd, iax/dx with kFxCoefBits fraction bits.
     double gscale;
     long long w1k, wdk, iak;
+    int fx_bits;  // F
 };
 
 }  // namespace lbk

@@ -36,6 +36,32 @@ namespace lbk {
 // a rounded 64x62-bit product, and the rest population is theta minus the
 // others, so sum_i f_i(x) = round(theta0(x) 2^F) exactly.
 // ---------------------------------------------------------------------------
+// round(v 2^F) to nearest, ties to even, from the fields of the IEEE double
+// v in integer arithmetic (v 2^F is exact; only its rounding to an integer is
+// done here).  Sets `range` when |v 2^F| >= 2^61, NaN and infinities included.
+__device__ __forceinline__ long long fx_round(double v, int F, bool &range)
+{
+    const long long bits = __double_as_longlong(v);
+    const int e = (int)((bits >> 52) & 0x7ff);
+    const long long mant = (bits & ((1ll << 52) - 1)) | (e ? (1ll << 52) : 0ll);
+    const int sh = (e ? e : 1) - 1075 + F;  // |v| 2^F = mant 2^sh
+    if (e == 0x7ff || sh > 8) {             // mant >= 2^52: sh >= 9 means >= 2^61
+        range = true;
+        return 0;
+    }
+    long long r;
+    if (sh >= 0) {
+        r = mant << sh;
+    } else if (sh < -53) {
+        r = 0;  // below one half
+    } else {
+        const int k = -sh;
+        const long long q = mant >> k, rem = mant & ((1ll << k) - 1), half = 1ll << (k - 1);
+        r = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+    }
+    return bits < 0 ? -r : r;
+}
+
 template <class L, typename T, bool FXI>
 __global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *__restrict__ theta0,
                             const double *__restrict__ grad, int *__restrict__ flag)
@@ -44,21 +70,28 @@ __global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *
     const int64_t nodes = (int64_t)g.N0 * g.rows;
     const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= nodes) return;
+    // coordinates in 32-bit arithmetic (nodes <= 2^31)
+    const unsigned nd = (unsigned)node;
     int c[4];
-    c[0] = (int)(node % g.N0);
-    const int64_t rw = node / g.N0;
-    c[1] = (int)(rw % g.N1);
-    c[2] = (int)((rw / g.N1) % g.N2);
-    c[3] = (int)(rw / ((int64_t)g.N1 * g.N2));
+    const unsigned rw = nd / (unsigned)g.N0;
+    c[0] = (int)(nd - rw * (unsigned)g.N0);
+    const unsigned r2 = rw / (unsigned)g.N1;
+    c[1] = (int)(rw - r2 * (unsigned)g.N1);
+    const unsigned r3 = r2 / (unsigned)g.N2;
+    c[2] = (int)(r2 - r3 * (unsigned)g.N2);
+    c[3] = (int)r3;
     const int n[4] = {g.N0, g.N1, g.N2, g.N3};
 
+    // checks on the bit patterns (integer pipes): theta > 0 and finite, a
+    // finite gradient (exponent field not all ones)
     const double th = theta0[node];
+    const long long tb = __double_as_longlong(th);
     double gr[D];
-    bool bad = !(th > 0.0) || !isfinite(th);
+    bool bad = !(tb > 0) || ((tb >> 52) & 0x7ff) == 0x7ff;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         gr[a] = grad[a * nodes + node];
-        bad |= !isfinite(gr[a]);
+        bad |= ((__double_as_longlong(gr[a]) >> 52) & 0x7ff) == 0x7ff;
         if (((g.mirror >> a) & 1u) && (c[a] == 0 || c[a] == n[a] - 1)) gr[a] = 0.0;
     }
     if (bad) atomicOr(flag, 1);
@@ -66,14 +99,10 @@ __global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *
     T val[Q];
     bool range = false;
     if constexpr (FXI) {
-        const long long t = __double2ll_rn(th * K.fxscale);
+        const long long t = fx_round(th, K.fx_bits, range);
         long long G[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const double gs = gr[a] * K.gscale;
-            if (!(fabs(gs) < 0x1p61)) range = true;
-            G[a] = range ? 0 : __double2ll_rn(gs);
-        }
+        for (int a = 0; a < D; ++a) G[a] = fx_round(gr[a] * K.gscale, 0, range);
         const long long W1 = mulfx(t, K.w1k), WD = mulfx(t, K.wdk);
         long long rest = 0;
         static_for<1, Q>([&](auto I) {
@@ -126,6 +155,28 @@ __global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *
     }
     if (range) atomicOr(flag, 2);
 
+    if (!g.mirror) {
+        // periodic: destination offset = sum over axes of one of three wrapped
+        // offsets (shift -1, 0, +1), formed once per node
+        int64_t off[4][3];
+        int64_t stride = 1;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int dn = c[a] == 0 ? n[a] - 1 : c[a] - 1;  // x_a - 1
+            const int up = c[a] == n[a] - 1 ? 0 : c[a] + 1;  // x_a + 1
+            off[a][0] = (int64_t)up * stride;                // e = -1 stores at x_a + 1
+            off[a][1] = (int64_t)c[a] * stride;
+            off[a][2] = (int64_t)dn * stride;                // e = +1 stores at x_a - 1
+            stride *= (a == 0) ? (int64_t)g.pitch : (int64_t)n[a];
+        }
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const int64_t at = off[0][L::E[i][0] + 1] + off[1][L::E[i][1] + 1] + off[2][L::E[i][2] + 1] +
+                               off[3][L::E[i][3] + 1];
+            dst[(int64_t)i * g.slab + at] = val[i];
+        });
+        return;
+    }
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int E0 = L::E[i][0], E1 = L::E[i][1], E2 = L::E[i][2], E3 = L::E[i][3];
@@ -456,6 +507,7 @@ static cudaError_t init_t(lb_ctx *c, const double *theta0, const double *grad, i
     K.theta_ref = (c->precision == LB_FP32_SHIFTED) ? c->theta_ref : 0.0;
     K.fxscale = ldexp(1.0, c->fx_bits);
     K.gscale = c->dx * K.fxscale;
+    K.fx_bits = c->fx_bits;
     const unsigned nb = (unsigned)((c->nodes + 255) / 256);
     if constexpr (std::is_same<T, long long>::value) {
         // integer formation needs every constant inside the 62-bit range and
