@@ -750,7 +750,7 @@ def run_profile_adjoint(local, spec):
 
 def run_profile_sweep(local, spec):
     """Minimal, repeatable command for ncu: init + STEPS sweeps of one grid,
-    then one recovery and one state sum."""
+    then one recovery, one state sum and the error norms."""
     import torch
     from paper_2309_02825_gb300 import lb
     torch.cuda.set_device(local)
@@ -768,8 +768,11 @@ def run_profile_sweep(local, spec):
                  torch.from_numpy(np.ascontiguousarray(prob.grad(N, dx))).cuda())
     for _ in range(steps):
         s.step(1)
-    s.macros(want=("theta", "u"))
+    th, _, u = s.macros(want=("theta", "u"))
     s.sum_theta()
+    T = steps * dt
+    s.reduce(th, u, torch.from_numpy(prob.theta(N, dx, T)).cuda(),
+             torch.from_numpy(np.ascontiguousarray(prob.u(N, dx, T))).cuda())
     torch.cuda.synchronize()
     s.close()
     print(json.dumps({"profile_sweep": spec, "ok": True}))

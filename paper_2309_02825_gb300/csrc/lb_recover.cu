@@ -145,7 +145,10 @@ __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ sr
     const int64_t node = row * g.N0 + x;
     const double thd = (double)th * scale + r.theta_ref;
     if (theta) theta[node] = thd;
-    if (!(thd > 0.0) || !isfinite(thd)) atomicOr(flag, 1);
+    {  // theta > 0 and finite, as bit tests on the integer pipes
+        const long long tb = __double_as_longlong(thd);
+        if (!(tb > 0) || ((tb >> 52) & 0x7ff) == 0x7ff) atomicOr(flag, 1);
+    }
     const double cu = r.ucoef / thd;  // the storage scale is folded into ucoef and gcoef
 #pragma unroll
     for (int a = 0; a < L::D; ++a) {
