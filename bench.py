@@ -628,6 +628,24 @@ def run_walls(local, peaks):
         gbs = 2 * 9 * 8 * n * n / (ms / 1e3) / 1e9
         out["sweep_2d_4096_fx64_" + kind] = {"sweep_ms": ms, "mlups": n * n / (ms / 1e3) / 1e6,
                                               "hbm_frac": gbs / peaks["hbm_gbs"]}
+    c3 = W.fourier_3d(256)
+    th3 = torch.from_numpy(c3.problem.theta(c3.N, c3.dx)).cuda()
+    g3 = torch.from_numpy(np.ascontiguousarray(c3.problem.grad(c3.N, c3.dx))).cuda()
+    for kind in ("periodic", "mirror"):
+        s = lb.Solver(3, c3.N, c3.nu, c3.dx, c3.dt, precision="fx64", stream=stream, boundary=[kind] * 3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            s.set_theta0(th3, g3)
+            s.step(10)
+            e0.record(stream)
+            s.step(50)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 50
+        s.close()
+        gbs = 2 * 19 * 8 * c3.nodes / (ms / 1e3) / 1e9
+        out["sweep_3d_256_fx64_" + kind] = {"sweep_ms": ms, "mlups": c3.nodes / (ms / 1e3) / 1e6,
+                                             "hbm_frac": gbs / peaks["hbm_gbs"]}
     ex1 = {}
     for eps in (0.5, 1.0, 1.5, 2.0):
         rows = {"theta": [], "u": []}
