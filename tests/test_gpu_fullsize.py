@@ -38,7 +38,7 @@ def _samples(N, rng, k=24):
            tuple([64] + [n - 1 for n in N[1:]]), tuple([N[0] - 1] + [n // 2 for n in N[1:]])]
     while len(pts) < k:
         pts.append(tuple(int(rng.integers(0, n)) for n in N))
-    return pts
+    return [tuple(v % n for v, n in zip(p, N)) for p in pts]  # warp-edge points wrap on short rows
 
 
 def _check(case, precision, nsteps, theta_ref=0.0):
@@ -206,3 +206,46 @@ def test_fx64_16384_squared_offsets_beyond_2_31():
         assert abs(got_t - tho[half, half]) <= 1e-12 * 3.0, (c, got_t, tho[half, half])
         assert np.max(np.abs(got_u - uo[:, half, half])) <= 1e-12 * 0.3, (c, got_u, uo[:, half, half])
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fx64"])
+def test_fullsize_4d_example4_50(precision):
+    """The 4D benchmark case (the paper's Example 4 at dx = 1/25: 50^4 nodes,
+    D4Q33, dt = 1/250) on sampled nodes against the patch oracle."""
+    dx, dt, eps = 1.0 / 25, 1.0 / 250, 0.08
+    nu = eps * dx * dx / dt
+    prob = W.ProductSineProblem(4, nu, (1, 2, 3, 4), 2.0, 2.0, origin=-1.0)
+    case = W.Case("example4_50", 4, (50,) * 4, nu, dx, dt, 250, prob)
+    worst, total, t0 = _check(case, precision, 2)
+    assert worst["theta"] <= 1e-12 and worst["u"] <= 1e-12, worst
+    assert abs(total - t0) <= 1e-13 * t0
+
+
+def test_fullsize_batched_512_instances():
+    """The batched benchmark workload (512 instances, autotuned schedule, FP32
+    shifted): sampled instances equal single-grid solves bit for bit after a
+    recorded graph plus direct launches (the single-grid solver is itself
+    checked against the oracle)."""
+    cases = W.batched_2d(512, nsteps=2000)
+    th0 = np.concatenate([c.problem.theta(c.N, c.dx).ravel() for c in cases])
+    g0 = np.concatenate([np.ascontiguousarray(c.problem.grad(c.N, c.dx)).ravel() for c in cases])
+    b = lb.Batch([c.N for c in cases], [c.nu for c in cases], [c.dx for c in cases], [c.dt for c in cases],
+                 precision="fp32s", theta_ref=[1.5] * len(cases))
+    b.autotune(4)
+    b.set_theta0(torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda())
+    n = 37
+    b.step(n)
+    th, u = b.macros()
+    ths, us = b.split(th), b.split(u, 2)
+    rng = np.random.default_rng(512)
+    for j in sorted(set(int(v) for v in rng.integers(0, len(cases), 6)) | {0, len(cases) - 1}):
+        c = cases[j]
+        s = lb.Solver(2, c.N, c.nu, c.dx, c.dt, precision="fp32s", theta_ref=1.5)
+        s.set_theta0(torch.from_numpy(c.problem.theta(c.N, c.dx)).cuda(),
+                     torch.from_numpy(np.ascontiguousarray(c.problem.grad(c.N, c.dx))).cuda())
+        s.step(n)
+        t1, _, u1 = s.macros()
+        assert torch.equal(ths[j], t1), j
+        assert torch.equal(us[j], u1), j
+        s.close()
+    b.close()
