@@ -134,7 +134,7 @@ typedef enum {
  * theta0 even across each wall, grad theta0's wall-normal component odd
  * (so it is taken as zero on the wall nodes whatever the caller passes).
  * lb_sum_theta returns the wall-weighted sum on such grids; the discrete
- * adjoint (lb_adjoint.h) supports periodic grids only.
+ * adjoint (lb_adjoint.h) differentiates the walled scheme too.
  * Errors: LB_EINVAL (NULL kind, unknown kind, N_a < 3 on a mirror axis),
  * LB_ECUDA.
  */

@@ -10,7 +10,8 @@
  *   dL/dtheta0 (one value per node) and dL/dnu (through eps = nu dt/dx^2 and
  *   the relaxation set of Theorem 2, Eq. (Bur-Sol); dx and dt fixed).
  * Reverse step: phi_n(x) = K^T [phi_{n+1}(x + e_i)_i]_i (reversed streaming,
- * transposed collision), plus the eps-derivative term
+ * transposed collision; across a mirror wall the transpose of the reflected
+ * pull, which gathers the reflected populations), plus the eps-derivative term
  * lambda_{n+1} . (dK/deps) f_n(x), which needs the forward states f_n: they
  * are kept as checkpoints every C steps and recomputed one segment at a
  * time (C = ceil(sqrt(T)) stores about 2 sqrt(T) states).
@@ -30,7 +31,8 @@ extern "C" {
 typedef struct lb_adj lb_adj;
 
 /*
- * Adjoint workspace for `ctx` (any precision; d = 1, 2, 3; periodic grids).
+ * Adjoint workspace for `ctx` (any precision; d = 1, 2, 3; periodic axes or
+ * mirror walls, lb_set_boundary).
  * The forward states are read in their storage type.  The reverse pass
  * computes in FP64 for LB_FP64 contexts, in FP32 for LB_FP32_SHIFTED contexts
  * (whose forward map is FP32-accurate), and for LB_FX64 contexts in 64-bit

@@ -68,6 +68,67 @@ __device__ __forceinline__ void gather_rev(const A *__restrict__ src, const Geom
     });
 }
 
+// Reverse pull on a grid with mirror walls.  The forward pull reads the
+// stored slot P_j(y) from the node x = y + e_j: f_j(x) reads it, and so does
+// f_{R_B(j)}(x) for every set B of walls that e_j points into at x (x on the
+// wall node of axis a in B, e_ja pointing out of the domain), because a pull
+// across a wall reads the reflected population.  The transpose therefore
+// gathers lambda_j(y) = sum over those B of phi_{R_B(j)}(x), and zero when x
+// lies beyond a wall (such slots are never read).  Plain loads, one node at a
+// time: only grids with walls take this path.
+__device__ __forceinline__ int adj_src(int c, int e, int n, bool mir, bool &ghost, int &wall, int bit)
+{
+    if (e == 0) return c;
+    const int s = c + e;
+    if (s >= 0 && s < n) {
+        if (mir && ((e < 0 && s == 0) || (e > 0 && s == n - 1))) wall |= bit;
+        return s;
+    }
+    if (!mir) return s < 0 ? s + n : s - n;
+    ghost = true;
+    return 0;
+}
+
+template <class L, typename A>
+__device__ __forceinline__ void gather_rev_walls(const A *__restrict__ src, const Geom &g, int64_t row, int x0,
+                                                 int lane, A (&f)[L::Q][2])
+{
+    const int y = (int)(row % g.N1);
+    const int z = (int)(row / g.N1);
+    const int xb = x0 + 2 * lane;
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int j = decltype(I)::value;
+        constexpr int ex = L::E[j][0], ey = L::E[j][1], ez = L::E[j][2];
+        constexpr int nz = (ey != 0 ? 2 : 0) | (ez != 0 ? 4 : 0);  // row axes e_j moves along
+        bool ghost = false;
+        int wall = 0;  // bit a: the wall of axis a at the source node
+        const int ys = adj_src(y, ey, g.N1, (g.mirror >> 1) & 1u, ghost, wall, 2);
+        const int zs = adj_src(z, ez, g.N2, (g.mirror >> 2) & 1u, ghost, wall, 4);
+        const int64_t rbase = ((int64_t)zs * g.N1 + ys) * g.pitch;
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            A acc = 0;
+            if (!ghost && xb + v < g.N0) {
+                bool gx = false;
+                int wx = 0;
+                const int xs = adj_src(xb + v, ex, g.N0, g.mirror & 1u, gx, wx, 1);
+                if (!gx) {
+                    static_for<0, 8>([&](auto Mi) {
+                        constexpr int M = 2 * decltype(Mi)::value;  // subsets of the row axes
+                        if constexpr ((M & ~nz) == 0) {
+                            if ((M & ~wall) == 0) {
+                                acc += src[(int64_t)reflect_pop<L>(j, M) * g.slab + rbase + xs];
+                                if (wx) acc += src[(int64_t)reflect_pop<L>(j, M | 1) * g.slab + rbase + xs];
+                            }
+                        }
+                    });
+                }
+            }
+            f[j][v] = acc;
+        }
+    });
+}
+
 // Moments of one node's distributions in the accumulation type of the
 // storage (exact int64 sums for fixed point): theta, J_a, P_aa, P_ab.
 template <class L, typename A> struct NodeMoments {
@@ -297,7 +358,7 @@ template <typename A> __device__ __forceinline__ A warp_sum(A v)
 }
 
 // phi_T = dL/df_T through u_a = ucoef J_a / theta; eps-term of the recovery.
-template <class L, typename T, typename A>
+template <class L, typename T, typename A, bool MIR = false>
 __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__restrict__ P, Geom g, AdjK K,
                                                                  const double *__restrict__ dLdu,
                                                                  A *__restrict__ phi, double *__restrict__ slot)
@@ -309,7 +370,7 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
     const int64_t row = seg / g.seg_per_row;
     const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
     T f[L::Q][V];
-    gather<L, T, V>(P, g, row, x0, lane, f);
+    gather<L, T, V, MIR>(P, g, row, x0, lane, f);
     const int64_t nodes = (int64_t)g.N0 * g.rows;
     double out[L::Q][V];
     double acc = 0.0;
@@ -363,7 +424,7 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
 }
 
 // One reverse step: phi_out = K^T lambda(phi_in); eps-term if NU.
-template <class L, typename T, bool NU, typename A>
+template <class L, typename T, bool NU, typename A, bool MIR = false>
 __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const A *__restrict__ phi_in,
                                                                  const T *__restrict__ Pn, A *__restrict__ phi_out,
                                                                  Geom g, AdjK K, double *__restrict__ slot,
@@ -376,11 +437,14 @@ __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const A *__rest
     const int64_t row = seg / g.seg_per_row;
     const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
     A lam[L::Q][V];
-    gather_rev<L, A>(phi_in, g, row, x0, lane, lam);
+    if constexpr (MIR)
+        gather_rev_walls<L, A>(phi_in, g, row, x0, lane, lam);
+    else
+        gather_rev<L, A>(phi_in, g, row, x0, lane, lam);
     EpsAcc<A> acc = 0;  // this lane's dL/deps terms
     bool range = false;
     T f[L::Q][V];
-    if constexpr (NU) gather<L, T, V>(Pn, g, row, x0, lane, f);
+    if constexpr (NU) gather<L, T, V, MIR>(Pn, g, row, x0, lane, f);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         A l[L::Q];
@@ -429,9 +493,17 @@ __global__ void adj_init_kernel(const A *__restrict__ phi, Geom g, AdjK K, const
         const int64_t rw = n / g.N0;
         const A *p = phi + rw * g.pitch + x;
         const double t0 = th0[n];
+        // on a wall node the initialisation takes the wall-normal gradient as
+        // zero: no dependence on it, no term through it
+        const int cc[3] = {x, (int)(rw % g.N1), (int)(rw / g.N1)};
+        const int nn[3] = {g.N0, g.N1, g.N2};
+        bool onwall[3] = {false, false, false};
         double gr[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-        for (int a = 0; a < L::D; ++a) gr[a] = grad[a * nodes + n];
+        for (int a = 0; a < L::D; ++a) {
+            onwall[a] = ((g.mirror >> a) & 1u) && (cc[a] == 0 || cc[a] == nn[a] - 1);
+            gr[a] = onwall[a] ? 0.0 : grad[a * nodes + n];
+        }
         double s = 0.0, hh[3] = {0.0, 0.0, 0.0};
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
@@ -456,15 +528,19 @@ __global__ void adj_init_kernel(const A *__restrict__ phi, Geom g, AdjK K, const
         });
         dth0[n] = s;
 #pragma unroll
-        for (int a = 0; a < L::D; ++a) h[a * nodes + n] = hh[a];
+        for (int a = 0; a < L::D; ++a) h[a * nodes + n] = onwall[a] ? 0.0 : hh[a];
     }
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) slot[n >> 5] += acc;
 }
 
-// dth0 += G^T h, with (G^T h)(x) = sum_a sum_k cof_k h_a(x - off_k e_a) / (12 dx).
+// dth0 += G^T h, with (G^T h)(x) = sum_a sum_k cof_k h_a(x - off_k e_a) / (12 dx)
+// on periodic axes.  On an axis with walls the forward difference reads
+// theta at the even reflection of x + off_k, so node y also collects the
+// terms whose reflected read lands on it: from x = -y - off_k (read beyond
+// the first wall) and x = 2(n - 1) - y - off_k (beyond the last).
 __global__ void adj_fd4t_kernel(const double *__restrict__ h, double *__restrict__ dth0, int d, int N0, int N1,
-                                int N2, double inv12dx)
+                                int N2, unsigned mirror, double inv12dx)
 {
     const int64_t nodes = (int64_t)N0 * N1 * N2;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -478,10 +554,24 @@ __global__ void adj_fd4t_kernel(const double *__restrict__ h, double *__restrict
     for (int a = 0; a < d; ++a) {
         const int off[4] = {2, 1, -1, -2};
         const double cof[4] = {-1.0, 8.0, -8.0, 1.0};
+        const int ya = (a == 0) ? x : ((a == 1) ? y : z), na = nn[a];
         for (int k = 0; k < 4; ++k) {
-            int c[3] = {x, y, z};
-            c[a] = ((c[a] - off[k]) % nn[a] + nn[a]) % nn[a];
-            s += cof[k] * h[a * nodes + ((int64_t)c[2] * N1 + c[1]) * N0 + c[0]];
+            int xs[3], cnt = 0;
+            if ((mirror >> a) & 1u) {
+                const int direct = ya - off[k];
+                if (direct >= 0 && direct < na) xs[cnt++] = direct;
+                const int lo = -ya - off[k];  // x + off_k = -y < 0 reflects onto y
+                if (ya > 0 && lo >= 0 && lo < na && lo + off[k] < 0) xs[cnt++] = lo;
+                const int hi = 2 * (na - 1) - ya - off[k];  // x + off_k > n - 1 reflects onto y
+                if (ya < na - 1 && hi >= 0 && hi < na && hi + off[k] > na - 1) xs[cnt++] = hi;
+            } else {
+                xs[cnt++] = ((ya - off[k]) % na + na) % na;
+            }
+            for (int m = 0; m < cnt; ++m) {
+                int c[3] = {x, y, z};
+                c[a] = xs[m];
+                s += cof[k] * h[a * nodes + ((int64_t)c[2] * N1 + c[1]) * N0 + c[0]];
+            }
         }
     }
     dth0[n] += s * inv12dx;
@@ -658,8 +748,12 @@ template <class L, typename T> cudaError_t seed_t(lb_adj *a, const double *dLdu)
             // FP64 seed into the other field, then round(phi 2^G) with max|phi| 2^G < 2^56:
             // seven bits of headroom for the channel sums and the (measured, < 1.3x) growth
             double *tmp = (double *)a->phi[a->pcur ^ 1];
-            lbk::adj_seed_kernel<L, T, double><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
-                (const T *)c->f[c->cur], a->ag, a->K, dLdu, tmp, a->slot_step);
+            if (a->ag.mirror)
+                lbk::adj_seed_kernel<L, T, double, true><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
+                    (const T *)c->f[c->cur], a->ag, a->K, dLdu, tmp, a->slot_step);
+            else
+                lbk::adj_seed_kernel<L, T, double><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
+                    (const T *)c->f[c->cur], a->ag, a->K, dLdu, tmp, a->slot_step);
             cudaError_t e = cudaGetLastError();
             const int64_t n = (int64_t)c->q * a->ag.slab;
             double mx = 0.0;
@@ -677,24 +771,33 @@ template <class L, typename T> cudaError_t seed_t(lb_adj *a, const double *dLdu)
         }
     }
     using A = AdjT<T>;
-    lbk::adj_seed_kernel<L, T, A><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
-        (const T *)c->f[c->cur], a->ag, a->K, dLdu, (A *)a->phi[a->pcur], a->slot_step);
+    if (a->ag.mirror)
+        lbk::adj_seed_kernel<L, T, A, true><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
+            (const T *)c->f[c->cur], a->ag, a->K, dLdu, (A *)a->phi[a->pcur], a->slot_step);
+    else
+        lbk::adj_seed_kernel<L, T, A><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
+            (const T *)c->f[c->cur], a->ag, a->K, dLdu, (A *)a->phi[a->pcur], a->slot_step);
     return cudaGetLastError();
 }
 
-template <class L, typename T, typename A> cudaError_t step_a(lb_adj *a, const void *Pn)
+template <class L, typename T, typename A, bool MIR> cudaError_t step_m(lb_adj *a, const void *Pn)
 {
     lb_ctx *c = a->ctx;
     const unsigned nb = (unsigned)sweep_blocks(a->ag);
     const A *in = (const A *)a->phi[a->pcur];
     A *out = (A *)a->phi[a->pcur ^ 1];
     if (a->want_nu)
-        lbk::adj_step_kernel<L, T, true, A><<<nb, lbk::kSweepThreads, 0, c->stream>>>(in, (const T *)Pn, out, a->ag,
-                                                                                      a->K, a->slot_step, a->dflag);
+        lbk::adj_step_kernel<L, T, true, A, MIR><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
+            in, (const T *)Pn, out, a->ag, a->K, a->slot_step, a->dflag);
     else
-        lbk::adj_step_kernel<L, T, false, A><<<nb, lbk::kSweepThreads, 0, c->stream>>>(in, (const T *)Pn, out, a->ag,
-                                                                                       a->K, a->slot_step, a->dflag);
+        lbk::adj_step_kernel<L, T, false, A, MIR><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
+            in, (const T *)Pn, out, a->ag, a->K, a->slot_step, a->dflag);
     return cudaGetLastError();
+}
+
+template <class L, typename T, typename A> cudaError_t step_a(lb_adj *a, const void *Pn)
+{
+    return a->ag.mirror ? step_m<L, T, A, true>(a, Pn) : step_m<L, T, A, false>(a, Pn);
 }
 
 template <class L, typename T> cudaError_t step_t(lb_adj *a, const void *Pn)
@@ -727,7 +830,7 @@ template <class L> cudaError_t init_t(lb_adj *a, double *dth0)
         e = init_a<L, double>(a, dth0);
     if (e != cudaSuccess) return e;
     lbk::adj_fd4t_kernel<<<nb, 256, 0, c->stream>>>(a->h, dth0, c->d, (int)c->N[0], (int)c->N[1], (int)c->N[2],
-                                                    a->K.inv12dx);
+                                                    c->geom.mirror, a->K.inv12dx);
     return cudaGetLastError();
 }
 
@@ -813,10 +916,6 @@ lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_a
         ctx->err = "lb_adjoint_create: dL/dnu needs the paper's relaxation set";
         return LB_EINVAL;
     }
-    if (ctx->geom.mirror) {
-        ctx->err = "lb_adjoint_create: the adjoint supports periodic grids only";
-        return LB_EINVAL;
-    }
     if (C == 0) C = (int64_t)ceil(sqrt((double)T));
     if (C < 1 || C > T) {
         ctx->err = "lb_adjoint_create: checkpoint interval out of range";
@@ -892,10 +991,7 @@ lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, dou
     lbk::NvtxRange nvtx_range("lb_adjoint_forward");
     if (!a || !theta0) return LB_EINVAL;
     lb_ctx *c = a->ctx;
-    if (c->geom.mirror) {
-        c->err = "lb_adjoint_forward: the adjoint supports periodic grids only";
-        return LB_EINVAL;
-    }
+    a->ag.mirror = c->geom.mirror;  // the walls may have been set after the workspace was made
     a->forward_done = a->seeded = false;
     a->seg_loaded = -1;
     lb_status st = lb_set_theta0(c, theta0, nullptr);  // FD4 gradient: a function of theta0 alone

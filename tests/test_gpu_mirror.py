@@ -219,9 +219,6 @@ def test_set_boundary_errors():
     with pytest.raises(lb.LBError) as ei:
         s.step(1)
     assert ei.value.status == lb.LB_ESTATE
-    with pytest.raises(lb.LBError) as ei:
-        lb.Adjoint(s, 4)
-    assert ei.value.status == lb.LB_EINVAL
     s.set_theta0(th0)
     s.step(3)
     th, _, u = s.macros()
