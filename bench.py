@@ -430,6 +430,28 @@ def run_batched(local):
     t_flat = timed(base_steps * 10) * steps / (base_steps * 10)
     b.close()
     lu = nodes * steps
+    # the same workload in 64-bit fixed point (FP64-grade accuracy, 144 B per update)
+    bx = lb.Batch(sizes, [c.nu for c in cases], [c.dx for c in cases], [c.dt for c in cases], precision="fx64",
+                  stream=stream)
+    choice_fx = bx.autotune(10)
+    ex0, ex1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        bx.set_theta0(th0_d, g0_d)
+        bx.step(64)
+        bx.set_theta0(th0_d, g0_d)
+        ex0.record(stream)
+        bx.step(steps)
+        ex1.record(stream)
+        thx, ux = bx.macros()
+        errx = bx.errors(thx, ux, torch.from_numpy(ex_t).cuda(), torch.from_numpy(ex_u).cuda())
+    torch.cuda.synchronize()
+    t_fx = ex0.elapsed_time(ex1) / 1e3
+    bx.close()
+    peak = load_peaks()["hbm_gbs"]
+    fx64 = {"aggregate_mlups": lu / t_fx / 1e6, "instances_per_s": len(cases) / t_fx, "seconds": t_fx,
+            "hbm_frac": 2 * 9 * 8 * lu / t_fx / 1e9 / peak, "autotune": choice_fx,
+            "u_rmse_max_over_instances": float(np.max(errx[:, 1])),
+            "theta_rmse_max_over_instances": float(np.max(errx[:, 0]))}
     return {
         "workload": "512 x 2D D2Q9, N log-uniform [32,512], nu log-uniform [0.005,0.1], dt=4dx^2, fp32 shifted, "
                     "2000 steps",
@@ -443,6 +465,8 @@ def run_batched(local):
         "speedup_vs_one_launch_per_instance": t_base / t_tuned,
         "u_rmse_max_over_instances": float(np.max(err[:, 1])),
         "theta_rmse_max_over_instances": float(np.max(err[:, 0])),
+        "hbm_frac": 2 * 9 * 4 * lu / t_tuned / 1e9 / load_peaks()["hbm_gbs"],
+        "fx64": fx64,
     }
 
 

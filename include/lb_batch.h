@@ -37,7 +37,9 @@ typedef struct lb_batch lb_batch;
  *   nu, dx, dt  host, count values each (> 0, finite).
  *   rs    host, count relaxation sets, or NULL for Eq. (Bur-Sol) everywhere
  *         (theta_ref then 0 for every instance; see lb_batch_set_theta_ref).
- *   precision  LB_FP32_SHIFTED or LB_FP64.
+ *   precision  LB_FP32_SHIFTED, LB_FP64 or LB_FX64 (64-bit fixed point as in lb.h,
+ *            each instance scaled by its own max|theta0| at lb_batch_set_theta0,
+ *            so an instance evolves bit for bit as the same grid would alone).
  *   stream     cudaStream_t (NULL = legacy default stream).
  * Allocates two state buffers for all instances plus small tables.
  * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA.

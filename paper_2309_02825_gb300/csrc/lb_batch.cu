@@ -22,9 +22,17 @@
 
 namespace lbk {
 
+// Collision constants of a storage type: floating point, or 62-bit fixed point.
+template <typename T> struct CollOf {
+    using type = Coll<T>;
+};
+template <> struct CollOf<long long> {
+    using type = CollFx;
+};
+
 template <typename T> struct InstDesc {
     Geom g;
-    Coll<T> k;
+    typename CollOf<T>::type k;
     int64_t off;  // element offset of the instance's state in each buffer
 };
 
@@ -109,6 +117,24 @@ __global__ void __launch_bounds__(kRedThreads) batch_errors_kernel(const int64_t
         out[4 * j + 3] = sh[3][0];
     }
     (void)total_nodes;
+}
+
+// max |theta0| of each instance (one block per instance): the fixed-point scale.
+__global__ void __launch_bounds__(kRedThreads) batch_maxabs_kernel(const int64_t *__restrict__ node_off,
+                                                                   const double *__restrict__ th,
+                                                                   double *__restrict__ out)
+{
+    __shared__ double sh[kRedThreads];
+    const int j = blockIdx.x;
+    double m = 0.0;
+    for (int64_t n = node_off[j] + threadIdx.x; n < node_off[j + 1]; n += blockDim.x) m = fmax(m, fabs(th[n]));
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = sh[0];
 }
 
 }  // namespace lbk
@@ -199,7 +225,10 @@ template <typename T> cudaError_t upload_desc(lb_batch *b)
     std::vector<lbk::InstDesc<T>> h(b->count);
     for (int j = 0; j < b->count; ++j) {
         h[j].g = b->inst[j].geom;
-        h[j].k = lbk::make_coll<T>(b->inst[j]);
+        if constexpr (std::is_same<T, long long>::value)
+            h[j].k = lbk::make_coll_fx(&b->inst[j]);
+        else
+            h[j].k = lbk::make_coll<T>(b->inst[j]);
         h[j].off = b->off[j];
     }
     cudaError_t e = cudaMalloc(&b->d_desc, sizeof(lbk::InstDesc<T>) * b->count);
@@ -215,6 +244,10 @@ cudaError_t launch_group(lb_batch *b, const Group &g, int from, cudaStream_t s)
         lbk::batch_sweep_kernel<lbk::D2Q9, double><<<g.nblocks, b->threads, 0, s>>>(
             (const lbk::InstDesc<double> *)b->d_desc, g.d_blk_inst, g.d_blk_seg0, (const double *)b->buf[from],
             (double *)b->buf[from ^ 1]);
+    else if (b->precision == LB_FX64)
+        lbk::batch_sweep_kernel<lbk::D2Q9, long long><<<g.nblocks, b->threads, 0, s>>>(
+            (const lbk::InstDesc<long long> *)b->d_desc, g.d_blk_inst, g.d_blk_seg0,
+            (const long long *)b->buf[from], (long long *)b->buf[from ^ 1]);
     else
         lbk::batch_sweep_kernel<lbk::D2Q9, float><<<g.nblocks, b->threads, 0, s>>>(
             (const lbk::InstDesc<float> *)b->d_desc, g.d_blk_inst, g.d_blk_seg0, (const float *)b->buf[from],
@@ -335,18 +368,18 @@ lb_status lb_batch_create(int count, const int64_t *N, const double *nu, const d
     if (!out) return LB_EINVAL;
     *out = nullptr;
     if (count < 1 || count > 65536 || !N || !nu || !dx || !dt) return LB_EINVAL;
-    if (precision != LB_FP32_SHIFTED && precision != LB_FP64) return LB_EINVAL;
+    if (precision != LB_FP32_SHIFTED && precision != LB_FP64 && precision != LB_FX64) return LB_EINVAL;
     lb_batch *b = new (std::nothrow) lb_batch();
     if (!b) return LB_ENOMEM;
     b->count = count;
     b->precision = precision;
-    b->elem = precision == LB_FP64 ? 8 : 4;
+    b->elem = precision == LB_FP32_SHIFTED ? 4 : 8;
     b->stream = (cudaStream_t)stream;
     cudaGetDevice(&b->device);
     b->inst.resize(count);
     b->off.resize(count);
     b->node_off.resize(count + 1);
-    const int V = precision == LB_FP64 ? lbk::Vec<double>::V : lbk::Vec<float>::V;
+    const int V = precision == LB_FP32_SHIFTED ? lbk::Vec<float>::V : lbk::Vec<double>::V;
     int64_t off = 0, noff = 0;
     for (int j = 0; j < count; ++j) {
         lb_ctx &c = b->inst[j];
@@ -395,7 +428,8 @@ lb_status lb_batch_create(int count, const int64_t *N, const double *nu, const d
             return e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA;
         }
     }
-    e = precision == LB_FP64 ? upload_desc<double>(b) : upload_desc<float>(b);
+    e = precision == LB_FP64 ? upload_desc<double>(b)
+                             : (precision == LB_FX64 ? upload_desc<long long>(b) : upload_desc<float>(b));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_node_off, sizeof(int64_t) * (count + 1));
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_node_off, b->node_off.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice);
@@ -450,6 +484,25 @@ lb_status lb_batch_set_theta0(lb_batch *b, const double *theta0, const double *g
     }
     if ((e = cudaMemsetAsync(b->d_flag, 0, sizeof(int) * 2, b->stream)) != cudaSuccess)
         return bcuda(b, e, "lb_batch_set_theta0");
+    if (b->precision == LB_FX64) {
+        // each instance's scale as for one grid: max|theta0_j| 2^F_j < 2^59
+        std::vector<double> mx(b->count);
+        lbk::batch_maxabs_kernel<<<b->count, lbk::kRedThreads, 0, b->stream>>>(b->d_node_off, theta0, b->d_err);
+        if ((e = cudaGetLastError()) != cudaSuccess ||
+            (e = cudaMemcpyAsync(mx.data(), b->d_err, sizeof(double) * b->count, cudaMemcpyDeviceToHost,
+                                 b->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+            return bcuda(b, e, "lb_batch_set_theta0: max|theta0|");
+        for (int j = 0; j < b->count; ++j) {
+            if (!(mx[j] > 0.0) || !isfinite(mx[j]))
+                return bfail(b, LB_ENONPOS, "lb_batch_set_theta0: theta0 must be finite and > 0");
+            int ex = 0;
+            frexp(mx[j], &ex);
+            b->inst[j].fx_bits = 59 - ex;
+            if (b->inst[j].fx_bits > 1000 || b->inst[j].fx_bits < -1000)
+                return bfail(b, LB_EINVAL, "lb_batch_set_theta0: theta0 magnitude outside the fixed-point range");
+        }
+    }
     b->cur = 0;
     for (int j = 0; j < b->count; ++j) {
         lb_ctx &c = b->inst[j];
@@ -465,7 +518,9 @@ lb_status lb_batch_set_theta0(lb_batch *b, const double *theta0, const double *g
     if ((e = cudaMemcpyAsync(&flag, b->d_flag, sizeof(int), cudaMemcpyDeviceToHost, b->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
         return bcuda(b, e, "lb_batch_set_theta0");
-    if (flag) return bfail(b, LB_ENONPOS, "lb_batch_set_theta0: theta0 must be finite and > 0");
+    if (flag & 1) return bfail(b, LB_ENONPOS, "lb_batch_set_theta0: theta0 must be finite and > 0");
+    if (flag & 2)
+        return bfail(b, LB_EINVAL, "lb_batch_set_theta0: a gradient too steep for the fixed-point range");
     b->initialized = true;
     return LB_OK;
 }

@@ -220,6 +220,7 @@ struct NvtxRange {
 // Returns false if a rate leaves (0, 2) or a weight is not finite.
 bool derive_params(lb_ctx &c, const lb_relax *rs);
 template <typename T> Coll<T> make_coll(const lb_ctx &c);
+CollFx make_coll_fx(const lb_ctx *c);  // the same constants in 62-bit fixed point
 
 constexpr int kRedThreads = 256;
 constexpr int kRedSlots = 16;  // doubles per block partial (>= 3*(d+1)+1)

@@ -395,7 +395,7 @@ class Batch:
             self.node_off.append(self.node_off[-1] + n)
         flat = (ctypes.c_int64 * (2 * self.count))(*[v for s in self.sizes for v in s])
         arr = lambda v: (ctypes.c_double * self.count)(*[float(x) for x in v])
-        self.precision = {"fp64": LB_FP64, "fp32s": LB_FP32_SHIFTED}[precision]
+        self.precision = {"fp64": LB_FP64, "fp32s": LB_FP32_SHIFTED, "fx64": LB_FX64}[precision]
         out = ctypes.c_void_p()
         st = self._lib.lb_batch_create(self.count, flat, arr(nu), arr(dx), arr(dt), None, self.precision,
                                        _stream_handle(stream), ctypes.byref(out))

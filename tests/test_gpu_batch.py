@@ -39,7 +39,7 @@ def _single(j, prob, dx, dt, n, precision, theta_ref):
     return th, u
 
 
-@pytest.mark.parametrize("precision", ["fp32s", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32s", "fp64", "fx64"])
 @pytest.mark.parametrize("sched", [(96e6, 256, True), (0.0, 128, False), (40e3, 512, True), (1e18, 256, True)])
 def test_batch_equals_single_instance_bitwise(precision, sched):
     probs, dxs, dts, th0, g0 = _setup()
@@ -56,10 +56,11 @@ def test_batch_equals_single_instance_bitwise(precision, sched):
         assert torch.equal(us[j], u1), j
 
 
-def test_batch_fp64_matches_oracle():
+@pytest.mark.parametrize("precision", ["fp64", "fx64"])
+def test_batch_fp64_matches_oracle(precision):
     probs, dxs, dts, th0, g0 = _setup(11)
     n = 20
-    b = lb.Batch(SIZES, NUS, dxs, dts, precision="fp64")
+    b = lb.Batch(SIZES, NUS, dxs, dts, precision=precision)
     b.set_theta0(torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda())
     b.step(n)
     th, u = b.macros()
