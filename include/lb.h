@@ -266,6 +266,19 @@ lb_status lb_load_state(lb_ctx *ctx, const void *buf, int64_t step);
  */
 lb_status lb_selftest_staging_timeout(double limit_s, void *stream, double *waited_s);
 
+/*
+ * Self-test of the integer -> FP64 conversions (round to nearest, ties to
+ * even, assembled from the IEEE 754 binary64 encoding on the integer pipes)
+ * that the fixed-point reverse pass uses for its exact 128-bit sums.  For
+ * i < n: out128[i] = the 128-bit integer hi[i] * 2^64 + lo[i] (hi signed,
+ * lo unsigned) converted, out64[i] = lo[i] read as a signed 64-bit integer,
+ * converted.  All four arrays are caller-owned device arrays of n entries;
+ * the call is ordered on `stream` and synchronises it.  LB_EINVAL for n < 0
+ * or a NULL array with n > 0.  No paper counterpart.
+ */
+lb_status lb_selftest_int_to_f64(const long long *hi, const unsigned long long *lo, int64_t n, double *out128,
+                                 double *out64, void *stream);
+
 /* Message for the last failing call on ctx (or of lb_create, with ctx == NULL). */
 const char *lb_last_error(const lb_ctx *ctx);
 

@@ -259,17 +259,11 @@ __device__ __forceinline__ A adj_node(A *l, const T *fv, const AdjK &K)
     return eterm;
 }
 
-__device__ __forceinline__ double i128_to_double(__int128 v)
-{
-    const long long hi = (long long)(v >> 64);
-    const unsigned long long lo = (unsigned long long)v;
-    return fma((double)hi, 0x1p64, (double)lo);
-}
-
 // The node update of the fixed-point reverse pass (64-bit fixed-point states):
 // K^T from exact integer channel sums and rounded 64x62-bit products; with
-// NU, lambda . (dK/deps) f as exact 128-bit dot products of the integer
-// channels with the state's integer moments, converted once each.  Sets
+// NU, lambda . (dK/deps) f from exact 128-bit dot products of the integer
+// channels with the state's integer moments, each converted to FP64 once (on
+// the integer pipes) and combined with the FP64 eps-derivatives.  Sets
 // `range` when an output leaves |v| < 2^59 (the fields start below 2^56).
 template <class L, bool NU>
 __device__ __forceinline__ double adj_node_fx(long long *l, const long long *fv, const AdjK &K, bool &range)
@@ -303,9 +297,9 @@ __device__ __forceinline__ double adj_node_fx(long long *l, const long long *fv,
 #pragma unroll
         for (int p = 0; p < NP; ++p) S3 += (__int128)m.Pab[p] * P[p];
         const Coll<double> &kd = K.kdx;
-        const double lt = fma(kd.c0, (double)l0, fma(kd.cA, (double)sax, kd.wd * (double)sdg));
-        eterm = fma((double)m.th, lt, fma(kd.k2, i128_to_double(S2), fma(kd.k1, i128_to_double(S1),
-                                                                           kd.k3 * i128_to_double(S3))));
+        const double lt = fma(kd.c0, i64_to_f64_rn(l0), fma(kd.cA, i64_to_f64_rn(sax), kd.wd * i64_to_f64_rn(sdg)));
+        eterm = fma(i64_to_f64_rn(m.th), lt,
+                    fma(kd.k2, i128_to_f64_rn(S2), fma(kd.k1, i128_to_f64_rn(S1), kd.k3 * i128_to_f64_rn(S3))));
     }
     const long long Lt = mulfx(l0, K.c0k) + mulfx(sax, K.cAk) + mulfx(sdg, K.wdk);
     long long LP[D], LJ[D];
@@ -337,6 +331,17 @@ __device__ __forceinline__ double adj_node_fx(long long *l, const long long *fv,
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) range |= !(l[i] < kLim && l[i] > -kLim);
     return eterm;
+}
+
+// The integer -> FP64 conversions of the fixed-point eps-term, for their self-test.
+__global__ void int_to_f64_selftest_kernel(const long long *__restrict__ hi, const unsigned long long *__restrict__ lo,
+                                           int64_t n, double *__restrict__ out128, double *__restrict__ out64)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const __int128 v = (__int128)(((unsigned __int128)(unsigned long long)hi[i] << 64) | lo[i]);
+        out128[i] = i128_to_f64_rn(v);
+        out64[i] = i64_to_f64_rn((long long)lo[i]);
+    }
 }
 
 // Sum type of a lane's eps-terms: the adjoint's own type, FP64 for fixed point.
@@ -382,8 +387,8 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
             constexpr int i = decltype(I)::value;
             const double fv = to_f(f[i][v], K.scale) + K.shift[i];
             th += fv;
-            static_for<0, L::D>([&](auto A) {
-                constexpr int a = decltype(A)::value;
+            static_for<0, L::D>([&](auto Ad) {
+                constexpr int a = decltype(Ad)::value;
                 constexpr int e = L::E[i][a];
                 if constexpr (e != 0) J[a] += e * fv;
             });
@@ -401,8 +406,8 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             double s = 0.0;
-            static_for<0, L::D>([&](auto A) {
-                constexpr int a = decltype(A)::value;
+            static_for<0, L::D>([&](auto Ad) {
+                constexpr int a = decltype(Ad)::value;
                 constexpr int e = L::E[i][a];
                 s += gu[a] * ((double)e * K.ucoef - u[a]);
             });
@@ -472,8 +477,10 @@ __global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const A *__rest
         if (range) atomicOr(flag, 1);
     }
     if constexpr (NU) {
+        // one writer per slot per launch, launches in stream order: the
+        // reduction (no return value, so the warp does not wait) is deterministic
         acc = warp_sum(acc);
-        if (lane == 0) slot[seg] += (double)acc;
+        if (lane == 0) atomicAdd(slot + seg, (double)acc);
     }
 }
 
@@ -620,6 +627,15 @@ struct lb_adj {
     bool forward_done = false, seeded = false;
     lbk::AdjK K{};
     size_t bytes = 0;
+    // Recorded graphs, by the parity of the buffer they start from: C forward
+    // sweeps (valid for the walls they were recorded with), and one whole
+    // reverse segment, C - 1 recompute sweeps then C reverse steps (valid for
+    // the constants K and walls they were recorded with).
+    cudaGraphExec_t fgraph[2] = {nullptr, nullptr};
+    unsigned fmirror[2] = {0u, 0u};
+    cudaGraphExec_t rgraph[2] = {nullptr, nullptr};
+    lbk::AdjK rK[2]{};
+    unsigned rmirror[2] = {0u, 0u};
 };
 
 namespace {
@@ -650,7 +666,45 @@ void free_adj(lb_adj *a)
     cudaFree(a->slot_init);
     cudaFree(a->dsum);
     cudaFree(a->dflag);
+    for (int p = 0; p < 2; ++p) {
+        if (a->fgraph[p]) cudaGraphExecDestroy(a->fgraph[p]);
+        if (a->rgraph[p]) cudaGraphExecDestroy(a->rgraph[p]);
+    }
     delete a;
+}
+
+// Record into *out the launches `body` makes on the context's stream (swapped
+// for a private capturing stream meanwhile).
+template <class F> cudaError_t record_graph(lb_ctx *c, cudaGraphExec_t *out, F &&body)
+{
+    if (*out) {
+        cudaGraphExecDestroy(*out);
+        *out = nullptr;
+    }
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaStream_t user = c->stream;
+    c->stream = cs;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = body();
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    c->stream = user;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    return e;
+}
+
+bool stream_capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return true;
+    return cap != cudaStreamCaptureStatusNone;
 }
 
 // Collision, recovery and initialisation constants and their eps-derivatives
@@ -1003,13 +1057,32 @@ lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, dou
         (e = cudaMemcpyAsync(a->grad, c->gradtmp, sizeof(double) * c->d * c->nodes, cudaMemcpyDeviceToDevice,
                              c->stream)) != cudaSuccess)
         return acuda(a, e, "lb_adjoint_forward");
+    const bool cap = stream_capturing(c->stream);
     for (int64_t k = 0; k * a->C < a->T; ++k) {
         if (a->want_nu &&
             (e = cudaMemcpyAsync(a->ck[k], c->f[c->cur], a->state_bytes, cudaMemcpyDeviceToDevice, c->stream)) !=
                 cudaSuccess)
             return acuda(a, e, "lb_adjoint_forward: checkpoint");
         const int64_t n = std::min<int64_t>(a->C, a->T - k * a->C);
-        if ((st = lb_step(c, n)) != LB_OK) return st;
+        if (n < a->C || cap) {  // a short last segment, or inside the caller's capture: plain launches
+            if ((st = lb_step(c, n)) != LB_OK) return st;
+            continue;
+        }
+        const int p = c->cur;
+        if (!a->fgraph[p] || a->fmirror[p] != c->geom.mirror) {
+            e = record_graph(c, &a->fgraph[p], [&]() {
+                cudaError_t r = cudaSuccess;
+                for (int64_t m = 0, q = p; m < n && r == cudaSuccess; ++m, q ^= 1)
+                    r = lbk::launch_sweep(c, c->f[q], c->f[q ^ 1]);
+                return r;
+            });
+            if (e != cudaSuccess) return acuda(a, e, "lb_adjoint_forward: record");
+            a->fmirror[p] = c->geom.mirror;
+        }
+        if ((e = cudaGraphLaunch(a->fgraph[p], c->stream)) != cudaSuccess)
+            return acuda(a, e, "lb_adjoint_forward: graph");
+        c->cur ^= (int)(n & 1);
+        c->step += n;
     }
     if ((theta || u) && (st = lb_macros(c, theta, nullptr, u)) != LB_OK) return st;
     a->forward_done = true;
@@ -1042,13 +1115,48 @@ lb_status lb_adjoint_step(lb_adj *a, int64_t nsteps)
     if (!a->seeded) return afail(a, LB_ESTATE, "lb_adjoint_step: call lb_adjoint_seed first");
     if (a->done + nsteps > a->T) return afail(a, LB_EINVAL, "lb_adjoint_step: more reverse steps than forward");
     cudaError_t e;
-    for (int64_t s = 0; s < nsteps; ++s) {
+    lb_ctx *c = a->ctx;
+    const bool cap = stream_capturing(c->stream);
+    const int64_t C = a->C;
+    for (int64_t s = 0; s < nsteps;) {
         const int64_t n = a->T - 1 - a->done;  // producing phi_n from phi_{n+1}
+        const int64_t k = n / C;
+        if (a->want_nu && !cap && a->seg_loaded != k && n == k * C + C - 1 && nsteps - s >= C) {
+            // a whole segment as one recorded graph: the same launches, in the same order, as below
+            if ((e = cudaMemcpyAsync(a->seg[0], a->ck[k], a->state_bytes, cudaMemcpyDeviceToDevice, c->stream)) !=
+                cudaSuccess)
+                return acuda(a, e, "lb_adjoint_step: checkpoint");
+            const int p = a->pcur;
+            if (!a->rgraph[p] || a->rmirror[p] != a->ag.mirror || memcmp(&a->rK[p], &a->K, sizeof(a->K)) != 0) {
+                e = record_graph(c, &a->rgraph[p], [&]() {
+                    cudaError_t r = cudaSuccess;
+                    for (int64_t m = 1; m < C && r == cudaSuccess; ++m)
+                        r = lbk::launch_sweep(c, a->seg[m - 1], a->seg[m]);
+                    for (int64_t j = C - 1; j >= 0 && r == cudaSuccess; --j) {
+                        r = do_step(a, a->seg[j]);
+                        a->pcur ^= 1;
+                    }
+                    a->pcur = p;
+                    return r;
+                });
+                if (e != cudaSuccess) return acuda(a, e, "lb_adjoint_step: record");
+                a->rK[p] = a->K;
+                a->rmirror[p] = a->ag.mirror;
+            }
+            if ((e = cudaGraphLaunch(a->rgraph[p], c->stream)) != cudaSuccess)
+                return acuda(a, e, "lb_adjoint_step: graph");
+            a->seg_loaded = k;
+            a->pcur ^= (int)(C & 1);
+            a->done += C;
+            s += C;
+            continue;
+        }
         const void *Pn = nullptr;
         if (a->want_nu && (e = state_at(a, n, &Pn)) != cudaSuccess) return acuda(a, e, "lb_adjoint_step: recompute");
         if ((e = do_step(a, Pn)) != cudaSuccess) return acuda(a, e, "lb_adjoint_step: launch");
         a->pcur ^= 1;
         ++a->done;
+        ++s;
     }
     return LB_OK;
 }
@@ -1083,6 +1191,19 @@ lb_status lb_adjoint_result(lb_adj *a, double *dL_dtheta0, double *dL_dnu)
     }
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return acuda(a, e, "lb_adjoint_result");
     return LB_OK;
+}
+
+lb_status lb_selftest_int_to_f64(const long long *hi, const unsigned long long *lo, int64_t n, double *out128,
+                                 double *out64, void *stream)
+{
+    if (n < 0 || (n > 0 && (!hi || !lo || !out128 || !out64))) return LB_EINVAL;
+    if (n == 0) return LB_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned nb = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+    lbk::int_to_f64_selftest_kernel<<<nb, 256, 0, st>>>(hi, lo, n, out128, out64);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? LB_OK : LB_ECUDA;
 }
 
 lb_status lb_adjoint_info(const lb_adj *a, double *info)

@@ -74,6 +74,51 @@ __device__ __forceinline__ long long mulfx(long long a, long long k)
     return (long long)((p + ((__int128)1 << (kFxCoefBits - 1))) >> kFxCoefBits);
 }
 
+// Integer -> FP64 with round-to-nearest-even, assembled from the IEEE 754
+// binary64 encoding on the integer pipes (the conversion instructions issue
+// at the FP64 rate, 1/64 of the integer rate on this part).  For a magnitude
+// a with its leading one at bit e: the 53 bits from e down are the
+// significand (implicit bit included), the bits below decide the rounding
+// (above half, or exactly half with an odd significand, round up; a carry out
+// of the significand moves into the exponent field by the same addition), and
+// the biased exponent is e + 1023.
+__device__ __forceinline__ double u64_bits_to_f64(unsigned long long a, unsigned long long sign)
+{
+    if (a == 0ull) return 0.0;
+    const int e = 63 - __clzll((long long)a);
+    unsigned long long mant, up = 0ull;
+    if (e <= 52) {
+        mant = a << (52 - e);
+    } else {
+        const int sh = e - 52;  // 1 .. 11
+        mant = a >> sh;
+        const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        up = (rem > half || (rem == half && (mant & 1ull))) ? 1ull : 0ull;
+    }
+    // (e + 1022) << 52 plus the significand's implicit 2^52 gives the biased exponent e + 1023
+    return __longlong_as_double((long long)((((unsigned long long)(e + 1022) << 52) + mant + up) | sign));
+}
+
+__device__ __forceinline__ double i64_to_f64_rn(long long v)
+{
+    const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    return u64_bits_to_f64(a, v < 0 ? 0x8000000000000000ull : 0ull);
+}
+
+__device__ __forceinline__ double i128_to_f64_rn(__int128 v)
+{
+    const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned __int128 a = v < 0 ? (unsigned __int128)0 - (unsigned __int128)v : (unsigned __int128)v;
+    const unsigned long long hi = (unsigned long long)(a >> 64);
+    if (hi == 0ull) return u64_bits_to_f64((unsigned long long)a, sign);
+    const int e = 127 - __clzll((long long)hi);  // 64 .. 127
+    const int sh = e - 52;                        // 12 .. 75
+    const unsigned long long mant = (unsigned long long)(a >> sh);
+    const unsigned __int128 rem = a & (((unsigned __int128)1 << sh) - 1), half = (unsigned __int128)1 << (sh - 1);
+    const unsigned long long up = (rem > half || (rem == half && (mant & 1ull))) ? 1ull : 0ull;
+    return __longlong_as_double((long long)((((unsigned long long)(e + 1022) << 52) + mant + up) | sign));
+}
+
 // Conversion of an FP64 value to the storage type (64-bit fixed point uses
 // round-to-nearest of v * 2^F).  `range` is set when a fixed-point value
 // would exceed 2^61 (4x the largest theta0), leaving the sums their headroom.

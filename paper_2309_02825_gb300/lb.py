@@ -79,6 +79,7 @@ def load():
             "lb_last_error": ([vp], ctypes.c_char_p),
             "lb_reduce_static": ([ctypes.c_int, i64, vp, vp, vp, vp, vp, vp], ctypes.c_int),
             "lb_selftest_staging_timeout": ([dbl, vp, pd], ctypes.c_int),
+            "lb_selftest_int_to_f64": ([vp, vp, i64, vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -229,6 +230,25 @@ def lb_selftest_staging_timeout(limit_s=0.05, stream=None):
     w = ctypes.c_double()
     st = lib.lb_selftest_staging_timeout(float(limit_s), _stream_handle(stream), ctypes.byref(w))
     return st, w.value
+
+
+def lb_selftest_int_to_f64(hi, lo, stream=None):
+    """(out128, out64): the library's integer -> FP64 conversions of the
+    128-bit integers hi * 2^64 + lo and of lo read as int64 (CUDA int64
+    tensors of equal length; lo holds the unsigned low words' bit patterns)."""
+    lib = load()
+    if not (isinstance(hi, torch.Tensor) and isinstance(lo, torch.Tensor) and hi.is_cuda and lo.is_cuda
+            and hi.dtype == torch.int64 and lo.dtype == torch.int64 and hi.is_contiguous() and lo.is_contiguous()
+            and hi.numel() == lo.numel()):
+        raise TypeError("hi and lo must be contiguous CUDA int64 tensors of equal length")
+    o128 = torch.empty(hi.numel(), dtype=torch.float64, device=hi.device)
+    o64 = torch.empty(hi.numel(), dtype=torch.float64, device=hi.device)
+    st = lib.lb_selftest_int_to_f64(ctypes.c_void_p(hi.data_ptr()), ctypes.c_void_p(lo.data_ptr()), hi.numel(),
+                                    ctypes.c_void_p(o128.data_ptr()), ctypes.c_void_p(o64.data_ptr()),
+                                    _stream_handle(stream))
+    if st != LB_OK:
+        raise LBError(st, "lb_selftest_int_to_f64")
+    return o128, o64
 
 
 def lb_state_layout(ctx):
