@@ -354,6 +354,26 @@ __device__ __forceinline__ void gather_two_phase(const T *__restrict__ src, cons
     });
 }
 
+// Gather for the flat lane mapping (periodic grids): one node (x, row) per
+// lane, and each population read by one scalar load at its source
+// (x - e_x mod N0, shifted row).  Neighbouring lanes read neighbouring
+// elements, so each load is coalesced even where the warp crosses a row end;
+// there are no shuffles and no per-lane halo branches.
+template <class L, typename T>
+__device__ __forceinline__ void gather_flat(const T *__restrict__ src, const Geom &g, int64_t row, int x,
+                                            T (&f)[L::Q])
+{
+    const RowPos rpos = row_pos<L::D>(g, row);
+    const int xl = (x == 0) ? g.N0 - 1 : x - 1;  // x - 1 and x + 1, periodic
+    const int xr = (x == g.N0 - 1) ? 0 : x + 1;
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2], ew = L::E[i][3];
+        const T *rp = src + (int64_t)i * g.slab + src_row<L::D, ey, ez, ew>(g, rpos) * g.pitch;
+        f[i] = __ldg(rp + (ex == 1 ? xl : (ex == -1 ? xr : x)));
+    });
+}
+
 template <class L, typename T, int V = Vec<T>::V, bool MIR = false>
 __device__ __forceinline__ void gather(const T *__restrict__ src, const Geom &g, int64_t row, int x0, int lane,
                                        T (&f)[L::Q][V])
@@ -748,6 +768,45 @@ __global__ void __launch_bounds__(sweep_threads<T>()) sweep_kernel(const T *__re
     T *dp = dst + row * g.pitch + x0 + V * lane;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * g.slab, f[i]);
+}
+
+// Node `q` of the flat mapping (row-major over the N0 nodes of each row):
+// its row and x.  Lanes past the last node take the last one (loads only;
+// they never store).
+__device__ __forceinline__ void flat_node(const Geom &g, int64_t q, int64_t &row, int &x)
+{
+    const unsigned n = (unsigned)(g.rows * g.N0);  // < 2^31 wherever the flat mapping is used
+    const unsigned qc = q < (int64_t)n ? (unsigned)q : n - 1u;
+    const unsigned r = qc / (unsigned)g.N0;
+    row = r;
+    x = (int)(qc - r * (unsigned)g.N0);
+}
+
+// The sweep with the flat mapping, for periodic 4D grids with 8-byte states
+// whose rows do not fill whole warps (Example 4's 20 .. 50 nodes per row):
+// same pull and collision per node as sweep_kernel.  Every lane works (the
+// row-segment mapping leaves up to 38 % of them idle at N0 = 20 .. 50), and
+// with one node per lane and no halo the kernel holds 80-90 registers instead
+// of 128-164, so more warps stay resident.
+template <class L, typename T, class K>
+__global__ void __launch_bounds__(sweep_threads<T>()) sweep_flat_kernel(const T *__restrict__ src,
+                                                                        T *__restrict__ dst, Geom g, K k)
+{
+    constexpr int TH = sweep_threads<T>();
+    const int lane = threadIdx.x & 31;
+    const int64_t seg = (int64_t)blockIdx.x * (TH / 32) + (threadIdx.x >> 5);
+    if (seg >= g.fseg) return;  // warp-uniform
+    const int64_t q = seg * 32 + lane;
+    int64_t row;
+    int x;
+    flat_node(g, q, row, x);
+    T f[L::Q];
+    gather_flat<L, T>(src, g, row, x, f);
+    collide(L{}, f, k);
+    if (q >= g.rows * g.N0) return;  // past the last node: loads only
+    T *dp = dst + row * g.pitch + x;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) dp[(int64_t)i * g.slab] = f[i];
 }
 
 }  // namespace lbk

@@ -34,7 +34,15 @@ CollFx make_coll_fx(const lb_ctx *c)
 template <class L> static cudaError_t sweep_fx_t(lb_ctx *c, const void *src, void *dst)
 {
     constexpr int TH = sweep_threads<long long>();
-    const unsigned nb = (unsigned)((c->geom.nseg + TH / 32 - 1) / (TH / 32));
+    const bool flat = sweep_flat(c->geom, L::D, 8);
+    const unsigned nb = (unsigned)(((flat ? c->geom.fseg : c->geom.nseg) + TH / 32 - 1) / (TH / 32));
+    if constexpr (L::D == 4) {
+        if (flat) {
+            sweep_flat_kernel<L, long long, CollFx><<<nb, TH, 0, c->stream>>>(
+                (const long long *)src, (long long *)dst, c->geom, make_coll_fx(c));
+            return cudaGetLastError();
+        }
+    }
     if (c->geom.mirror)
         sweep_kernel<L, long long, CollFx, true><<<nb, TH, 0, c->stream>>>(
             (const long long *)src, (long long *)dst, c->geom, make_coll_fx(c));

@@ -86,6 +86,11 @@ struct Geom {
     int seg_per_row;     // ceil(pitch / (32*W)): warp segments per row, W values a lane
     int64_t nseg;        // rows * seg_per_row (one warp per segment)
     unsigned mirror;     // bit a: axis a has mirror walls on nodes 0 and N_a - 1 (else periodic)
+    // Flat mapping of the periodic 4D sweep with 8-byte states: the nodes
+    // numbered row-major, one per lane, 32 to a warp, running on over row
+    // ends.  fseg = its warp count, 0 where rows fill whole warps (or the
+    // node count reaches 2^31).
+    int64_t fseg;
 };
 
 // Index of the velocity e_i with its components on the axes of mask M
@@ -126,8 +131,16 @@ inline Geom make_geom(int64_t N0, int64_t N1, int64_t N2, int64_t N3, int V, int
     g.seg_per_row = (g.pitch + 32 * W - 1) / (32 * W);
     g.nseg = g.rows * g.seg_per_row;
     g.mirror = 0;
+    const int64_t nodes = g.rows * g.N0;
+    g.fseg = (g.pitch % (32 * W) != 0 && nodes < (1ll << 31) - 64) ? (nodes + 31) / 32 : 0;
     return g;
 }
+
+// Whether a sweep of lattice dimension d with elem-byte states takes the flat
+// mapping: measured faster only for 4D 8-byte states (whose row-segment
+// gather holds q = 33 vectors and keeps few warps resident), and used only on
+// periodic grids.
+inline bool sweep_flat(const Geom &g, int d, int elem) { return d == 4 && elem == 8 && g.fseg && !g.mirror; }
 
 // Collision constants (lattice units), precomputed on the host from the
 // relaxation set.  With sigma = c_s^2/c^2 = 2 w1 + 4(d-1) wd the

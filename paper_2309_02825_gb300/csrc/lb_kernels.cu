@@ -462,7 +462,15 @@ template Coll<float> make_coll<float>(const lb_ctx &);
 template <class L, typename T> static cudaError_t sweep_t(lb_ctx *c, const void *src, void *dst)
 {
     constexpr int TH = sweep_threads<T>();
-    const unsigned nb = (unsigned)((c->geom.nseg + TH / 32 - 1) / (TH / 32));
+    const bool flat = sweep_flat(c->geom, L::D, (int)sizeof(T));
+    const unsigned nb = (unsigned)(((flat ? c->geom.fseg : c->geom.nseg) + TH / 32 - 1) / (TH / 32));
+    if constexpr (L::D == 4 && sizeof(T) == 8) {
+        if (flat) {
+            sweep_flat_kernel<L, T, Coll<T>><<<nb, TH, 0, c->stream>>>((const T *)src, (T *)dst, c->geom,
+                                                                       make_coll<T>(*c));
+            return cudaGetLastError();
+        }
+    }
     if (c->geom.mirror)
         sweep_kernel<L, T, Coll<T>, true><<<nb, TH, 0, c->stream>>>(
             (const T *)src, (T *)dst, c->geom, make_coll<T>(*c));
