@@ -84,6 +84,8 @@ CASES = [
     (2, (200, 17), 150),
     (3, (37, 22, 13), 1), (3, (37, 22, 13), 9), (3, (64, 16, 8), 16), (3, (3, 4, 5), 5), (3, (70, 1, 6), 4),
     (4, (10, 8, 6, 5), 1), (4, (10, 8, 6, 5), 6), (4, (70, 3, 4, 2), 4), (4, (3, 4, 2, 5), 3),
+    # rows that fill whole warps: the 4D 8-byte sweeps take row segments here, the flat mapping elsewhere
+    (4, (64, 3, 4, 3), 4), (4, (32, 5, 3, 3), 3),
 ]
 
 
