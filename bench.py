@@ -862,7 +862,8 @@ def time_oracle(N, sweeps):
 
 
 def cpu_baseline(args):
-    sweeps = 2
+    # about 1.5 s per 4096^2 sweep on one Grace core: the work of 8 such sweeps is a 10-15 s sample
+    sweeps = max(8, int(round(8 * (4096.0 / max(args.N, 1)) ** 2)))
     v, el = time_oracle(args.N, sweeps)
     return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d sweeps of the %d^2 D2Q9 FP64 oracle (%.1f s, single thread)" % (sweeps, args.N, el)}
