@@ -129,6 +129,63 @@ __device__ __forceinline__ void gather_rev_walls(const A *__restrict__ src, cons
     });
 }
 
+// The periodic two-phase gather split in two calls, so that a kernel can
+// issue the vector loads of two fields before it shuffles either (the same
+// loads and halo scalars as gather_two_phase).  REV pulls from x + e_i, the
+// adjoint's reverse pull, instead of x - e_i.  gather_late_finish shifts by
+// e_x and reads the row-end wrap of the lane holding the row's last node.
+template <class L, typename T, int V, bool REV>
+__device__ __forceinline__ void gather_early(const T *__restrict__ src, const Geom &g, const RowPos &rpos, int x0,
+                                             int lane, T (&f)[L::Q][V], T (&halo)[L::Q])
+{
+    const int xb = x0 + V * lane;
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int sg = REV ? -1 : 1;
+        constexpr int ex = sg * L::E[i][0], ey = sg * L::E[i][1], ez = sg * L::E[i][2], ew = sg * L::E[i][3];
+        const T *rp = src + (int64_t)i * g.slab + src_row<L::D, ey, ez, ew>(g, rpos) * g.pitch;
+        ld_vec(rp + xb, f[i]);
+        halo[i] = T(0);
+        if constexpr (ex == 1) {
+            if (lane == 0) halo[i] = rp[xb == 0 ? g.N0 - 1 : xb - 1];
+        } else if constexpr (ex == -1) {
+            const int x = xb + V - 1;
+            if (lane == 31 && x + 1 < g.N0) halo[i] = rp[x + 1];
+        }
+    });
+}
+
+template <class L, typename T, int V, bool REV>
+__device__ __forceinline__ void gather_late_finish(const T *__restrict__ src, const Geom &g, const RowPos &rpos,
+                                                   int x0, int lane, T (&f)[L::Q][V], const T (&halo)[L::Q])
+{
+    const int xb = x0 + V * lane;
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int sg = REV ? -1 : 1;
+        constexpr int ex = sg * L::E[i][0], ey = sg * L::E[i][1], ez = sg * L::E[i][2], ew = sg * L::E[i][3];
+        if constexpr (ex == 1) {
+            T left = __shfl_up_sync(0xffffffffu, f[i][V - 1], 1);
+            if (lane == 0) left = halo[i];
+#pragma unroll
+            for (int k = V - 1; k > 0; --k) f[i][k] = f[i][k - 1];
+            f[i][0] = left;
+        } else if constexpr (ex == -1) {
+            T right = __shfl_down_sync(0xffffffffu, f[i][0], 1);
+            if (lane == 31) right = halo[i];
+#pragma unroll
+            for (int k = 0; k < V - 1; ++k) f[i][k] = f[i][k + 1];
+            f[i][V - 1] = right;
+            if (xb + V >= g.N0) {  // the node at x = N0 - 1 pulls across the row end
+                const T *wp = src + (int64_t)i * g.slab + src_row<L::D, ey, ez, ew>(g, rpos) * g.pitch;
+#pragma unroll
+                for (int k = 0; k < V; ++k)
+                    if (xb + k + 1 == g.N0) f[i][k] = wp[0];
+            }
+        }
+    });
+}
+
 // Moments of one node's distributions in the accumulation type of the
 // storage (exact int64 sums for fixed point): theta, J_a, P_aa, P_ab.
 template <class L, typename A> struct NodeMoments {
@@ -428,28 +485,47 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
     if (lane == 0) slot[seg] += acc;
 }
 
+// Threads per block of the reverse step: 128 for FP32 arithmetic, whose
+// early-issued gathers need 72 registers (at 256 threads a 512^2 step would
+// no longer fit one wave), else 256.
+template <typename A> __host__ __device__ constexpr int adj_threads()
+{
+    return std::is_same<A, float>::value ? 128 : kSweepThreads;
+}
+
 // One reverse step: phi_out = K^T lambda(phi_in); eps-term if NU.
 template <class L, typename T, bool NU, typename A, bool MIR = false>
-__global__ void __launch_bounds__(kSweepThreads) adj_step_kernel(const A *__restrict__ phi_in,
+__global__ void __launch_bounds__(adj_threads<A>()) adj_step_kernel(const A *__restrict__ phi_in,
                                                                  const T *__restrict__ Pn, A *__restrict__ phi_out,
                                                                  Geom g, AdjK K, double *__restrict__ slot,
                                                                  int *__restrict__ flag)
 {
     constexpr int V = 2;
     const int lane = threadIdx.x & 31;
-    const int64_t seg = (int64_t)blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
+    const int64_t seg = (int64_t)blockIdx.x * (adj_threads<A>() / 32) + (threadIdx.x >> 5);
     if (seg >= g.nseg) return;
     const int64_t row = seg / g.seg_per_row;
     const int x0 = (int)(seg - row * g.seg_per_row) * (32 * V);
     A lam[L::Q][V];
-    if constexpr (MIR)
-        gather_rev_walls<L, A>(phi_in, g, row, x0, lane, lam);
-    else
-        gather_rev<L, A>(phi_in, g, row, x0, lane, lam);
+    T f[L::Q][V];
+    if constexpr (!MIR && NU && std::is_same<A, float>::value) {
+        // FP32: the vector loads of both fields in flight before either is shuffled
+        const RowPos rpos = row_pos<L::D>(g, row);
+        A hl[L::Q];
+        T hf[L::Q];
+        gather_early<L, A, V, true>(phi_in, g, rpos, x0, lane, lam, hl);
+        gather_early<L, T, V, false>(Pn, g, rpos, x0, lane, f, hf);
+        gather_late_finish<L, A, V, true>(phi_in, g, rpos, x0, lane, lam, hl);
+        gather_late_finish<L, T, V, false>(Pn, g, rpos, x0, lane, f, hf);
+    } else {
+        if constexpr (MIR)
+            gather_rev_walls<L, A>(phi_in, g, row, x0, lane, lam);
+        else
+            gather_rev<L, A>(phi_in, g, row, x0, lane, lam);
+        if constexpr (NU) gather<L, T, V, MIR>(Pn, g, row, x0, lane, f);
+    }
     EpsAcc<A> acc = 0;  // this lane's dL/deps terms
     bool range = false;
-    T f[L::Q][V];
-    if constexpr (NU) gather<L, T, V, MIR>(Pn, g, row, x0, lane, f);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         A l[L::Q];
@@ -837,14 +913,15 @@ template <class L, typename T> cudaError_t seed_t(lb_adj *a, const double *dLdu)
 template <class L, typename T, typename A, bool MIR> cudaError_t step_m(lb_adj *a, const void *Pn)
 {
     lb_ctx *c = a->ctx;
-    const unsigned nb = (unsigned)sweep_blocks(a->ag);
+    constexpr int TH = lbk::adj_threads<A>();
+    const unsigned nb = (unsigned)((a->ag.nseg + TH / 32 - 1) / (TH / 32));
     const A *in = (const A *)a->phi[a->pcur];
     A *out = (A *)a->phi[a->pcur ^ 1];
     if (a->want_nu)
-        lbk::adj_step_kernel<L, T, true, A, MIR><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
+        lbk::adj_step_kernel<L, T, true, A, MIR><<<nb, TH, 0, c->stream>>>(
             in, (const T *)Pn, out, a->ag, a->K, a->slot_step, a->dflag);
     else
-        lbk::adj_step_kernel<L, T, false, A, MIR><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
+        lbk::adj_step_kernel<L, T, false, A, MIR><<<nb, TH, 0, c->stream>>>(
             in, (const T *)Pn, out, a->ag, a->K, a->slot_step, a->dflag);
     return cudaGetLastError();
 }
