@@ -81,7 +81,7 @@ lb_status lb_batch_errors(lb_batch *b, const double *theta, const double *u, con
 
 /*
  * Autotuner: times `trial_steps` steps for each candidate (group byte budget
- * 48, 96, 128 MB or all instances in one group, x 128, 256 or 512 threads
+ * 48, 96, 128 MB or all instances in one group, x 64, 128, 256 or 512 threads
  * per block) on this batch's real sizes and keeps the fastest.  Must be
  * called before lb_batch_set_theta0 (it overwrites the state).  choice
  * (host, may be NULL) receives {budget_bytes, threads_per_block, groups,
@@ -93,7 +93,7 @@ lb_status lb_batch_autotune(lb_batch *b, int trial_steps, double *choice);
  * Set the schedule explicitly: budget_bytes <= 0 puts every instance in its
  * own group (one launch per instance per step), a budget above the total
  * state puts all instances in one group (one launch per step); threads is
- * 128, 256 or 512; use_graph = 0 launches every step directly instead of
+ * 64, 128, 256 or 512; use_graph = 0 launches every step directly instead of
  * replaying recorded graphs.  Keeps the state.
  */
 lb_status lb_batch_set_schedule(lb_batch *b, double budget_bytes, int threads, int use_graph);

@@ -579,7 +579,7 @@ lb_status lb_batch_autotune(lb_batch *b, int trial_steps, double *choice)
     // one instance per group is the naive baseline and never the fastest; it is
     // left out of the search (lb_batch_set_schedule can still select it)
     const double budgets[] = {48e6, 96e6, 128e6, 1e18};
-    const int threads[] = {128, 256, 512};
+    const int threads[] = {64, 128, 256, 512};
     double best = 1e300, best_b = b->budget;
     int best_t = b->threads;
     cudaEvent_t e0, e1;
@@ -626,7 +626,8 @@ lb_status lb_batch_autotune(lb_batch *b, int trial_steps, double *choice)
 
 lb_status lb_batch_set_schedule(lb_batch *b, double budget, int threads, int use_graph)
 {
-    if (!b || !(threads == 128 || threads == 256 || threads == 512) || !isfinite(budget)) return LB_EINVAL;
+    if (!b || !(threads == 64 || threads == 128 || threads == 256 || threads == 512) || !isfinite(budget))
+        return LB_EINVAL;
     cudaError_t e = cudaStreamSynchronize(b->stream);  // tables in use by queued launches
     if (e != cudaSuccess) return bcuda(b, e, "lb_batch_set_schedule");
     return build_schedule(b, budget, threads, use_graph != 0);

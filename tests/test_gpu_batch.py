@@ -40,7 +40,8 @@ def _single(j, prob, dx, dt, n, precision, theta_ref):
 
 
 @pytest.mark.parametrize("precision", ["fp32s", "fp64", "fx64"])
-@pytest.mark.parametrize("sched", [(96e6, 256, True), (0.0, 128, False), (40e3, 512, True), (1e18, 256, True)])
+@pytest.mark.parametrize("sched", [(96e6, 256, True), (0.0, 128, False), (40e3, 512, True), (1e18, 256, True),
+                                   (1e18, 64, True)])
 def test_batch_equals_single_instance_bitwise(precision, sched):
     probs, dxs, dts, th0, g0 = _setup()
     n = 37  # one recorded 32-step graph plus 5 direct launches, odd parity
@@ -79,7 +80,7 @@ def test_batch_autotune_and_errors():
     probs, dxs, dts, th0, g0 = _setup(3)
     b = lb.Batch(SIZES, NUS, dxs, dts, precision="fp32s", theta_ref=[1.5] * len(SIZES))
     choice = b.autotune(4)
-    assert choice["threads"] in (128, 256, 512) and choice["groups"] >= 1 and choice["us_per_step"] > 0
+    assert choice["threads"] in (64, 128, 256, 512) and choice["groups"] >= 1 and choice["us_per_step"] > 0
     b.set_theta0(torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda())
     n = 40
     b.step(n)
