@@ -257,7 +257,16 @@ __device__ __forceinline__ A adj_node(A *l, const T *fv, const AdjK &K)
         // f moments: theta = sum f, P_aa gains sigma theta_ref from the FP32
         // storage shift (w theta_ref has no J or P_ab part)
         A th, Paa[D], J[D], Pab[NP > 0 ? NP : 1];
-        if constexpr (std::is_same<A, float>::value && std::is_same<T, float>::value) {
+        if constexpr (std::is_same<T, double>::value) {  // FP64 states: scale 1, no shift
+            th = m.th;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                Paa[a] = m.Paa[a];
+                J[a] = m.J[a];
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p) Pab[p] = m.Pab[p];
+        } else if constexpr (std::is_same<A, float>::value && std::is_same<T, float>::value) {
             th = m.th + K.mshift_th_f;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
@@ -485,12 +494,13 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
     if (lane == 0) slot[seg] += acc;
 }
 
-// Threads per block of the reverse step: 128 for FP32 arithmetic, whose
-// early-issued gathers need 72 registers (at 256 threads a 512^2 step would
-// no longer fit one wave), else 256.
+// Threads per block of the reverse step: 128 for floating-point arithmetic
+// (FP32: its early-issued gathers need 72 registers, and at 256 threads a
+// 512^2 step would no longer fit one wave; FP64: at 92 registers 128-thread
+// blocks keep 20 warps per SM resident instead of 16), 256 for fixed point.
 template <typename A> __host__ __device__ constexpr int adj_threads()
 {
-    return std::is_same<A, float>::value ? 128 : kSweepThreads;
+    return std::is_same<A, long long>::value ? kSweepThreads : 128;
 }
 
 // One reverse step: phi_out = K^T lambda(phi_in); eps-term if NU.
