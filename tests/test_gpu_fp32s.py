@@ -43,7 +43,9 @@ def _run(d, N, nsteps, seed=21, theta_ref=1.5):
 
 CASES = [(1, (200,), 1), (1, (200,), 40), (2, (150, 70), 1), (2, (150, 70), 25), (2, (64, 64), 20),
          (2, (3, 130), 6), (3, (140, 20, 9), 1), (3, (140, 20, 9), 12), (3, (5, 4, 3), 5),
-         (4, (12, 7, 5, 4), 5)]
+         (4, (12, 7, 5, 4), 5),
+         # 4D rows with padding, of odd length, and filling whole warps
+         (4, (50, 3, 4, 3), 3), (4, (11, 5, 4, 3), 4), (4, (64, 3, 3, 3), 3)]
 
 
 @pytest.mark.parametrize("d,N,nsteps", CASES)
