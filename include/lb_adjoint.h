@@ -69,7 +69,13 @@ lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, dou
  */
 lb_status lb_adjoint_seed(lb_adj *a, const double *dL_du);
 
-/* Run `nsteps` reverse steps (the remaining count is T minus those done). */
+/*
+ * Run `nsteps` reverse steps (the remaining count is T minus those done).
+ * Whole checkpoint segments replay a recorded graph; the results do not
+ * depend on how the steps are split across calls.  LB_ESTATE if the
+ * context's walls were changed (lb_set_boundary) since lb_adjoint_forward:
+ * the checkpoints belong to the old geometry.
+ */
 lb_status lb_adjoint_step(lb_adj *a, int64_t nsteps);
 
 /*

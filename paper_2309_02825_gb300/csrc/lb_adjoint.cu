@@ -1201,6 +1201,8 @@ lb_status lb_adjoint_step(lb_adj *a, int64_t nsteps)
     if (!a || nsteps < 0) return LB_EINVAL;
     if (!a->seeded) return afail(a, LB_ESTATE, "lb_adjoint_step: call lb_adjoint_seed first");
     if (a->done + nsteps > a->T) return afail(a, LB_EINVAL, "lb_adjoint_step: more reverse steps than forward");
+    if (a->ctx->geom.mirror != a->ag.mirror)
+        return afail(a, LB_ESTATE, "lb_adjoint_step: the walls changed since lb_adjoint_forward");
     cudaError_t e;
     lb_ctx *c = a->ctx;
     const bool cap = stream_capturing(c->stream);

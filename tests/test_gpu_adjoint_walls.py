@@ -102,3 +102,26 @@ def test_wall_adjoint_fp32_shifted_tracks_fp64():
     g32, dnu32 = _gpu_gradient(d, N, mirror, nu, dx, dt, th0, ut, T, "fp32s")
     assert np.max(np.abs(g32 - g64)) <= 1e-3 * np.max(np.abs(g64))
     assert dnu32 == pytest.approx(dnu64, rel=1e-3)
+
+
+def test_wall_change_after_forward_is_refused():
+    """Checkpoints belong to the geometry of the forward pass: reverse steps
+    after lb_set_boundary report LB_ESTATE until a new forward."""
+    d, N, T = 2, (12, 10), 6
+    th0, ut, nu, dx, dt = _case(d, N, 5)
+    s = lb.Solver(d, N, nu, dx, dt, precision="fp64", theta_ref=1.5, boundary=["mirror", "periodic"])
+    a = lb.Adjoint(s, T, want_nu=True)
+    u = a.forward(torch.from_numpy(th0).cuda())
+    a.seed((u - torch.from_numpy(ut).cuda()).contiguous())
+    a.step(2)
+    lb.lb_set_boundary(s.ctx, ["periodic", "periodic"])
+    with pytest.raises(lb.LBError) as ei:
+        a.step(1)
+    assert ei.value.status == lb.LB_ESTATE
+    u = a.forward(torch.from_numpy(th0).cuda())  # a new forward on the new geometry
+    a.seed((u - torch.from_numpy(ut).cuda()).contiguous())
+    a.step(T)
+    g, dnu = a.result()
+    assert bool(torch.isfinite(g).all()) and np.isfinite(dnu)
+    a.close()
+    s.close()
