@@ -69,3 +69,20 @@ def test_oracle_adjoint_matches_dense_jacobian(d, N, T):
         du = ucoef * (dJ * th[None] - J * dth[None]) / (th[None] ** 2)
         dense[j] = np.sum(r * du)
     assert np.max(np.abs(g.ravel() - dense)) <= 1e-12 * np.max(np.abs(dense))
+
+
+@pytest.mark.parametrize("d,N,T", [(1, (16,), 12), (2, (8, 6), 8), (3, (5, 4, 4), 4)])
+def test_oracle_dnu_matches_fourth_order_differences(d, N, T):
+    """dL/dnu to about 1e-10: the loss is a smooth function of nu (eps enters
+    the relaxation rates and weights of Eq. (Bur-Sol) rationally), so the
+    five-point difference [L(-2h) - 8 L(-h) + 8 L(h) - L(2h)] / 12h has
+    truncation error O(h^4) and rounding error O(eps_mach / h); at h = 3e-4 nu
+    the two agree to 2e-13 .. 7e-11 on these cases.  A wrong eps-derivative
+    anywhere in the adjoint (collision, initialisation or recovery term) is
+    off by far more."""
+    th0, ut, nu, dx, dt = _case(d, N, T, 51 + d)
+    _, _, dnu = O.Model(d, N, nu, dx, dt).adjoint(th0, ut, T)
+    h = 3e-4 * nu
+    Lh = {k: O.Model(d, N, nu + k * h, dx, dt).loss(th0, ut, T) for k in (-2, -1, 1, 2)}
+    fd4 = (Lh[-2] - 8 * Lh[-1] + 8 * Lh[1] - Lh[2]) / (12 * h)
+    assert dnu == pytest.approx(fd4, rel=1e-9)
