@@ -69,7 +69,7 @@ def parse():
     p.add_argument("--accuracy", action="store_true",
                    help="print the error-vs-exact convergence table (1D, 2D up to 4096^2, 3D up to 256^3) and exit")
     p.add_argument("--accuracy-precisions", default="fp64,fx64,fp32s")
-    p.add_argument("--profile-batch", default=None, metavar="COUNT,STEPS",
+    p.add_argument("--profile-batch", default=None, metavar="COUNT,STEPS[,PREC]",
                    help="minimal command for ncu: COUNT batched 2D instances, STEPS steps, then exit")
     p.add_argument("--profile-adjoint", default=None, metavar="PREC,N,T",
                    help="minimal command for ncu: forward + seed + T reverse steps at N^2, then exit")
@@ -748,17 +748,21 @@ def run_4d(local, peaks):
 
 def run_profile_batch(local, spec):
     """Minimal, repeatable command for ncu: the first COUNT instances of the
-    batched workload (FP32s, flat schedule), STEPS steps."""
+    batched workload (PREC, default FP32s; flat schedule with the block size
+    the autotuner picks for that precision), STEPS steps."""
     import torch
     from paper_2309_02825_gb300 import lb
     torch.cuda.set_device(local)
-    count, steps = (int(v) for v in spec.split(","))
+    parts = spec.split(",")
+    count, steps = int(parts[0]), int(parts[1])
+    prec = parts[2] if len(parts) > 2 else "fp32s"
     cases = W.batched_2d(512, nsteps=2000)[:count]
     th0 = np.concatenate([c.problem.theta(c.N, c.dx).ravel() for c in cases])
     g0 = np.concatenate([np.ascontiguousarray(c.problem.grad(c.N, c.dx)).ravel() for c in cases])
+    kw = {"theta_ref": [1.5] * len(cases)} if prec == "fp32s" else {}
     b = lb.Batch([c.N for c in cases], [c.nu for c in cases], [c.dx for c in cases], [c.dt for c in cases],
-                 precision="fp32s", theta_ref=[1.5] * len(cases))
-    b.set_schedule(1e18, 128, False)
+                 precision=prec, **kw)
+    b.set_schedule(1e18, 64 if prec == "fx64" else 128, False)
     b.set_theta0(torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda())
     b.step(steps)
     torch.cuda.synchronize()
