@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
 
 // Threads per block of the reverse step: 128 for floating-point arithmetic
 // (FP32: its early-issued gathers need 72 registers, and at 256 threads a
-// 512^2 step would no longer fit one wave; FP64: at 92 registers 128-thread
+// 512^2 step would no longer fit one wave; FP64: at about 90 registers 128-thread
 // blocks keep 20 warps per SM resident instead of 16), 256 for fixed point.
 template <typename A> __host__ __device__ constexpr int adj_threads()
 {
