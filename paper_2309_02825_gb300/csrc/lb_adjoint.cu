@@ -329,7 +329,9 @@ __device__ __forceinline__ A adj_node(A *l, const T *fv, const AdjK &K)
 // K^T from exact integer channel sums and rounded 64x62-bit products; with
 // NU, lambda . (dK/deps) f from exact 128-bit dot products of the integer
 // channels with the state's integer moments, each converted to FP64 once (on
-// the integer pipes) and combined with the FP64 eps-derivatives.  Sets
+// the integer pipes; the int64 channel and moment values by the hardware
+// conversion, which keeps the FP64 and integer pipes in balance) and
+// combined with the FP64 eps-derivatives.  Sets
 // `range` when an output leaves |v| < 2^59 (the fields start below 2^56).
 template <class L, bool NU>
 __device__ __forceinline__ double adj_node_fx(long long *l, const long long *fv, const AdjK &K, bool &range)
@@ -363,8 +365,8 @@ __device__ __forceinline__ double adj_node_fx(long long *l, const long long *fv,
 #pragma unroll
         for (int p = 0; p < NP; ++p) S3 += (__int128)m.Pab[p] * P[p];
         const Coll<double> &kd = K.kdx;
-        const double lt = fma(kd.c0, i64_to_f64_rn(l0), fma(kd.cA, i64_to_f64_rn(sax), kd.wd * i64_to_f64_rn(sdg)));
-        eterm = fma(i64_to_f64_rn(m.th), lt,
+        const double lt = fma(kd.c0, (double)l0, fma(kd.cA, (double)sax, kd.wd * (double)sdg));
+        eterm = fma((double)m.th, lt,
                     fma(kd.k2, i128_to_f64_rn(S2), fma(kd.k1, i128_to_f64_rn(S1), kd.k3 * i128_to_f64_rn(S3))));
     }
     const long long Lt = mulfx(l0, K.c0k) + mulfx(sax, K.cAk) + mulfx(sdg, K.wdk);
@@ -394,8 +396,10 @@ __device__ __forceinline__ double adj_node_fx(long long *l, const long long *fv,
         l[B0 + 4 * p + 3] = Xm + W;  // (+1, -1)
     });
     constexpr long long kLim = 1ll << 59;  // next step's channel sums (<= 12 terms) stay below 2^63
+    // -kLim < v < kLim as one unsigned comparison of v + (kLim - 1)
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) range |= !(l[i] < kLim && l[i] > -kLim);
+    for (int i = 0; i < L::Q; ++i)
+        range |= (unsigned long long)l[i] + (unsigned long long)(kLim - 1) > (unsigned long long)(2 * kLim - 2);
     return eterm;
 }
 
