@@ -42,13 +42,17 @@ _CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle with gcc into ``oracle/_build/liborc.so``."""
+    """Compile the C oracle with gcc into ``oracle/_build/liborc.so``, with
+    OpenMP over the node loops when the compiler has it (the results do not
+    depend on it: see ``set_threads``)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + ".%d.tmp" % os.getpid()
-    subprocess.run(["gcc", *_CFLAGS, "-o", tmp, _SRC, "-lm"], check=True)
+    r = subprocess.run(["gcc", *_CFLAGS, "-fopenmp", "-o", tmp, _SRC, "-lm"], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(["gcc", *_CFLAGS, "-o", tmp, _SRC, "-lm"], check=True)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -86,12 +90,26 @@ def _load():
         lib.orc_recover.argtypes = [vp, dp, dp, dp, dp]
         lib.orc_total.argtypes = [vp, dp]
         lib.orc_total.restype = ctypes.c_double
-        lib.orc_adjoint.argtypes = [vp, dp, dp, ctypes.c_long, dp, dp]
+        lib.orc_adjoint.argtypes = [vp, dp, dp, dp, ctypes.c_long, ctypes.c_long, dp, dp]
         lib.orc_adjoint.restype = ctypes.c_double
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_get_threads.restype = ctypes.c_int
         lib.orc_loss.argtypes = [vp, dp, dp, ctypes.c_long]
         lib.orc_loss.restype = ctypes.c_double
         _lib = lib
         return lib
+
+
+def set_threads(n: int) -> None:
+    """Host threads for the oracle's node loops (OpenMP).  Each node is
+    computed as in a serial loop and sums over nodes are taken serially in
+    node order, so results are bit-identical for every thread count."""
+    _load().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    """Threads the oracle's node loops use (1 without OpenMP)."""
+    return int(_load().orc_get_threads())
 
 
 def _dp(a):
@@ -245,13 +263,18 @@ class Model:
         ut = _f64(utarget).reshape((self.d,) + self.shape)
         return float(self._lib.orc_loss(self._h, _dp(th), _dp(ut), int(T)))
 
-    def adjoint(self, theta0, utarget, T):
-        """(L, dL/dtheta0, dL/dnu) by the discrete adjoint (paper relaxation set)."""
+    def adjoint(self, theta0, utarget, T, theta_target=None, checkpoint=0):
+        """(L, dL/dtheta0, dL/dnu) by the discrete adjoint (paper relaxation set)
+        for L = 1/2 sum |u(T) - utarget|^2 [+ 1/2 sum (theta(T) - theta_target)^2].
+        ``checkpoint`` = 0 keeps every forward state; C > 0 keeps every C-th
+        and recomputes one segment at a time (same results, bit for bit)."""
         th = _f64(theta0).reshape(self.shape)
         ut = _f64(utarget).reshape((self.d,) + self.shape)
+        tt = None if theta_target is None else _f64(theta_target).reshape(self.shape)
         g = np.zeros(self.shape)
         de = ctypes.c_double()
-        L = self._lib.orc_adjoint(self._h, _dp(th), _dp(ut), int(T), _dp(g), ctypes.byref(de))
+        L = self._lib.orc_adjoint(self._h, _dp(th), _dp(ut), _dp(tt), int(T), int(checkpoint), _dp(g),
+                                  ctypes.byref(de))
         if not np.isfinite(L):
             raise MemoryError("oracle adjoint")
         p = self.params

@@ -22,6 +22,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXD 4
 #define ORC_MAXQ (1 + 2 * ORC_MAXD * ORC_MAXD)
@@ -31,6 +34,29 @@
 /* ------------------------------------------------------------------ */
 
 int orc_q(int d) { return 1 + 2 * d * d; }
+
+/*
+ * Host threads.  The node loops below are split across OpenMP threads when
+ * the library is built with OpenMP; each node's values are computed exactly
+ * as in the serial loop and every sum over nodes is taken serially in node
+ * order, so the results do not depend on the thread count.
+ */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /*
  * Discrete velocities in lattice units e_i = c_i / c, written to
@@ -313,8 +339,9 @@ static long coords_node(const orc_model *m, const long *x)
  */
 void orc_fd4_gradient(const orc_model *m, const double *theta, double *grad)
 {
-    long x[ORC_MAXD], y[ORC_MAXD];
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < m->nodes; ++n) {
+        long x[ORC_MAXD], y[ORC_MAXD];
         node_coords(m, n, x);
         for (int a = 0; a < m->d; ++a) {
             double acc = 0.0;
@@ -350,8 +377,9 @@ void orc_initialize(const orc_model *m, const double *theta0, const double *grad
         orc_fd4_gradient(m, theta0, gbuf);
         grad0 = gbuf;
     }
-    double g[ORC_MAXQ];
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < nodes; ++n) {
+        double g[ORC_MAXQ];
         for (int k = 0; k < q; ++k) {
             double cdotgrad = 0.0;
             for (int a = 0; a < d; ++a) cdotgrad += m->c * m->e[k * d + a] * grad0[a * nodes + n];
@@ -377,9 +405,10 @@ void orc_step(const orc_model *m, const double *f_in, double *f_out)
 {
     int q = m->q, d = m->d;
     long nodes = m->nodes;
-    long x[ORC_MAXD], y[ORC_MAXD];
-    double fl[ORC_MAXQ], fne[ORC_MAXQ];
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < nodes; ++n) {
+        long x[ORC_MAXD], y[ORC_MAXD];
+        double fl[ORC_MAXQ], fne[ORC_MAXQ];
         double theta = 0.0;
         for (int i = 0; i < q; ++i) {
             fl[i] = f_in[i * nodes + n];
@@ -424,6 +453,7 @@ void orc_recover(const orc_model *m, const double *f, double *theta, double *gra
 {
     int q = m->q, d = m->d;
     long nodes = m->nodes;
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < nodes; ++n) {
         double th = 0.0;
         for (int k = 0; k < q; ++k) th += f[k * nodes + n];
@@ -481,28 +511,63 @@ static void paper_set_deriv(int d, double eps, double *ds1, double *ds2x, double
     }
 }
 
-/* L and its gradients with respect to theta0 (nodes values) and eps.
- * Requires a model built with the paper's relaxation set.  Returns L, or
- * NAN on allocation failure. */
-double orc_adjoint(const orc_model *m, const double *theta0, const double *utarget, long T,
-                   double *dL_dtheta0, double *dL_deps)
+/*
+ * L and its gradients with respect to theta0 (nodes values) and eps, for
+ *   L = 1/2 sum_x sum_a (u_a(x,T) - utarget_a(x))^2
+ *       [+ 1/2 sum_x (theta(x,T) - ttarget(x))^2   when ttarget != NULL].
+ * Requires a model built with the paper's relaxation set.
+ * C = 0 keeps every forward state f_0..f_T in memory.  C > 0 keeps f_n only
+ * at n = 0, C, 2C, ... and recomputes the states of one segment of C steps
+ * at a time, by the same steps, as the reverse pass reaches it; the states,
+ * and so the results, are the same bit for bit.
+ * Every sum over nodes is taken serially in node order (per-node terms are
+ * formed first, in parallel), so the results do not depend on the thread
+ * count.  Returns L, or NAN on allocation failure or invalid C.
+ */
+double orc_adjoint(const orc_model *m, const double *theta0, const double *utarget, const double *ttarget,
+                   long T, long C, double *dL_dtheta0, double *dL_deps)
 {
     int q = m->q, d = m->d;
     long nodes = m->nodes;
     size_t fs = (size_t)q * (size_t)nodes;
-    double *F = (double *)malloc(sizeof(double) * fs * (size_t)(T + 1));
+    if (T < 0 || C < 0 || C > (T > 0 ? T : 1)) return NAN;
+    /* kept states: all T + 1 (C = 0), or ceil(T/C) checkpoints, f_T and one segment */
+    long nck = (C == 0) ? T + 1 : (T + C - 1) / C;
+    size_t kept = (C == 0) ? (size_t)(T + 1) : (size_t)nck + 1 + (size_t)C;
+    double *F = (double *)malloc(sizeof(double) * fs * kept);
     double *grad = (double *)malloc(sizeof(double) * d * nodes);
     double *phi = (double *)malloc(sizeof(double) * fs);
     double *phin = (double *)malloc(sizeof(double) * fs);
     double *h = (double *)malloc(sizeof(double) * d * nodes);
-    if (!F || !grad || !phi || !phin || !h) {
-        free(F); free(grad); free(phi); free(phin); free(h);
+    double *terms = (double *)malloc(sizeof(double) * (size_t)nodes * (size_t)(q > d + 1 ? q : d + 1) * 2);
+    if (!F || !grad || !phi || !phin || !h || !terms) {
+        free(F); free(grad); free(phi); free(phin); free(h); free(terms);
         return NAN;
     }
-    /* forward, keeping every state */
+    /* forward.  C = 0: F holds f_n at F + fs n.  C > 0: checkpoint k (f_kC)
+     * at F + fs k, f_T at F + fs nck, the segment buffer after it. */
     orc_fd4_gradient(m, theta0, grad);
     orc_initialize(m, theta0, grad, F);
-    for (long n = 0; n < T; ++n) orc_step(m, F + fs * n, F + fs * (n + 1));
+    double *fT;
+    double *seg = NULL;
+    if (C == 0) {
+        for (long n = 0; n < T; ++n) orc_step(m, F + fs * n, F + fs * (n + 1));
+        fT = F + fs * T;
+    } else {
+        fT = F + fs * nck;
+        seg = fT + fs;
+        memcpy(seg, F, sizeof(double) * fs);
+        double *cur = seg, *nxt = seg + fs; /* two scratch states of the segment buffer (C >= 1: room for 1) */
+        if (C == 1) nxt = fT;               /* C = 1: every state is a checkpoint; use f_T's slot as scratch */
+        for (long n = 0; n < T; ++n) {
+            orc_step(m, cur, nxt);
+            double *t = cur;
+            cur = nxt;
+            nxt = t;
+            if ((n + 1) % C == 0 && (n + 1) / C < nck) memcpy(F + fs * ((n + 1) / C), cur, sizeof(double) * fs);
+        }
+        if (cur != fT) memcpy(fT, cur, sizeof(double) * fs);
+    }
 
     /* derivatives of the parameters with respect to eps */
     double ds1, ds2x, ds22, dw1, dwd;
@@ -542,10 +607,14 @@ double orc_adjoint(const orc_model *m, const double *theta0, const double *utarg
             dK[i * q + j] = dk;
         }
 
-    /* recovery at T and the seed phi_T = dL/df_T */
+    /* recovery at T and the seed phi_T = dL/df_T.  Per node x: the loss
+     * terms of u_0..u_{d-1} (and theta) in terms[2(d+1)x + ...], their eps
+     * terms after them; summed below in node order. */
     double L = 0.0, deps = 0.0;
-    const double *fT = F + fs * T;
+    const int ns = d + 1;
+#pragma omp parallel for schedule(static)
     for (long x = 0; x < nodes; ++x) {
+        double *tl = terms + (size_t)2 * ns * x, *te = tl + ns;
         double th = 0.0;
         for (int k = 0; k < q; ++k) th += fT[k * nodes + x];
         for (int k = 0; k < q; ++k) phi[k * nodes + x] = 0.0;
@@ -558,22 +627,52 @@ double orc_adjoint(const orc_model *m, const double *theta0, const double *utarg
             }
             double u = (2.0 - m->s1) * j / th;
             double r = u - utarget[a * nodes + x];
-            L += 0.5 * r * r;
+            tl[a] = 0.5 * r * r;
             for (int k = 0; k < q; ++k) {
                 double djdf = m->c * m->e[k * d + a] - sew;
                 phi[k * nodes + x] += r * (2.0 - m->s1) * (djdf * th - j) / (th * th);
             }
             /* explicit eps dependence of u: through s1 and through w in f^ne */
-            deps += r * (-ds1 * j / th + (2.0 - m->s1) * (-dsew * th) / th);
+            te[a] = r * (-ds1 * j / th + (2.0 - m->s1) * (-dsew * th) / th);
         }
+        if (ttarget) {
+            /* theta = sum_k f_k: d theta / d f_k = 1, no explicit eps dependence */
+            double rt = th - ttarget[x];
+            tl[d] = 0.5 * rt * rt;
+            for (int k = 0; k < q; ++k) phi[k * nodes + x] += rt;
+        }
+    }
+    for (long x = 0; x < nodes; ++x) {
+        const double *tl = terms + (size_t)2 * ns * x, *te = tl + ns;
+        for (int a = 0; a < d; ++a) {
+            L += tl[a];
+            deps += te[a];
+        }
+        if (ttarget) L += tl[d];
     }
 
     /* reverse steps: f_{n+1}(x + e_i)_i = (K f_n(x))_i */
-    long xc[ORC_MAXD], yc[ORC_MAXD];
-    double mu[ORC_MAXQ];
+    long curseg = -1;
     for (long n = T - 1; n >= 0; --n) {
-        const double *fn = F + fs * n;
+        const double *fn;
+        if (C == 0) {
+            fn = F + fs * n;
+        } else {
+            long k = n / C;
+            if (k != curseg) {
+                /* recompute the states kC .. min(kC + C, T) - 1 from checkpoint k */
+                long len = (k + 1) * C <= T ? C : T - k * C;
+                memcpy(seg, F + fs * k, sizeof(double) * fs);
+                for (long j = 1; j < len; ++j) orc_step(m, seg + fs * (j - 1), seg + fs * j);
+                curseg = k;
+            }
+            fn = seg + fs * (n - k * C);
+        }
+#pragma omp parallel for schedule(static)
         for (long x = 0; x < nodes; ++x) {
+            long xc[ORC_MAXD], yc[ORC_MAXD];
+            double mu[ORC_MAXQ];
+            double *tx = terms + (size_t)q * x;
             node_coords(m, x, xc);
             for (int i = 0; i < q; ++i) {
                 for (int a = 0; a < d; ++a) yc[a] = xc[a] + m->e[i * d + a];
@@ -587,16 +686,19 @@ double orc_adjoint(const orc_model *m, const double *theta0, const double *utarg
             for (int i = 0; i < q; ++i) {
                 double s = 0.0;
                 for (int j = 0; j < q; ++j) s += dK[i * q + j] * fn[j * nodes + x];
-                deps += mu[i] * s;
+                tx[i] = mu[i] * s;
             }
         }
+        for (size_t k = 0; k < fs; ++k) deps += terms[k];
         double *t = phi;
         phi = phin;
         phin = t;
     }
 
     /* initialisation: f_0 = w theta0 - dt Cinv (w o (c e . g)), g = G theta0 */
+#pragma omp parallel for schedule(static)
     for (long x = 0; x < nodes; ++x) {
+        double *tx = terms + (size_t)q * x;
         double s = 0.0;
         for (int i = 0; i < q; ++i) s += m->w[i] * phi[i * nodes + x];
         dL_dtheta0[x] = s;
@@ -617,13 +719,16 @@ double orc_adjoint(const orc_model *m, const double *theta0, const double *utarg
                 for (int a = 0; a < d; ++a) cg += m->c * m->e[k * d + a] * grad[a * nodes + x];
                 v -= m->dt * (dCinv[i * q + k] * m->w[k] + m->Cinv[i * q + k] * dw[k]) * cg;
             }
-            deps += phi[i * nodes + x] * v;
+            tx[i] = phi[i * nodes + x] * v;
         }
     }
+    for (size_t k = 0; k < fs; ++k) deps += terms[k];
     /* transpose of the fourth-order difference: (G^T h)(x) = sum_k cof_k h(x - off_k e_a) / (12 dx) */
     static const int off[4] = {2, 1, -1, -2};
     static const double cof[4] = {-1.0, 8.0, -8.0, 1.0};
+#pragma omp parallel for schedule(static)
     for (long x = 0; x < nodes; ++x) {
+        long xc[ORC_MAXD], yc[ORC_MAXD];
         node_coords(m, x, xc);
         double s = 0.0;
         for (int a = 0; a < d; ++a)
@@ -635,7 +740,7 @@ double orc_adjoint(const orc_model *m, const double *theta0, const double *utarg
         dL_dtheta0[x] += s / (12.0 * m->dx);
     }
     *dL_deps = deps;
-    free(F); free(grad); free(phi); free(phin); free(h);
+    free(F); free(grad); free(phi); free(phin); free(h); free(terms);
     return L;
 }
 

@@ -86,3 +86,86 @@ def test_oracle_dnu_matches_fourth_order_differences(d, N, T):
     Lh = {k: O.Model(d, N, nu + k * h, dx, dt).loss(th0, ut, T) for k in (-2, -1, 1, 2)}
     fd4 = (Lh[-2] - 8 * Lh[-1] + 8 * Lh[1] - Lh[2]) / (12 * h)
     assert dnu == pytest.approx(fd4, rel=1e-9)
+
+
+def _loss_with_theta(m, th0, ut, tt, T):
+    """L = 1/2 |u(T) - ut|^2 + 1/2 |theta(T) - tt|^2 from plain oracle runs
+    (initialisation with the FD4 gradient, T steps, recovery)."""
+    th, _, u = m.recover(m.run(m.initialize(th0), T))
+    return 0.5 * float(np.sum((u - ut) ** 2)) + 0.5 * float(np.sum((th - tt) ** 2))
+
+
+@pytest.mark.parametrize("d,N,T", [(1, (6,), 7), (2, (5, 4), 4), (3, (4, 3, 3), 3)])
+def test_oracle_theta_misfit_term_matches_dense_jacobian(d, N, T):
+    """The optional theta term of the loss: theta = sum_k f_k, so it seeds
+    dL/df_k with theta - theta_target at every k.  Checked exactly against the
+    dense Jacobian of the linear map theta0 -> f_T, and dL/dnu (theta has no
+    explicit eps dependence) against a five-point difference in nu."""
+    th0, ut, nu, dx, dt = _case(d, N, T, 61 + d)
+    rng = np.random.default_rng(7 + d)
+    tt = th0 + 0.01 * rng.standard_normal(th0.shape)
+    m = O.Model(d, N, nu, dx, dt)
+    L, g, dnu = m.adjoint(th0, ut, T, theta_target=tt)
+    assert L == pytest.approx(_loss_with_theta(m, th0, ut, tt, T), rel=1e-13)
+    e = m.matrices()["e"]
+    p = m.params
+    ucoef = (2.0 - p["s1"]) * p["c"]
+
+    def moments(f):
+        return f.sum(axis=0), np.stack([np.tensordot(e[:, a], f, axes=(0, 0)) for a in range(d)])
+
+    th, J = moments(m.run(m.initialize(th0), T))
+    r = ucoef * J / th[None] - ut
+    rt = th - tt
+    dense = np.zeros(th0.size)
+    for j in range(th0.size):
+        ej = np.zeros(th0.size)
+        ej[j] = 1.0
+        dth, dJ = moments(m.run(m.initialize(ej.reshape(th0.shape)), T))
+        du = ucoef * (dJ * th[None] - J * dth[None]) / (th[None] ** 2)
+        dense[j] = np.sum(r * du) + np.sum(rt * dth)
+    assert np.max(np.abs(g.ravel() - dense)) <= 1e-12 * np.max(np.abs(dense))
+    # the theta term is not negligible here: dropping it moves the gradient by O(1)
+    _, g_u, _ = m.adjoint(th0, ut, T)
+    assert np.max(np.abs(g - g_u)) > 1e-3 * np.max(np.abs(dense))
+    h = 3e-4 * nu
+    Lh = {k: _loss_with_theta(O.Model(d, N, nu + k * h, dx, dt), th0, ut, tt, T) for k in (-2, -1, 1, 2)}
+    assert dnu == pytest.approx((Lh[-2] - 8 * Lh[-1] + 8 * Lh[1] - Lh[2]) / (12 * h), rel=1e-9)
+
+
+@pytest.mark.parametrize("d,N,T", [(1, (24,), 20), (2, (10, 8), 13), (3, (6, 5, 4), 7)])
+def test_oracle_checkpointed_adjoint_is_bit_identical(d, N, T):
+    """Keeping every C-th forward state and recomputing one segment at a time
+    replays the same steps, so the loss and both gradients equal those of the
+    run that keeps every state, bit for bit (C = 1, T, and C not dividing T)."""
+    th0, ut, nu, dx, dt = _case(d, N, T, 71 + d)
+    tt = th0 * 1.001
+    m = O.Model(d, N, nu, dx, dt)
+    for theta_target in (None, tt):
+        ref = m.adjoint(th0, ut, T, theta_target=theta_target, checkpoint=0)
+        for C in (1, 2, 3, 5, T):
+            L, g, dnu = m.adjoint(th0, ut, T, theta_target=theta_target, checkpoint=C)
+            assert L == ref[0] and np.array_equal(g, ref[1]) and dnu == ref[2], C
+
+
+def test_oracle_results_do_not_depend_on_threads():
+    """Node loops run on OpenMP threads; each node is computed as in a serial
+    loop and sums over nodes are serial, so 1 and 4 threads agree bit for bit."""
+    d, N, T = 2, (31, 20), 9
+    th0, ut, nu, dx, dt = _case(d, N, T, 81)
+    m = O.Model(d, N, nu, dx, dt)
+    out = []
+    before = O.threads()
+    try:
+        for n in (1, 4):
+            O.set_threads(n)
+            f0 = m.initialize(th0)
+            f = m.run(f0, T)
+            out.append((f0, f, m.recover(f), m.fd4_gradient(th0), m.adjoint(th0, ut, T, checkpoint=3)))
+    finally:
+        O.set_threads(before)
+    a, b = out
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[3], b[3])
+    for x, y in zip(a[2], b[2]):
+        assert np.array_equal(x, y)
+    assert a[4][0] == b[4][0] and np.array_equal(a[4][1], b[4][1]) and a[4][2] == b[4][2]
