@@ -512,6 +512,27 @@ static void paper_set_deriv(int d, double eps, double *ds1, double *ds2x, double
 }
 
 /*
+ * Compensated (Neumaier) summation: the running sum plus a correction that
+ * collects the low-order bits each addition drops, so the error of a sum of
+ * n terms stays near one rounding of the result instead of growing with n.
+ * dL/deps sums T * nodes * q terms of both signs (about 5e9 at 512^2,
+ * T = 2000), far too many for a plain running sum to hold 1e-12.
+ */
+typedef struct {
+    double s, c;
+} orc_ksum;
+static void ksum_add(orc_ksum *k, double x)
+{
+    double t = k->s + x;
+    if (fabs(k->s) >= fabs(x))
+        k->c += (k->s - t) + x;
+    else
+        k->c += (x - t) + k->s;
+    k->s = t;
+}
+static double ksum_value(const orc_ksum *k) { return k->s + k->c; }
+
+/*
  * L and its gradients with respect to theta0 (nodes values) and eps, for
  *   L = 1/2 sum_x sum_a (u_a(x,T) - utarget_a(x))^2
  *       [+ 1/2 sum_x (theta(x,T) - ttarget(x))^2   when ttarget != NULL].
@@ -522,7 +543,8 @@ static void paper_set_deriv(int d, double eps, double *ds1, double *ds2x, double
  * and so the results, are the same bit for bit.
  * Every sum over nodes is taken serially in node order (per-node terms are
  * formed first, in parallel), so the results do not depend on the thread
- * count.  Returns L, or NAN on allocation failure or invalid C.
+ * count; L and dL/deps are compensated sums (orc_ksum).  Returns L, or NAN on
+ * allocation failure or invalid C.
  */
 double orc_adjoint(const orc_model *m, const double *theta0, const double *utarget, const double *ttarget,
                    long T, long C, double *dL_dtheta0, double *dL_deps)
@@ -610,7 +632,7 @@ double orc_adjoint(const orc_model *m, const double *theta0, const double *utarg
     /* recovery at T and the seed phi_T = dL/df_T.  Per node x: the loss
      * terms of u_0..u_{d-1} (and theta) in terms[2(d+1)x + ...], their eps
      * terms after them; summed below in node order. */
-    double L = 0.0, deps = 0.0;
+    orc_ksum L = {0.0, 0.0}, deps = {0.0, 0.0};
     const int ns = d + 1;
 #pragma omp parallel for schedule(static)
     for (long x = 0; x < nodes; ++x) {
@@ -645,10 +667,10 @@ double orc_adjoint(const orc_model *m, const double *theta0, const double *utarg
     for (long x = 0; x < nodes; ++x) {
         const double *tl = terms + (size_t)2 * ns * x, *te = tl + ns;
         for (int a = 0; a < d; ++a) {
-            L += tl[a];
-            deps += te[a];
+            ksum_add(&L, tl[a]);
+            ksum_add(&deps, te[a]);
         }
-        if (ttarget) L += tl[d];
+        if (ttarget) ksum_add(&L, tl[d]);
     }
 
     /* reverse steps: f_{n+1}(x + e_i)_i = (K f_n(x))_i */
@@ -689,7 +711,7 @@ double orc_adjoint(const orc_model *m, const double *theta0, const double *utarg
                 tx[i] = mu[i] * s;
             }
         }
-        for (size_t k = 0; k < fs; ++k) deps += terms[k];
+        for (size_t k = 0; k < fs; ++k) ksum_add(&deps, terms[k]);
         double *t = phi;
         phi = phin;
         phin = t;
@@ -722,7 +744,7 @@ double orc_adjoint(const orc_model *m, const double *theta0, const double *utarg
             tx[i] = phi[i * nodes + x] * v;
         }
     }
-    for (size_t k = 0; k < fs; ++k) deps += terms[k];
+    for (size_t k = 0; k < fs; ++k) ksum_add(&deps, terms[k]);
     /* transpose of the fourth-order difference: (G^T h)(x) = sum_k cof_k h(x - off_k e_a) / (12 dx) */
     static const int off[4] = {2, 1, -1, -2};
     static const double cof[4] = {-1.0, 8.0, -8.0, 1.0};
@@ -739,9 +761,9 @@ double orc_adjoint(const orc_model *m, const double *theta0, const double *utarg
             }
         dL_dtheta0[x] += s / (12.0 * m->dx);
     }
-    *dL_deps = deps;
+    *dL_deps = ksum_value(&deps);
     free(F); free(grad); free(phi); free(phin); free(h); free(terms);
-    return L;
+    return ksum_value(&L);
 }
 
 /* L only (the same forward as orc_adjoint), for finite-difference checks. */
