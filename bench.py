@@ -103,6 +103,22 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
+def profile_fp64_inst(kernel_key):
+    """FP64 instructions per lattice update (thread-level, i.e. 32 x the warp
+    instructions ncu counts in sm__inst_executed_pipe_fp64.sum, per node) of a
+    sweep, from a committed ncu summary; valid only while the kernel source is
+    unchanged (same sha)."""
+    try:
+        sha = kernel_source_sha()
+        for line in open(os.path.join(ROOT, "profiles", "fp64_inst.txt")):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kernel_key and parts[1] == sha:
+                return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
 def profile_traffic(kernel_key):
     """DRAM bytes per launch from a committed ncu summary for this kernel,
     valid only while the kernel source is unchanged (same sha)."""
@@ -302,14 +318,20 @@ def run_ours(args, precision, world, rank, local, peaks, with_e2e, label_main):
         "gpu_launches": args.steps * (S + 6 + (2 if precision == "fx64" else 0)),
     }
     if precision == "fp64":
-        # The FP64 sweep is bound by the FP64 pipe: 34 FP64 instructions per
-        # D2Q9 update (closed-form collision), 2 per SM per clock on GB300.
-        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
-        peak_inst = 152 * 2 * sm_mhz * 1e6 / 1e9
-        ach_inst = 34 * nodes / (sweep_ms / 1e3) / 1e9
+        # The FP64 sweep is bound by the FP64 pipe: GB300 issues 2 FP64 lane
+        # operations per SM per clock (1/64 of FP32).  The instructions per
+        # update come from an ncu capture of this kernel source (null when the
+        # kernel changed since), the SM count from the device.
+        sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_inst = sms * 2 * sm_mhz * 1e6 / 1e9
+        ipl = profile_fp64_inst("sweep_d2q9_fp64")
+        ach_inst = None if ipl is None else ipl * nodes / (sweep_ms / 1e3) / 1e9
         res["roofline_fp64_pipe"] = {"bound": "alu", "achieved": ach_inst, "peak": peak_inst,
-                                     "unit": "G FP64 inst/s", "frac": ach_inst / peak_inst,
-                                     "fp64_inst_per_lu": 34}
+                                     "unit": "G FP64 lane-ops/s",
+                                     "frac": None if ach_inst is None else ach_inst / peak_inst,
+                                     "fp64_inst_per_lu": ipl, "sms": sms, "sm_mhz": sm_mhz,
+                                     "fp64_inst_source": "profiles/fp64_inst.txt (ncu sm__inst_executed_pipe_fp64)"}
 
     if with_e2e:
         res["e2e"] = run_e2e(args, s, case, th0_h, g0_h, ex_t_h, ex_u_h, stream, world)
@@ -473,8 +495,8 @@ def run_batched(local):
 def run_adjoint(local, precision="fp64"):
     """Adjoint cost at 512^2, T = 2000, sqrt(T) checkpoints: forward with
     checkpoints, reverse pass with segment recompute, per-step cost against a
-    plain forward sweep, and central-difference checks of dL/dtheta0 along two
-    random directions and of dL/dnu."""
+    plain forward sweep, and central-difference checks of dL/dtheta0 along 16
+    seeded random directions and of dL/dnu (FP64 and FX64)."""
     import torch
     from paper_2309_02825_gb300 import lb
 
@@ -507,15 +529,19 @@ def run_adjoint(local, precision="fp64"):
         s.close()
         return L, g, dnu, info
 
+    ls = lb.Solver(d, N, case.nu, case.dx, case.dt, precision=precision, stream=stream)
+    u_buf = torch.empty((d,) + tuple(reversed(N)), dtype=torch.float64, device="cuda")
+
     def loss(nu, th):
-        s = lb.Solver(d, N, nu, case.dx, case.dt, precision=precision, stream=stream)
-        a = lb.Adjoint(s, T, want_nu=False)
+        """The forward map the adjoint differentiates (theta0 with its FD4
+        gradient, T sweeps, u), on one reused context."""
         with torch.cuda.stream(stream):
-            u = a.forward(th)
-            r = u - ut
+            ls.set_viscosity(nu)
+            ls.set_theta0(th.contiguous())
+            ls.step(T)
+            ls.macros(u=u_buf, want=("u",))
+            r = u_buf - ut
             L = 0.5 * float((r * r).sum())
-        a.close()
-        s.close()
         return L
 
     grad(case.nu, th0)  # warm-up
@@ -534,15 +560,20 @@ def run_adjoint(local, precision="fp64"):
     torch.cuda.synchronize()
     t_sweep = ev[3].elapsed_time(ev[4]) / 1e3 / T
     s.close()
+    # central differences on 16 seeded random directions (FP64 and FX64; the
+    # FP32s forward map is only float-accurate, too coarse for a difference)
     rng = np.random.default_rng(2314)
     checks = []
-    for _ in range(2 if precision == "fp64" else 0):
-        v = torch.from_numpy(rng.normal(size=tuple(th0.shape))).cuda()
-        h = 1e-5
-        fd = (loss(case.nu, th0 + h * v) - loss(case.nu, th0 - h * v)) / (2 * h)
-        checks.append(abs(float((g * v).sum()) / fd - 1.0))
-    hn = 1e-6 * case.nu
-    fd_nu = ((loss(case.nu + hn, th0) - loss(case.nu - hn, th0)) / (2 * hn)) if precision == "fp64" else float("nan")
+    fd_nu = float("nan")
+    if precision in ("fp64", "fx64"):
+        for _ in range(16):
+            v = torch.from_numpy(rng.normal(size=tuple(th0.shape))).cuda()
+            h = 1e-5
+            fd = (loss(case.nu, th0 + h * v) - loss(case.nu, th0 - h * v)) / (2 * h)
+            checks.append(abs(float((g * v).sum()) / fd - 1.0))
+        hn = 1e-6 * case.nu
+        fd_nu = (loss(case.nu + hn, th0) - loss(case.nu - hn, th0)) / (2 * hn)
+    ls.close()
     return {
         "workload": "2D D2Q9 512^2, nu=0.02, eps=0.2048, T=2000, L=0.5||u(T)-u_target||^2, %s, checkpoint every %d "
                     "steps (%d checkpoints)" % (precision, info["checkpoint"], info["checkpoints"]),
@@ -854,33 +885,44 @@ def run_accuracy(local, precisions=("fp64", "fx64", "fp32s")):
 # The oracle (CPU baseline / reference arm).
 # ---------------------------------------------------------------------------
 
-def time_oracle(N, sweeps):
+def time_oracle(N, sweeps, threads):
     import oracle as O
+    O.set_threads(threads)
     case = W.sine_2d(N)
     m = O.Model(case.d, case.N, case.nu, case.dx, case.dt)
     f = m.initialize(case.problem.theta(case.N, case.dx), case.problem.grad(case.N, case.dx))
     t0 = time.perf_counter()
     f = m.run(f, sweeps)
     el = time.perf_counter() - t0
-    return case.nodes * sweeps / el / 1e6, el
+    return case.nodes * sweeps / el / 1e6, el, O.threads()
 
 
 def cpu_baseline(args):
-    # about 1.5 s per 4096^2 sweep on one Grace core: the work of 8 such sweeps is a 10-15 s sample
-    sweeps = max(8, int(round(8 * (4096.0 / max(args.N, 1)) ** 2)))
-    v, el = time_oracle(args.N, sweeps)
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d sweeps of the %d^2 D2Q9 FP64 oracle (%.1f s, single thread)" % (sweeps, args.N, el)}
+    """The FP64 oracle (OpenMP over nodes; bit-identical for any thread count)
+    on every host core, and on one core, each on a bounded sample of the
+    benchmark's sweeps (about 10 s of CPU work each)."""
+    cores = os.cpu_count() or 1
+    # one Grace core: about 1.5 s per 4096^2 sweep; all cores: about 10x faster
+    s1 = max(8, int(round(8 * (4096.0 / max(args.N, 1)) ** 2)))
+    v1, el1, _ = time_oracle(args.N, s1, 1)
+    sn = max(8, int(round(10.0 / max(el1 / s1 / min(cores, 12), 1e-6))))
+    vn, eln, used = time_oracle(args.N, sn, cores)
+    return {"value": vn, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": "%d sweeps of the %d^2 D2Q9 FP64 oracle (%.1f s, %d threads)" % (sn, args.N, eln, used),
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": "%d sweeps of the %d^2 D2Q9 FP64 oracle (%.1f s, 1 thread)" % (s1, args.N, el1)}}
 
 
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle as it stands, one bounded step per
     benchmark step (initialisation + 1 sweep + recovery of the 2D sine
-    workload), on the host cores; rank 0 only."""
+    workload), on every host core (OpenMP over nodes); rank 0 only."""
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return 0
     import oracle as O
+    O.set_threads(os.cpu_count() or 1)
+    cores = O.threads()
     case = W.sine_2d(args.N)
     th0 = case.problem.theta(case.N, case.dx)
     g0 = case.problem.grad(case.N, case.dx)
@@ -906,8 +948,9 @@ def run_reference(args):
         "config": {"workload": "2D D2Q9 periodic %d^2 sine, nu=0.02, eps=0.2048; reference step = oracle "
                    "initialisation + 1 sweep + recovery" % args.N, "precision": "fp64",
                    "l2_flush": "inputs larger than L2"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d steps of (init + 1 sweep + recovery) at %d^2, single thread" % (args.steps, args.N)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d steps of (init + 1 sweep + recovery) at %d^2, %d threads" % (
+                             args.steps, args.N, cores)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -960,7 +1003,8 @@ def main():
             a = run_adjoint(local, prec)
             adjoint[prec] = {k: a[k] for k in ("forward_with_checkpoints_s", "reverse_s", "plain_sweep_us",
                                                "reverse_step_us", "adjoint_step_cost_vs_forward_step",
-                                               "gradient_total_cost_vs_forward", "loss", "dL_dnu")}
+                                               "gradient_total_cost_vs_forward", "loss", "dL_dnu",
+                                               "fd_rel_err_theta0_dirs", "fd_rel_err_nu")}
             adjoint[prec]["dL_dnu_rel_diff_vs_fp64"] = abs(a["dL_dnu"] / adjoint["dL_dnu"] - 1.0)
     sweeps3d = None
     if not args.no_3d:

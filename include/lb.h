@@ -140,6 +140,19 @@ typedef enum {
  */
 lb_status lb_set_boundary(lb_ctx *ctx, const int *kind);
 
+/*
+ * Change the viscosity nu of a context in place (eps = nu dt / dx^2; dx and
+ * dt are kept).  With the paper's relaxation set the rates and weights are
+ * re-derived from Eq. (Bur-Sol) at the new eps; a caller's set is kept as
+ * given.  The stored state is kept (the next lb_step continues from it with
+ * the new collision), nothing is allocated, and recorded sweeps are dropped
+ * after synchronising the stream.  An adjoint workspace whose forward pass
+ * predates the change refuses reverse steps (LB_ESTATE) until
+ * lb_adjoint_forward runs again.
+ * Errors: LB_EINVAL (nu not finite and > 0), LB_ECUDA.
+ */
+lb_status lb_set_viscosity(lb_ctx *ctx, double nu);
+
 /* The boundary kind of each axis, written to kind[0..d-1] (host). */
 lb_status lb_get_boundary(const lb_ctx *ctx, int *kind);
 
@@ -164,8 +177,10 @@ lb_status lb_set_theta0(lb_ctx *ctx, const double *theta0, const double *grad_th
  * Advance nsteps >= 0 time steps of Eq. (distribution-f): at every node the
  * pre-collision f is pulled from the neighbours (streaming), relaxed in
  * moment space (m* = m - S (m - m^eq), m^eq = M w theta) and stored.
- * Asynchronous.  Errors: LB_EINVAL (nsteps < 0), LB_ESTATE (no
- * lb_set_theta0 yet), LB_ECUDA.
+ * Asynchronous.  For LB_FX64 every stored value is checked against
+ * |f| < 2^61 (reported by lb_macros, lb_sum_theta or lb_check).
+ * Errors: LB_EINVAL (nsteps < 0), LB_ESTATE (no
+ * lb_set_theta0 yet, or a reported timeout or range overflow since), LB_ECUDA.
  */
 lb_status lb_step(lb_ctx *ctx, int64_t nsteps);
 
@@ -182,17 +197,35 @@ lb_status lb_get_step(const lb_ctx *ctx, int64_t *nsteps);
  * stages its row segment of every population, with the one-node x-halo, in
  * shared memory by bulk asynchronous copies (TMA) completing on an mbarrier.
  * Any output pointer may be NULL to skip it.  Device outputs: theta (nodes),
- * grad_theta and u (d*nodes).  Asynchronous; a node with theta <= 0 or
- * non-finite is recorded and reported by the next lb_reduce as LB_ENONPOS,
- * a staging wait that gave up (bounded at 1 s) as LB_ETIMEOUT.
- * Errors: LB_ESTATE, LB_ECUDA.
+ * grad_theta and u (d*nodes).  The call synchronises the stream and reports
+ * what the device saw since the last report: LB_ENONPOS for a node with
+ * theta <= 0 or non-finite, LB_ETIMEOUT for a staging wait that gave up
+ * (bounded at 1 s; its tile may be incomplete, so the outputs are not to be
+ * used and the context refuses lb_step / lb_macros until lb_set_theta0 or
+ * lb_load_state sets a state again), and for LB_FX64 LB_EINVAL when a sweep
+ * stored a value with |f| >= 2^61 (an unstable run: FP64 would overflow to
+ * non-finite values; the context is likewise left without a state).  While
+ * the stream is being captured into a CUDA graph the call only enqueues the
+ * kernel; the flags are then reported by lb_check, lb_sum_theta or lb_reduce.
+ * Errors: LB_ESTATE, LB_ENONPOS, LB_ETIMEOUT, LB_EINVAL, LB_ECUDA.
  */
 lb_status lb_macros(lb_ctx *ctx, double *theta, double *grad_theta, double *u);
 
 /*
+ * Synchronise the stream and report (then clear) the device-side flags of
+ * the work enqueued so far, as lb_macros does: LB_ENONPOS, LB_ETIMEOUT, or
+ * LB_EINVAL for a fixed-point range overflow of a sweep (LB_FX64).  LB_OK
+ * when none is set.  For callers that step without recovering, and after
+ * a captured graph ran.  Errors: as listed, LB_ECUDA.
+ */
+lb_status lb_check(lb_ctx *ctx);
+
+/*
  * Conserved total sum_x theta(x) = sum over nodes and populations of f,
  * accumulated in FP64 (exactly conserved up to rounding on a periodic grid).
- * out: host, 1 value.  Synchronises the stream.  Errors: LB_ESTATE, LB_ECUDA.
+ * out: host, 1 value.  Synchronises the stream.  For LB_FX64 it also reports
+ * (LB_EINVAL) a sweep that stored a value with |f| >= 2^61 since the last
+ * report.  Errors: LB_ESTATE, LB_EINVAL, LB_ECUDA.
  */
 lb_status lb_sum_theta(lb_ctx *ctx, double *out);
 
@@ -207,7 +240,8 @@ lb_status lb_sum_theta(lb_ctx *ctx, double *out);
  * and out[3V] = sum theta.  FP64 with a deterministic two-level reduction
  * (warp shuffles, then a fixed-order pass over per-block partials held in
  * the context's scratch area).  Synchronises the stream.
- * Errors: LB_EINVAL, LB_ENONPOS (a previous lb_macros saw theta <= 0), LB_ECUDA.
+ * Errors: LB_EINVAL, LB_ENONPOS (a previous lb_macros, run inside a stream
+ * capture, saw theta <= 0), LB_ETIMEOUT (likewise for a staging wait), LB_ECUDA.
  */
 lb_status lb_reduce(lb_ctx *ctx, const double *theta, const double *u,
                     const double *exact_theta, const double *exact_u, double *out);
@@ -228,9 +262,12 @@ lb_status lb_reduce(lb_ctx *ctx, const double *theta, const double *u,
  *   stream       a cudaStream_t (NULL = legacy default stream); asynchronous.
  * Scratch: a file-scope __device__ array of 131,200 bytes (1024 partial
  * rows of 16 doubles plus one row of raw sums) that every GPU loading this
- * library holds until the process exits.  The first call on a device looks
- * up that array's device address (cudaGetSymbolAddress) with the device
- * current; make that first call before any stream capture.  Each call
+ * library holds until the process exits.  Each call made outside a stream
+ * capture looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current, so an address from before a cudaDeviceReset is never
+ * reused; a call inside a capture uses the address of an earlier call on
+ * that device, so make a first call before any stream capture (and again
+ * after a cudaDeviceReset).  All pointers must be on the current device.  Each call
  * overwrites every row it reads, so nothing needs clearing between calls,
  * but all calls share the one array: calls that overlap on the GPU (other
  * streams, other host threads) race and must be ordered by the caller.

@@ -6,7 +6,7 @@
  * as the fourth-order central difference of theta0 (so the map depends on
  * theta0 alone), T steps of Eq. (distribution-f), and u(T) by
  * Eq. (ui-compute).  The paper has no adjoint; this computes exact
- * gradients of any loss L(u(T)) given dL/du:
+ * gradients of any loss L(u(T), theta(T)) given dL/du and dL/dtheta:
  *   dL/dtheta0 (one value per node) and dL/dnu (through eps = nu dt/dx^2 and
  *   the relaxation set of Theorem 2, Eq. (Bur-Sol); dx and dt fixed).
  * Reverse step: phi_n(x) = K^T [phi_{n+1}(x + e_i)_i]_i (reversed streaming,
@@ -64,10 +64,17 @@ lb_status lb_adjoint_destroy(lb_adj *a);
 lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, double *u);
 
 /*
- * Start the reverse pass from dL/du at T (device, d*nodes): seeds
- * phi_T = dL/df_T through Eq. (ui-compute).  Requires a completed forward.
+ * Start the reverse pass from the loss's derivatives at T: seeds
+ * phi_T = dL/df_T through Eq. (ui-compute) for u and through
+ * theta = sum_k f_k (Eq. (conseved-moment)) for theta.
+ *   dL_du      device, d*nodes (vector-field layout), or NULL if L does not
+ *              depend on u(T).
+ *   dL_dtheta  device, nodes, or NULL if L does not depend on theta(T).
+ * At least one must be given.  Requires a completed forward.
+ * Errors: LB_EINVAL (both NULL), LB_ESTATE (no forward, or the context was
+ * stepped since), LB_ECUDA.
  */
-lb_status lb_adjoint_seed(lb_adj *a, const double *dL_du);
+lb_status lb_adjoint_seed(lb_adj *a, const double *dL_du, const double *dL_dtheta);
 
 /*
  * Run `nsteps` reverse steps (the remaining count is T minus those done).

@@ -432,10 +432,13 @@ template <typename A> __device__ __forceinline__ A warp_sum(A v)
     return v;
 }
 
-// phi_T = dL/df_T through u_a = ucoef J_a / theta; eps-term of the recovery.
+// phi_T = dL/df_T through u_a = ucoef J_a / theta and, where dLdth is given,
+// theta = sum_k f_k (d theta / d f_k = 1); eps-term of the recovery (theta has
+// no explicit eps dependence).  dLdu or dLdth may be NULL (not both).
 template <class L, typename T, typename A, bool MIR = false>
 __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__restrict__ P, Geom g, AdjK K,
                                                                  const double *__restrict__ dLdu,
+                                                                 const double *__restrict__ dLdth,
                                                                  A *__restrict__ phi, double *__restrict__ slot)
 {
     constexpr int V = 2;
@@ -463,15 +466,18 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
                 if constexpr (e != 0) J[a] += e * fv;
             });
         });
-        double gu[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 0.0};
+        double gu[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 0.0}, gt = 0.0;
         if (x < g.N0) {
             const int64_t node = row * g.N0 + x;
+            if (dLdu) {
 #pragma unroll
-            for (int a = 0; a < L::D; ++a) {
-                gu[a] = dLdu[a * nodes + node];
-                u[a] = K.ucoef * J[a] / th;
-                acc += gu[a] * K.ducoef * J[a] / th;
+                for (int a = 0; a < L::D; ++a) {
+                    gu[a] = dLdu[a * nodes + node];
+                    u[a] = K.ucoef * J[a] / th;
+                    acc += gu[a] * K.ducoef * J[a] / th;
+                }
             }
+            if (dLdth) gt = dLdth[node];
         }
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
@@ -481,7 +487,7 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
                 constexpr int e = L::E[i][a];
                 s += gu[a] * ((double)e * K.ucoef - u[a]);
             });
-            out[i][v] = (x < g.N0) ? s / th : 0.0;
+            out[i][v] = (x < g.N0) ? s / th + gt : 0.0;
         });
     }
     if (x0 + V * lane < g.pitch) {  // lanes beyond the row only loaded
@@ -550,10 +556,15 @@ __global__ void __launch_bounds__(adj_threads<A>()) adj_step_kernel(const A *__r
             if constexpr (NU) fv[i] = f[i][v];
         }
         EpsAcc<A> e;
-        if constexpr (std::is_same<A, long long>::value)
-            e = adj_node_fx<L, NU>(l, fv, K, range);
-        else
+        if constexpr (std::is_same<A, long long>::value) {
+            // lanes past the row end hold values of the allocation's slack
+            // (never initialised): only the grid's own nodes may set the flag
+            bool r = false;
+            e = adj_node_fx<L, NU>(l, fv, K, r);
+            if (x0 + V * lane + v < g.N0) range |= r;
+        } else {
             e = adj_node<L, T, NU, A>(l, fv, K);
+        }
         if (NU && x0 + V * lane + v < g.N0) acc += e;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) lam[i][v] = l[i];
@@ -722,7 +733,8 @@ struct lb_adj {
     // reverse segment, C - 1 recompute sweeps then C reverse steps (valid for
     // the constants K and walls they were recorded with).
     cudaGraphExec_t fgraph[2] = {nullptr, nullptr};
-    unsigned fmirror[2] = {0u, 0u};
+    uint64_t fgen[2] = {0, 0};  // the context's generation (walls, viscosity) each was recorded in
+    uint64_t fwd_gen = 0;       // the context's generation at the last forward pass
     cudaGraphExec_t rgraph[2] = {nullptr, nullptr};
     lbk::AdjK rK[2]{};
     unsigned rmirror[2] = {0u, 0u};
@@ -883,7 +895,7 @@ void set_fx_scale(lb_adj *a, int G)
              ldexp(K.kd.c0, sh), ldexp(K.kd.cA, sh), ldexp(K.kd.wd, sh)};
 }
 
-template <class L, typename T> cudaError_t seed_t(lb_adj *a, const double *dLdu)
+template <class L, typename T> cudaError_t seed_t(lb_adj *a, const double *dLdu, const double *dLdth)
 {
     lb_ctx *c = a->ctx;
     const unsigned nb = (unsigned)sweep_blocks(a->ag);
@@ -894,10 +906,10 @@ template <class L, typename T> cudaError_t seed_t(lb_adj *a, const double *dLdu)
             double *tmp = (double *)a->phi[a->pcur ^ 1];
             if (a->ag.mirror)
                 lbk::adj_seed_kernel<L, T, double, true><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
-                    (const T *)c->f[c->cur], a->ag, a->K, dLdu, tmp, a->slot_step);
+                    (const T *)c->f[c->cur], a->ag, a->K, dLdu, dLdth, tmp, a->slot_step);
             else
                 lbk::adj_seed_kernel<L, T, double><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
-                    (const T *)c->f[c->cur], a->ag, a->K, dLdu, tmp, a->slot_step);
+                    (const T *)c->f[c->cur], a->ag, a->K, dLdu, dLdth, tmp, a->slot_step);
             cudaError_t e = cudaGetLastError();
             const int64_t n = (int64_t)c->q * a->ag.slab;
             double mx = 0.0;
@@ -917,10 +929,10 @@ template <class L, typename T> cudaError_t seed_t(lb_adj *a, const double *dLdu)
     using A = AdjT<T>;
     if (a->ag.mirror)
         lbk::adj_seed_kernel<L, T, A, true><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
-            (const T *)c->f[c->cur], a->ag, a->K, dLdu, (A *)a->phi[a->pcur], a->slot_step);
+            (const T *)c->f[c->cur], a->ag, a->K, dLdu, dLdth, (A *)a->phi[a->pcur], a->slot_step);
     else
         lbk::adj_seed_kernel<L, T, A><<<nb, lbk::kSweepThreads, 0, c->stream>>>(
-            (const T *)c->f[c->cur], a->ag, a->K, dLdu, (A *)a->phi[a->pcur], a->slot_step);
+            (const T *)c->f[c->cur], a->ag, a->K, dLdu, dLdth, (A *)a->phi[a->pcur], a->slot_step);
     return cudaGetLastError();
 }
 
@@ -979,21 +991,21 @@ template <class L> cudaError_t init_t(lb_adj *a, double *dth0)
     return cudaGetLastError();
 }
 
-template <class L> cudaError_t seed_l(lb_adj *a, const double *dLdu)
+template <class L> cudaError_t seed_l(lb_adj *a, const double *dLdu, const double *dLdth)
 {
     switch (a->ctx->precision) {
-    case LB_FX64: return seed_t<L, long long>(a, dLdu);
-    case LB_FP32_SHIFTED: return seed_t<L, float>(a, dLdu);
-    default: return seed_t<L, double>(a, dLdu);
+    case LB_FX64: return seed_t<L, long long>(a, dLdu, dLdth);
+    case LB_FP32_SHIFTED: return seed_t<L, float>(a, dLdu, dLdth);
+    default: return seed_t<L, double>(a, dLdu, dLdth);
     }
 }
 
-cudaError_t do_seed(lb_adj *a, const double *dLdu)
+cudaError_t do_seed(lb_adj *a, const double *dLdu, const double *dLdth)
 {
     switch (a->ctx->d) {
-    case 1: return seed_l<lbk::D1Q3>(a, dLdu);
-    case 2: return seed_l<lbk::D2Q9>(a, dLdu);
-    default: return seed_l<lbk::D3Q19>(a, dLdu);
+    case 1: return seed_l<lbk::D1Q3>(a, dLdu, dLdth);
+    case 2: return seed_l<lbk::D2Q9>(a, dLdu, dLdth);
+    default: return seed_l<lbk::D3Q19>(a, dLdu, dLdth);
     }
 }
 
@@ -1142,6 +1154,7 @@ lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, dou
     lb_status st = lb_set_theta0(c, theta0, nullptr);  // FD4 gradient: a function of theta0 alone
     if (st != LB_OK) return st;
     make_adjk(a);  // after lb_set_theta0: the FX64 scale is known now
+    a->fwd_gen = c->gen;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(a->th0, theta0, sizeof(double) * c->nodes, cudaMemcpyDeviceToDevice, c->stream)) !=
             cudaSuccess ||
@@ -1160,7 +1173,7 @@ lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, dou
             continue;
         }
         const int p = c->cur;
-        if (!a->fgraph[p] || a->fmirror[p] != c->geom.mirror) {
+        if (!a->fgraph[p] || a->fgen[p] != c->gen) {
             e = record_graph(c, &a->fgraph[p], [&]() {
                 cudaError_t r = cudaSuccess;
                 for (int64_t m = 0, q = p; m < n && r == cudaSuccess; ++m, q ^= 1)
@@ -1168,7 +1181,7 @@ lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, dou
                 return r;
             });
             if (e != cudaSuccess) return acuda(a, e, "lb_adjoint_forward: record");
-            a->fmirror[p] = c->geom.mirror;
+            a->fgen[p] = c->gen;
         }
         if ((e = cudaGraphLaunch(a->fgraph[p], c->stream)) != cudaSuccess)
             return acuda(a, e, "lb_adjoint_forward: graph");
@@ -1180,10 +1193,11 @@ lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, dou
     return LB_OK;
 }
 
-lb_status lb_adjoint_seed(lb_adj *a, const double *dLdu)
+lb_status lb_adjoint_seed(lb_adj *a, const double *dLdu, const double *dLdth)
 {
     lbk::NvtxRange nvtx_range("lb_adjoint_seed");
-    if (!a || !dLdu) return LB_EINVAL;
+    if (!a) return LB_EINVAL;
+    if (!dLdu && !dLdth) return afail(a, LB_EINVAL, "lb_adjoint_seed: dL_du and dL_dtheta are both NULL");
     if (!a->forward_done || a->ctx->step != a->T)
         return afail(a, LB_ESTATE, "lb_adjoint_seed: run lb_adjoint_forward first (and do not step the context)");
     lb_ctx *c = a->ctx;
@@ -1193,7 +1207,7 @@ lb_status lb_adjoint_seed(lb_adj *a, const double *dLdu)
         (e = cudaMemsetAsync(a->dflag, 0, sizeof(int), c->stream)) != cudaSuccess)
         return acuda(a, e, "lb_adjoint_seed");
     a->pcur = 0;
-    if ((e = do_seed(a, dLdu)) != cudaSuccess) return acuda(a, e, "lb_adjoint_seed: launch");
+    if ((e = do_seed(a, dLdu, dLdth)) != cudaSuccess) return acuda(a, e, "lb_adjoint_seed: launch");
     a->done = 0;
     a->seeded = true;
     return LB_OK;
@@ -1205,8 +1219,8 @@ lb_status lb_adjoint_step(lb_adj *a, int64_t nsteps)
     if (!a || nsteps < 0) return LB_EINVAL;
     if (!a->seeded) return afail(a, LB_ESTATE, "lb_adjoint_step: call lb_adjoint_seed first");
     if (a->done + nsteps > a->T) return afail(a, LB_EINVAL, "lb_adjoint_step: more reverse steps than forward");
-    if (a->ctx->geom.mirror != a->ag.mirror)
-        return afail(a, LB_ESTATE, "lb_adjoint_step: the walls changed since lb_adjoint_forward");
+    if (a->ctx->geom.mirror != a->ag.mirror || a->ctx->gen != a->fwd_gen)
+        return afail(a, LB_ESTATE, "lb_adjoint_step: the walls or the viscosity changed since lb_adjoint_forward");
     cudaError_t e;
     lb_ctx *c = a->ctx;
     const bool cap = stream_capturing(c->stream);

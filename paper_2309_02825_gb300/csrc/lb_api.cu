@@ -87,6 +87,40 @@ cudaError_t record_sweeps(lb_ctx *c, int from)
     return e;
 }
 
+// Read back and clear the recovery and range flags (ctx->dflag[1..2]) after
+// the work enqueued so far; synchronises the stream.  A staging timeout or a
+// fixed-point range overflow leaves the context uninitialised: the state (or
+// a staging tile) may be corrupt, so lb_step and lb_macros refuse to run
+// until lb_set_theta0 or lb_load_state sets a state again.
+lb_status read_flags(lb_ctx *c, const char *who)
+{
+    int fl[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(fl, c->dflag + lbk::kFlagRecover, sizeof fl, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dflag + lbk::kFlagRecover, 0, sizeof fl, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, who);
+    const std::string w(who);
+    if (fl[0] & 4) {
+        c->initialized = false;
+        return fail(c, LB_ETIMEOUT, w + ": a shared-memory staging wait of the recovery timed out; set the state "
+                                        "again (lb_set_theta0 or lb_load_state)");
+    }
+    if (fl[1]) {
+        c->initialized = false;
+        return fail(c, LB_EINVAL, w + ": a fixed-point distribution reached |f| >= 2^61 (the run is unstable: an "
+                                      "FP64 run would overflow); set the state again");
+    }
+    if (fl[0]) return fail(c, LB_ENONPOS, w + ": theta <= 0 or non-finite at some node");
+    return LB_OK;
+}
+
+bool capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return true;
+    return cap != cudaStreamCaptureStatusNone;
+}
+
 }  // namespace
 
 namespace lbk {
@@ -248,6 +282,45 @@ lb_status lb_set_boundary(lb_ctx *c, const int *kind)
         }
     c->geom.mirror = mask;
     c->initialized = false;  // the stored state follows the old walls: initialise again
+    ++c->gen;
+    return LB_OK;
+}
+
+lb_status lb_set_viscosity(lb_ctx *c, double nu)
+{
+    lbk::NvtxRange nvtx_range("lb_set_viscosity");
+    if (!c) return LB_EINVAL;
+    if (!finite_pos(nu)) return fail(c, LB_EINVAL, "lb_set_viscosity: nu must be finite and > 0");
+    lb_ctx trial;
+    trial.d = c->d;
+    trial.dx = c->dx;
+    trial.dt = c->dt;
+    trial.c = c->c;
+    trial.nu = nu;
+    trial.eps = nu * c->dt / (c->dx * c->dx);
+    const lb_relax rs = {c->paper ? 1 : 0, c->s1, c->s2x, c->s22, c->w1, c->wd, c->theta_ref};
+    if (!lbk::derive_params(trial, &rs))
+        return fail(c, LB_EINVAL, "lb_set_viscosity: the relaxation set leaves (0, 2) at this nu");
+    DeviceGuard dg(c);
+    // recorded sweeps carry the old collision constants; drain the stream before dropping them
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lb_set_viscosity");
+    for (auto &g : c->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    c->nu = nu;
+    c->eps = trial.eps;
+    c->s1 = trial.s1;
+    c->s2x = trial.s2x;
+    c->s22 = trial.s22;
+    c->w0 = trial.w0;
+    c->w1 = trial.w1;
+    c->wd = trial.wd;
+    c->sigma = trial.sigma;
+    c->cs2 = trial.cs2;
+    ++c->gen;
     return LB_OK;
 }
 
@@ -275,7 +348,7 @@ lb_status lb_set_theta0(lb_ctx *c, const double *theta0, const double *grad)
             return cuda_fail(c, e, "lb_set_theta0: fd4 launch");
         grad = c->gradtmp;
     }
-    if ((e = cudaMemsetAsync(c->dflag, 0, sizeof(int), c->stream)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(c->dflag, 0, sizeof(int) * 3, c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "lb_set_theta0: flag reset");
     if (c->precision == LB_FX64) {
         // Fixed-point scale: max|theta0| * 2^F < 2^59.  Every moment sum is
@@ -351,9 +424,20 @@ lb_status lb_macros(lb_ctx *c, double *theta, double *grad, double *u)
     if (!c->initialized) return fail(c, LB_ESTATE, "lb_macros: call lb_set_theta0 first");
     if (!theta && !grad && !u) return LB_OK;
     DeviceGuard dg(c);
-    cudaError_t e = lbk::launch_macros(c, c->f[c->cur], theta, grad, u, c->dflag + 1);
+    cudaError_t e = lbk::launch_macros(c, c->f[c->cur], theta, grad, u, c->dflag + lbk::kFlagRecover);
     if (e != cudaSuccess) return cuda_fail(c, e, "lb_macros: launch");
-    return LB_OK;
+    // inside the caller's stream capture nothing can be read back: the flags
+    // then wait for lb_check, lb_sum_theta or lb_reduce
+    if (capturing(c->stream)) return LB_OK;
+    return read_flags(c, "lb_macros");
+}
+
+lb_status lb_check(lb_ctx *c)
+{
+    lbk::NvtxRange nvtx_range("lb_check");
+    if (!c) return LB_EINVAL;
+    DeviceGuard dg(c);
+    return read_flags(c, "lb_check");
 }
 
 lb_status lb_sum_theta(lb_ctx *c, double *out)
@@ -364,9 +448,18 @@ lb_status lb_sum_theta(lb_ctx *c, double *out)
     DeviceGuard dg(c);
     cudaError_t e = lbk::launch_sum_state(c, c->f[c->cur], c->dout);
     double v = 0.0;
+    int range = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&v, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&range, c->dflag + lbk::kFlagRange, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dflag + lbk::kFlagRange, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lb_sum_theta");
+    if (range) {
+        c->initialized = false;
+        return fail(c, LB_EINVAL, "lb_sum_theta: a fixed-point distribution reached |f| >= 2^61 (the run is "
+                                  "unstable: an FP64 run would overflow); set the state again");
+    }
     if (c->precision == LB_FP32_SHIFTED) {
         // sum of the node weights: N_a per periodic axis, N_a - 1 per mirror axis
         double wn = 1.0;
@@ -405,7 +498,10 @@ lb_status lb_reduce(lb_ctx *c, const double *theta, const double *u, const doubl
         out[3 * v + 2] = have ? (sx > 0 ? sqrt(se / sx) : (se > 0 ? INFINITY : 0.0)) : NAN;
     }
     out[3 * (c->d + 1)] = raw[ns - 1];
-    if (flag & 4) return fail(c, LB_ETIMEOUT, "lb_macros: a shared-memory staging wait timed out");
+    if (flag & 4) {
+        c->initialized = false;
+        return fail(c, LB_ETIMEOUT, "lb_macros: a shared-memory staging wait timed out");
+    }
     if (flag) return fail(c, LB_ENONPOS, "lb_macros saw theta <= 0 or non-finite");
     return LB_OK;
 }
@@ -438,6 +534,7 @@ lb_status lb_load_state(lb_ctx *c, const void *buf, int64_t step)
     DeviceGuard dg(c);
     cudaError_t e = cudaMemcpyAsync(c->f[c->cur], buf, (size_t)c->q * c->geom.slab * c->elem,
                                     cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dflag + lbk::kFlagRecover, 0, sizeof(int) * 2, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lb_load_state");
     c->initialized = true;
     c->step = step;

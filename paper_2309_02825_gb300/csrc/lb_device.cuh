@@ -763,6 +763,19 @@ __global__ void __launch_bounds__(sweep_threads<T>()) sweep_kernel(const T *__re
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) f[i][v] = n[i];
     }
+    if constexpr (std::is_same<K, CollFxR>::value) {
+        // |v| < 2^61 iff v + 2^61 lies in [0, 2^62): only the high word of
+        // the sum changes, so OR the high words + 2^29 and test bits 30, 31
+        unsigned acc = 0u;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            if (x0 + V * lane + v < g.N0) {
+#pragma unroll
+                for (int i = 0; i < L::Q; ++i) acc |= (unsigned)((unsigned long long)f[i][v] >> 32) + 0x20000000u;
+            }
+        }
+        if (__any_sync(0xffffffffu, acc >= 0x40000000u) && lane == 0) atomicOr(k.range, 1);
+    }
 
     if (x0 + V * lane >= g.pitch) return;  // beyond the row: loads only
     T *dp = dst + row * g.pitch + x0 + V * lane;
@@ -803,6 +816,14 @@ __global__ void __launch_bounds__(sweep_threads<T>()) sweep_flat_kernel(const T 
     T f[L::Q];
     gather_flat<L, T>(src, g, row, x, f);
     collide(L{}, f, k);
+    if constexpr (std::is_same<K, CollFxR>::value) {
+        unsigned acc = 0u;  // |v| < 2^61 check, as in sweep_kernel
+        if (q < g.rows * g.N0) {
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) acc |= (unsigned)((unsigned long long)f[i] >> 32) + 0x20000000u;
+        }
+        if (__any_sync(0xffffffffu, acc >= 0x40000000u) && lane == 0) atomicOr(k.range, 1);
+    }
     if (q >= g.rows * g.N0) return;  // past the last node: loads only
     T *dp = dst + row * g.pitch + x;
 #pragma unroll

@@ -31,6 +31,15 @@ CollFx make_coll_fx(const lb_ctx *c)
     return k;
 }
 
+// The constants with the context's range flag, for the single-grid sweeps.
+static CollFxR make_coll_fxr(lb_ctx *c)
+{
+    CollFxR k;
+    static_cast<CollFx &>(k) = make_coll_fx(c);
+    k.range = c->dflag + kFlagRange;
+    return k;
+}
+
 template <class L> static cudaError_t sweep_fx_t(lb_ctx *c, const void *src, void *dst)
 {
     constexpr int TH = sweep_threads<long long>();
@@ -38,17 +47,17 @@ template <class L> static cudaError_t sweep_fx_t(lb_ctx *c, const void *src, voi
     const unsigned nb = (unsigned)(((flat ? c->geom.fseg : c->geom.nseg) + TH / 32 - 1) / (TH / 32));
     if constexpr (L::D == 4) {
         if (flat) {
-            sweep_flat_kernel<L, long long, CollFx><<<nb, TH, 0, c->stream>>>(
-                (const long long *)src, (long long *)dst, c->geom, make_coll_fx(c));
+            sweep_flat_kernel<L, long long, CollFxR><<<nb, TH, 0, c->stream>>>(
+                (const long long *)src, (long long *)dst, c->geom, make_coll_fxr(c));
             return cudaGetLastError();
         }
     }
     if (c->geom.mirror)
-        sweep_kernel<L, long long, CollFx, true><<<nb, TH, 0, c->stream>>>(
-            (const long long *)src, (long long *)dst, c->geom, make_coll_fx(c));
+        sweep_kernel<L, long long, CollFxR, true><<<nb, TH, 0, c->stream>>>(
+            (const long long *)src, (long long *)dst, c->geom, make_coll_fxr(c));
     else
-        sweep_kernel<L, long long, CollFx><<<nb, TH, 0, c->stream>>>(
-            (const long long *)src, (long long *)dst, c->geom, make_coll_fx(c));
+        sweep_kernel<L, long long, CollFxR><<<nb, TH, 0, c->stream>>>(
+            (const long long *)src, (long long *)dst, c->geom, make_coll_fxr(c));
     return cudaGetLastError();
 }
 

@@ -161,6 +161,15 @@ template <typename T> struct Coll {
 struct CollFx {
     long long k1, k2, k3, cA, wd;
 };
+// The single-grid fixed-point sweep also checks every value it stores
+// against |v| < 2^61 and sets *range when one is not (an unstable custom
+// relaxation set grows the state until int64 would wrap; FP64 would reach
+// Inf/NaN instead).  Moment sums of values below 2^61 that stay below 2^63
+// are exact, so a run whose values cross 2^61 is caught at the step it does,
+// unless that one step grows them from below 2^61 past 2^63 / q.
+struct CollFxR : CollFx {
+    int *range;
+};
 constexpr int kFxCoefBits = 62;
 
 // Recovery constants (Sec. III.C): u_a = ucoef * J_a / theta with
@@ -213,6 +222,7 @@ struct lb_ctx {
     bool initialized = false;
     int64_t step = 0;
     int device = 0;
+    uint64_t gen = 0;  // bumped whenever the walls or the viscosity change (recorded launches go stale)
     std::string err;
 };
 
@@ -234,6 +244,10 @@ struct NvtxRange {
 bool derive_params(lb_ctx &c, const lb_relax *rs);
 template <typename T> Coll<T> make_coll(const lb_ctx &c);
 CollFx make_coll_fx(const lb_ctx *c);  // the same constants in 62-bit fixed point
+// Device flags of a context (ctx->dflag): 0 initialisation, 1 recovery
+// (bit 0: theta <= 0 or non-finite, bit 2: a staging wait timed out),
+// 2 fixed-point sweep range (CollFxR).
+constexpr int kFlagInit = 0, kFlagRecover = 1, kFlagRange = 2;
 
 constexpr int kRedThreads = 256;
 constexpr int kRedSlots = 16;  // doubles per block partial (>= 3*(d+1)+1)

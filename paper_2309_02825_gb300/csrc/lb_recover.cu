@@ -110,7 +110,12 @@ __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ sr
     }
     if (!mbar_wait_bounded(barp, 0)) {
         if (threadIdx.x == 0) atomicOr(flag, 4);
-        mbar_wait_bounded(barp, 0);  // let this block's copies land before its shared memory goes away
+        // Give this block's copies a second bounded interval to land before its
+        // shared memory goes away.  If that also runs out the block returns with
+        // copies possibly still in flight; the host treats flag bit 2 as fatal
+        // for the context's state (lb_macros returns LB_ETIMEOUT and the context
+        // needs a new state before it launches again).
+        mbar_wait_bounded(barp, 0);
         return;
     }
 

@@ -36,16 +36,21 @@ double *g_scratch_addr[kMaxDevices] = {nullptr};
 int g_blocks[kMaxDevices] = {0};
 
 // Per-device set-up: the host-side name g_norms_scratch is only a stand-in
-// for the device array, so its device address is looked up once per
-// device, with that device current.
-cudaError_t scratch_for_current_device(double **ptr, int *nblocks)
+// for the device array, so its device address is looked up with that device
+// current.  The lookup is repeated on every call made outside a stream
+// capture (a cheap host call), so an address cached before a
+// cudaDeviceReset is never reused; inside a capture, where a first lookup
+// could load the module, the cached address of an earlier call is used.
+cudaError_t scratch_for_current_device(cudaStream_t stream, double **ptr, int *nblocks)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
     std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_norms_scratch);
         if (e != cudaSuccess) return e;
@@ -89,7 +94,7 @@ extern "C" lb_status lb_reduce_static(int d, int64_t nodes, const double *theta,
     if ((u == nullptr) != (exact_u == nullptr)) return LB_EINVAL;
     double *scratch = nullptr;
     int nb = 0;
-    cudaError_t e = scratch_for_current_device(&scratch, &nb);
+    cudaError_t e = scratch_for_current_device((cudaStream_t)stream, &scratch, &nb);
     if (e != cudaSuccess) return LB_ECUDA;
     // Every block overwrites its whole partial row and the fold overwrites
     // the raw row, so nothing has to be cleared between calls.

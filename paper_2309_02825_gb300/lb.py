@@ -71,6 +71,8 @@ def load():
             "lb_step": ([vp, i64], ctypes.c_int),
             "lb_get_step": ([vp, p64], ctypes.c_int),
             "lb_macros": ([vp, vp, vp, vp], ctypes.c_int),
+            "lb_check": ([vp], ctypes.c_int),
+            "lb_set_viscosity": ([vp, dbl], ctypes.c_int),
             "lb_sum_theta": ([vp, pd], ctypes.c_int),
             "lb_reduce": ([vp, vp, vp, vp, vp, pd], ctypes.c_int),
             "lb_state_layout": ([vp, p64, p64, p64], ctypes.c_int),
@@ -192,6 +194,17 @@ def lb_macros(ctx, theta=None, grad_theta=None, u=None):
     _check(lib, ctx, st, "lb_macros")
 
 
+def lb_check(ctx):
+    """Synchronise and raise LBError for any device-side flag set since the last report."""
+    lib = load()
+    _check(lib, ctx, lib.lb_check(ctx), "lb_check")
+
+
+def lb_set_viscosity(ctx, nu):
+    lib = load()
+    _check(lib, ctx, lib.lb_set_viscosity(ctx, float(nu)), "lb_set_viscosity")
+
+
 def lb_sum_theta(ctx):
     lib = load()
     v = ctypes.c_double()
@@ -215,10 +228,25 @@ def lb_reduce(ctx, theta, u, exact_theta, exact_u, d):
 
 def lb_reduce_static(d, nodes, theta, u, exact_theta, exact_u, out, stream=None):
     """Allocation-free error norms (device output ``out`` of 3(d+1)+1 doubles),
-    for callers that cannot allocate device memory; see include/lb.h."""
+    for callers that cannot allocate device memory; see include/lb.h.  The
+    tensors must hold exactly ``nodes`` (theta fields) and ``d * nodes``
+    (velocity fields) values and lie on the current device."""
     lib = load()
-    st = lib.lb_reduce_static(int(d), int(nodes), _ptr(theta, "theta"), _ptr(u, "u"),
-                              _ptr(exact_theta, "exact_theta"), _ptr(exact_u, "exact_u"),
+    d, nodes = int(d), int(nodes)
+    # sizes the library serves are checked against the tensors here; others
+    # go to the library, which rejects them (LB_EINVAL)
+    n = nodes if (1 <= d <= 3 and 1 <= nodes <= (1 << 31)) else None
+    if n is not None:
+        dev = torch.cuda.current_device()
+        for name, t in (("theta", theta), ("u", u), ("exact_theta", exact_theta), ("exact_u", exact_u),
+                        ("out", out)):
+            if isinstance(t, torch.Tensor) and t.is_cuda and t.device.index != dev:
+                raise ValueError("%s is on cuda:%d, not the current device cuda:%d" % (name, t.device.index, dev))
+        if not isinstance(out, torch.Tensor) or out.numel() < 3 * (d + 1) + 1:
+            raise ValueError("out must hold at least 3(d+1)+1 = %d doubles" % (3 * (d + 1) + 1))
+    st = lib.lb_reduce_static(d, nodes, _ptr(theta, "theta", numel=n), _ptr(u, "u", numel=None if n is None else d * n),
+                              _ptr(exact_theta, "exact_theta", numel=n),
+                              _ptr(exact_u, "exact_u", numel=None if n is None else d * n),
                               _ptr(out, "out"), _stream_handle(stream))
     if st != LB_OK:
         raise LBError(st, "lb_reduce_static")
@@ -343,6 +371,13 @@ class Solver:
 
     def sum_theta(self):
         return lb_sum_theta(self.ctx)
+
+    def check(self):
+        lb_check(self.ctx)
+
+    def set_viscosity(self, nu):
+        lb_set_viscosity(self.ctx, nu)
+        self.params = lb_get_params(self.ctx)
 
     def reduce(self, theta, u, exact_theta, exact_u):
         return lb_reduce(self.ctx, theta, u, exact_theta, exact_u, self.d)
@@ -496,7 +531,7 @@ _adj_sigs = {
     "lb_adjoint_create": (["vp", "i64", "i64", "i", "pvp"], "i"),
     "lb_adjoint_destroy": (["vp"], "i"),
     "lb_adjoint_forward": (["vp", "vp", "vp", "vp"], "i"),
-    "lb_adjoint_seed": (["vp", "vp"], "i"),
+    "lb_adjoint_seed": (["vp", "vp", "vp"], "i"),
     "lb_adjoint_step": (["vp", "i64"], "i"),
     "lb_adjoint_result": (["vp", "vp", "pd"], "i"),
     "lb_adjoint_info": (["vp", "pd"], "i"),
@@ -551,8 +586,10 @@ class Adjoint:
         self._call("lb_adjoint_forward", _ptr(theta0, "theta0", numel=s.nodes), _ptr(theta, "theta"), _ptr(u, "u"))
         return u
 
-    def seed(self, dL_du):
-        self._call("lb_adjoint_seed", _ptr(dL_du, "dL_du", numel=self.solver.d * self.solver.nodes))
+    def seed(self, dL_du=None, dL_dtheta=None):
+        """Seed with dL/du(T) (d*nodes) and/or dL/dtheta(T) (nodes); either may be None."""
+        self._call("lb_adjoint_seed", _ptr(dL_du, "dL_du", numel=self.solver.d * self.solver.nodes),
+                   _ptr(dL_dtheta, "dL_dtheta", numel=self.solver.nodes))
 
     def step(self, n):
         self._call("lb_adjoint_step", int(n))

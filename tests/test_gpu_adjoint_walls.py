@@ -91,7 +91,7 @@ def test_wall_adjoint_matches_dense_jacobian_and_nu_differences(d, N, mirror, T,
           - _oracle_loss(d, N, mirror, nu - h, dx, dt, th0, ut, T)) / (2 * h)
     print("wall adjoint %s d=%d N=%s walls=%s: dtheta0 rel %.2e, dnu rel %.2e"
           % (precision, d, N, mirror, rel, abs(dnu / fd - 1)))
-    assert rel <= 1e-9
+    assert rel <= 1e-12
     assert dnu == pytest.approx(fd, rel=1e-6)
 
 

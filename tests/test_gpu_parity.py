@@ -19,7 +19,6 @@ from paper_2309_02825_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
-EPS64 = 2.0 ** -53
 
 
 def _dev(a):
@@ -35,25 +34,31 @@ def _relmax(a, b):
     return float(np.max(np.abs(a - b)) / (scale if scale > 0 else 1.0))
 
 
-def _check_fp64(ref, got, m, nsteps):
-    """theta: max |gpu - oracle| <= 1e-12 max |theta|.  grad and u come from
-    J = sum_k e_k f_k, a sum whose terms are O(theta): its rounding floor is
-    about q eps sum_k |f_k| no matter how small J is, so for them the bound is
-    1e-12 max|field| plus that floor (times sqrt(steps + 1) for the rounding
-    carried by f), scaled by the recovery coefficient of each field."""
-    th_o = ref[0]
-    p = m.params
-    sigma = 2 * p["w1"] + 4 * (m.d - 1) * p["wd"]
-    floor_j = 8 * m.q * EPS64 * np.max(np.abs(th_o)) * np.sqrt(nsteps + 1)
-    coef = {"grad": p["s1"] / (sigma * p["dx"]), "u": (2 - p["s1"]) * p["c"] / np.min(th_o)}
+def _check_fp64(ref, got, m, nsteps, ref0=None):
+    """theta, grad theta and u each: max |gpu - oracle| <= 1e-12 max |oracle|.
+
+    ref0 (the oracle's fields at step 0) is given only for the grids listed in
+    DECAYING: there the bound is 1e-12 of max(|field(T)|, |field(0)|)."""
     out = {}
-    for name, a, b in zip(("theta", "grad", "u"), got, ref):
+    for k, (name, a, b) in enumerate(zip(("theta", "grad", "u"), got, ref)):
         diff = float(np.max(np.abs(a - b)))
         scale = float(np.max(np.abs(b)))
-        bound = TOL64 * scale + (coef[name] * floor_j if name in coef else 0.0)
         out[name] = diff / scale if scale > 0 else diff
-        assert diff <= bound, (name, diff, bound, out[name])
+        if ref0 is not None:
+            scale = max(scale, float(np.max(np.abs(ref0[k]))))
+        assert diff <= TOL64 * scale, (name, diff, TOL64 * scale, out[name])
     return out
+
+
+# 1D grids of one to three nodes, where every node is at the periodic wrap:
+# grad theta and u have no spatial structure left to keep them up and decay
+# geometrically (J by a factor (1 - s1) per step on one node) to 1e-6 .. 1e-4
+# of their initial size, while the rounding carried from the first steps
+# stays at the initial size.  For these grids the bound is 1e-12 of the
+# initial field's size; measured against the final field's own maximum the
+# differences are 1.6e-12 .. 5.1e-11 (grad), all other cases meet 1e-12 of
+# their own maximum.
+DECAYING = {(1, (1,)), (1, (2,)), (1, (3,))}
 
 
 def _problem(d, N, seed, nu=0.02):
@@ -69,7 +74,9 @@ def _run_both(d, N, nsteps, seed=11, precision="fp64", grad=True, relax=None, th
     th0 = prob.theta(N, dx)
     g0 = prob.grad(N, dx) if grad else None
     m = O.Model(d, N, nu, dx, dt, relax)
-    th_o, g_o, u_o = m.recover(m.run(m.initialize(th0, g0), nsteps))
+    f0 = m.initialize(th0, g0)
+    th_o, g_o, u_o = m.recover(m.run(f0, nsteps))
+    m.ref0 = m.recover(f0) if (d, tuple(N)) in DECAYING else None
     s = lb.Solver(d, N, nu, dx, dt, relax=relax, precision=precision, theta_ref=theta_ref)
     s.set_theta0(_dev(th0), None if g0 is None else _dev(g0))
     s.step(nsteps)
@@ -94,7 +101,7 @@ CASES = [
 def test_fp64_matches_oracle(d, N, nsteps, precision):
     """FP64 storage and 64-bit fixed-point storage both meet the FP64 bar."""
     ref, got, _, m = _run_both(d, N, nsteps, precision=precision)
-    rel = _check_fp64(ref, got, m, nsteps)
+    rel = _check_fp64(ref, got, m, nsteps, m.ref0)
     print("%s parity d=%d N=%s steps=%d rel: %s" % (precision, d, N, nsteps, rel))
 
 
@@ -282,3 +289,96 @@ def test_steps_captured_into_a_caller_graph():
     th, _, u = s.macros()
     torch.cuda.synchronize()
     assert torch.equal(th, th_ref) and torch.equal(u, u_ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fx64", "fp32s"])
+def test_set_viscosity_equals_a_new_context(precision):
+    """lb_set_viscosity re-derives Eq. (Bur-Sol) in place: a context made at
+    nu1 and moved to nu2 steps exactly like one made at nu2 (also across a
+    change between steps, where recorded sweeps must be dropped)."""
+    d, N = 2, (70, 45)
+    prob, dx, dt = _problem(d, N, 17)
+    th0, g0 = _dev(prob.theta(N, dx)), _dev(prob.grad(N, dx))
+    a = lb.Solver(d, N, 0.013, dx, dt, precision=precision, theta_ref=1.5)
+    a.set_viscosity(prob.nu)
+    b = lb.Solver(d, N, prob.nu, dx, dt, precision=precision, theta_ref=1.5)
+    assert a.params == b.params
+    for s in (a, b):
+        s.set_theta0(th0, g0)
+        s.step(40)
+    a.set_viscosity(0.031)
+    a.step(40)
+    a.set_viscosity(prob.nu)
+    a.step(33)
+    b.set_viscosity(0.031)
+    b.step(40)
+    b.set_viscosity(prob.nu)
+    for _ in range(33):
+        b.step(1)
+    for x, y in zip(a.macros(), b.macros()):
+        assert torch.equal(x, y)
+    with pytest.raises(lb.LBError) as ei:
+        a.set_viscosity(-1.0)
+    assert ei.value.status == lb.LB_EINVAL
+
+
+def test_macros_reports_nonpositive_theta_itself():
+    """lb_macros reads back its own flag: a state whose theta is negative
+    somewhere is reported by that call (LB_ENONPOS), not by a later one."""
+    d, N = 2, (64, 40)
+    prob, dx, dt = _problem(d, N, 3)
+    s = lb.Solver(d, N, prob.nu, dx, dt)
+    s.set_theta0(_dev(prob.theta(N, dx)), _dev(prob.grad(N, dx)))
+    s.step(3)
+    s.macros()
+    snap = s.save_state()
+    vals = snap.view(torch.float64)
+    pitch, slab, _ = s.state_layout()
+    vals[5 * pitch + 7] = -50.0  # rest population of one node (population 0)
+    s.load_state(snap, 3)
+    with pytest.raises(lb.LBError) as ei:
+        s.macros()
+    assert ei.value.status == lb.LB_ENONPOS
+    s.check()  # reported once, then cleared
+    s.set_theta0(_dev(prob.theta(N, dx)), _dev(prob.grad(N, dx)))
+    s.macros()
+
+
+# Rates inside (0, 2) with weights that make the scheme unstable: the largest
+# |eigenvalue| of one step's Fourier symbol is 1.34 on this grid.
+UNSTABLE = {"s1": 1.46, "s2x": 1.07, "s22": 0.69, "w1": 0.29, "wd": -0.01}
+
+
+def test_fx64_range_overflow_is_reported_not_wrapped():
+    """An unstable custom relaxation set grows the state geometrically.  FX64
+    stores int64 values: the sweep flags |f| >= 2^61 and lb_macros reports
+    LB_EINVAL instead of returning wrapped values; the context then refuses
+    to step until a new state is set.  FP64 reaches non-finite theta
+    (LB_ENONPOS) on the same set."""
+    d, N = 2, (40, 30)
+    prob, dx, dt = _problem(d, N, 11)
+    th0, g0 = _dev(prob.theta(N, dx)), _dev(prob.grad(N, dx))
+    fx = lb.Solver(d, N, prob.nu, dx, dt, relax=UNSTABLE, precision="fx64")
+    fx.set_theta0(th0, g0)
+    fx.step(20)
+    fx.macros()  # still in range after 20 steps
+    fx.step(400)
+    with pytest.raises(lb.LBError) as ei:
+        fx.macros()
+    assert ei.value.status == lb.LB_EINVAL
+    with pytest.raises(lb.LBError) as ei:
+        fx.step(1)
+    assert ei.value.status == lb.LB_ESTATE
+    fx.set_theta0(th0, g0)  # a new state clears it
+    fx.step(5)
+    fx.check()
+    fx.step(400)
+    with pytest.raises(lb.LBError) as ei:
+        fx.sum_theta()
+    assert ei.value.status == lb.LB_EINVAL
+    f64 = lb.Solver(d, N, prob.nu, dx, dt, relax=UNSTABLE, precision="fp64")
+    f64.set_theta0(th0, g0)
+    f64.step(3000)
+    with pytest.raises(lb.LBError) as ei:
+        f64.macros()
+    assert ei.value.status == lb.LB_ENONPOS
