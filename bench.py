@@ -69,7 +69,7 @@ def parse():
     p.add_argument("--accuracy", action="store_true",
                    help="print the error-vs-exact convergence table (1D, 2D up to 4096^2, 3D up to 256^3) and exit")
     p.add_argument("--accuracy-precisions", default="fp64,fx64,fp32s")
-    p.add_argument("--profile-batch", default=None, metavar="COUNT,STEPS[,PREC]",
+    p.add_argument("--profile-batch", default=None, metavar="COUNT,STEPS[,PREC[,K,TILE,THREADS]]",
                    help="minimal command for ncu: COUNT batched 2D instances, STEPS steps, then exit")
     p.add_argument("--profile-adjoint", default=None, metavar="PREC,N,T",
                    help="minimal command for ncu: forward + seed + T reverse steps at N^2, then exit")
@@ -406,10 +406,27 @@ def run_e2e(args, s, case, th0_h, g0_h, ex_t_h, ex_u_h, stream, world):
             "u_rmse_last_step": results[-1]["u0"]["rmse"]}
 
 
+def blocked_bytes_per_lu(sizes, K, tile, elem, q=9):
+    """HBM bytes per lattice update of blocked launches (K steps each): every
+    tile is read with its K-node halo and written once per launch, tiles cut
+    as the library cuts them (ceil(N / tile) near-equal tiles per axis)."""
+    moved, lus = 0, 0
+    for n0, n1 in sizes:
+        ntx, nty = -(-n0 // tile), -(-n1 // tile)
+        tx, ty = -(-n0 // ntx), -(-n1 // nty)
+        for y0 in range(0, n1, ty):
+            for x0 in range(0, n0, tx):
+                w, h = min(tx, n0 - x0), min(ty, n1 - y0)
+                moved += q * elem * ((w + 2 * K) * (h + 2 * K) + w * h)
+                lus += w * h * K
+    return moved / lus
+
+
 def run_batched(local):
     """512 independent 2D instances (N log-uniform in [32, 512], nu log-uniform
-    in [0.005, 0.1], dt = 4 dx^2), FP32 shifted, 2000 steps: autotuned L2-sized
-    groups vs one launch per instance per step vs one flat launch per step."""
+    in [0.005, 0.1], dt = 4 dx^2), FP32 shifted, 2000 steps: the autotuned
+    schedule (blocked launches of K steps in shared memory, or one launch per
+    step) vs one launch per instance per step vs one flat launch per step."""
     import torch
     from paper_2309_02825_gb300 import lb
 
@@ -439,12 +456,12 @@ def run_batched(local):
         return e0.elapsed_time(e1) / 1e3
 
     t_tuned = timed(steps)
+    sched = b.schedule()
     with torch.cuda.stream(stream):
         th, u = b.macros()
         ex_t = np.concatenate([c.problem.theta(c.N, c.dx, c.t_end).ravel() for c in cases])
         ex_u = np.concatenate([np.ascontiguousarray(c.problem.u(c.N, c.dx, c.t_end)).ravel() for c in cases])
         err = b.errors(th, u, torch.from_numpy(ex_t).cuda(), torch.from_numpy(ex_u).cuda())
-    sched = b.schedule()
     base_steps = 20
     b.set_schedule(0.0, 256, False)
     t_base = timed(base_steps) * steps / base_steps
@@ -470,8 +487,20 @@ def run_batched(local):
     t_fx = ex0.elapsed_time(ex1) / 1e3
     bx.close()
     peak = load_peaks()["hbm_gbs"]
+
+    def roof(choice, t, elem):
+        """Per-step-equivalent fraction (2 q elem bytes per update, what one
+        launch per step must move) and, for blocked launches, the fraction of
+        the bytes they do move."""
+        out = {"per_step_equivalent_hbm_frac": 2 * 9 * elem * lu / t / 1e9 / peak}
+        if choice["steps_per_launch"]:
+            bpl = blocked_bytes_per_lu(sizes, choice["steps_per_launch"], choice["tile"], elem)
+            out.update({"blocked_bytes_per_lu": bpl, "blocked_hbm_gbs": bpl * lu / t / 1e9,
+                        "blocked_hbm_frac": bpl * lu / t / 1e9 / peak})
+        return out
+
     fx64 = {"aggregate_mlups": lu / t_fx / 1e6, "instances_per_s": len(cases) / t_fx, "seconds": t_fx,
-            "hbm_frac": 2 * 9 * 8 * lu / t_fx / 1e9 / peak, "autotune": choice_fx,
+            "autotune": choice_fx, **roof(choice_fx, t_fx, 8),
             "u_rmse_max_over_instances": float(np.max(errx[:, 1])),
             "theta_rmse_max_over_instances": float(np.max(errx[:, 0]))}
     return {
@@ -479,7 +508,7 @@ def run_batched(local):
                     "2000 steps",
         "instances": len(cases), "total_nodes": nodes, "steps": steps,
         "instances_per_s": len(cases) / t_tuned, "aggregate_mlups": lu / t_tuned / 1e6, "seconds": t_tuned,
-        "schedule": {"budget_bytes": sched["budget_bytes"], "threads": sched["threads"], "groups": sched["groups"]},
+        "schedule": sched,
         "autotune": choice,
         "one_launch_per_instance": {"aggregate_mlups": lu / t_base / 1e6, "instances_per_s": len(cases) / t_base,
                                     "sample_steps": base_steps},
@@ -487,7 +516,7 @@ def run_batched(local):
         "speedup_vs_one_launch_per_instance": t_base / t_tuned,
         "u_rmse_max_over_instances": float(np.max(err[:, 1])),
         "theta_rmse_max_over_instances": float(np.max(err[:, 0])),
-        "hbm_frac": 2 * 9 * 4 * lu / t_tuned / 1e9 / load_peaks()["hbm_gbs"],
+        **roof(choice, t_tuned, 4),
         "fx64": fx64,
     }
 
@@ -779,8 +808,9 @@ def run_4d(local, peaks):
 
 def run_profile_batch(local, spec):
     """Minimal, repeatable command for ncu: the first COUNT instances of the
-    batched workload (PREC, default FP32s; flat schedule with the block size
-    the autotuner picks for that precision), STEPS steps."""
+    batched workload (PREC, default FP32s), STEPS steps; with K,TILE,THREADS
+    appended, blocked launches of K steps, else the flat one-launch-per-step
+    schedule with the block size the autotuner picks for that precision."""
     import torch
     from paper_2309_02825_gb300 import lb
     torch.cuda.set_device(local)
@@ -793,7 +823,10 @@ def run_profile_batch(local, spec):
     kw = {"theta_ref": [1.5] * len(cases)} if prec == "fp32s" else {}
     b = lb.Batch([c.N for c in cases], [c.nu for c in cases], [c.dx for c in cases], [c.dt for c in cases],
                  precision=prec, **kw)
-    b.set_schedule(1e18, 64 if prec == "fx64" else 128, False)
+    if len(parts) > 5:
+        b.set_blocking(int(parts[3]), int(parts[4]), int(parts[5]), False)
+    else:
+        b.set_schedule(1e18, 64 if prec == "fx64" else 128, False)
     b.set_theta0(torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda())
     b.step(steps)
     torch.cuda.synchronize()

@@ -10,13 +10,20 @@
  * array and 2*N0_j*N1_j (x component first) to a vector array; offsets are
  * the prefix sums of N0_j*N1_j.
  *
- * Scheduling: instances are bin-packed (largest first) into groups whose two
- * state buffers fit a byte budget chosen to stay resident in L2.  A group
- * runs all requested steps back to back, one launch per step (each block of
- * a launch belongs to one instance), so its state is read from L2 rather
- * than HBM after the first step.  The launches are recorded once into CUDA
- * graphs and replayed.  lb_batch_autotune times candidate budgets and block
- * shapes on the caller's batch and keeps the fastest.
+ * Scheduling, two kinds:
+ *  - one launch per step: instances are bin-packed (largest first) into
+ *    groups whose two state buffers fit a byte budget chosen to stay
+ *    resident in L2; a group runs all requested steps back to back (each
+ *    block of a launch belongs to one instance);
+ *  - blocked (lb_batch_set_blocking): each launch advances every instance K
+ *    steps.  A block loads one tile of one instance with a K-node periodic
+ *    halo into shared memory, runs K steps there (the halo shrinking by one
+ *    node per step) and stores the tile, so HBM is read and written once per
+ *    K steps instead of every step.  Blocks never wait on one another.
+ * Either way the launches are recorded once into CUDA graphs and replayed,
+ * and every instance evolves bit for bit as the same grid would alone.
+ * lb_batch_autotune times both kinds (budgets, block sizes, steps per
+ * launch, tile sizes) on the caller's batch and keeps the fastest.
  */
 #ifndef LB_BATCH_H
 #define LB_BATCH_H
@@ -80,25 +87,43 @@ lb_status lb_batch_errors(lb_batch *b, const double *theta, const double *u, con
                           const double *exact_u, double *out);
 
 /*
- * Autotuner: times `trial_steps` steps for each candidate (group byte budget
- * 48, 96, 128 MB or all instances in one group, x 64, 128, 256 or 512 threads
- * per block) on this batch's real sizes and keeps the fastest.  Must be
- * called before lb_batch_set_theta0 (it overwrites the state).  choice
- * (host, may be NULL) receives {budget_bytes, threads_per_block, groups,
- * microseconds per step of the winner}.  Synchronises the stream.
+ * Autotuner: times about `trial_steps` steps (rounded up to whole launches)
+ * for each candidate on this batch's real sizes and keeps the fastest:
+ *  - one launch per step: group byte budget 48, 96, 128 MB or all instances
+ *    in one group, x 64, 128, 256 or 512 threads per block;
+ *  - blocked: K = 2, 4, 6, 8 or 12 steps per launch x the largest square tile
+ *    whose two buffers (with the K-node halo) fit one, or two, blocks per SM
+ *    x 256, 512 or 1024 threads per block.
+ * Must be called before lb_batch_set_theta0 (it overwrites the state).
+ * choice (host, may be NULL) receives {budget_bytes, threads_per_block,
+ * groups, microseconds per step of the winner, steps per launch (0: one
+ * launch per step), tile edge (0 likewise)}.  Synchronises the stream.
  */
 lb_status lb_batch_autotune(lb_batch *b, int trial_steps, double *choice);
 
 /*
- * Set the schedule explicitly: budget_bytes <= 0 puts every instance in its
- * own group (one launch per instance per step), a budget above the total
- * state puts all instances in one group (one launch per step); threads is
- * 64, 128, 256 or 512; use_graph = 0 launches every step directly instead of
- * replaying recorded graphs.  Keeps the state.
+ * Blocked schedule (see the scheduling note above): steps_per_launch K in
+ * 1..64 steps per launch; each instance axis of N nodes is cut into
+ * ceil(N / tile) near-equal tiles; threads 256, 512 or 1024 per block;
+ * use_graph as for lb_batch_set_schedule.  K = 0 returns to one launch per
+ * step.  A final launch of fewer than K steps covers a remainder.  Keeps the
+ * state.  Errors: LB_EINVAL (out of range, or the largest tile plus its halo
+ * needs more shared memory per block than the device has), LB_ECUDA.
+ */
+lb_status lb_batch_set_blocking(lb_batch *b, int steps_per_launch, int tile, int threads, int use_graph);
+
+/*
+ * Set a one-launch-per-step schedule explicitly (leaving blocked launches):
+ * budget_bytes <= 0 puts every instance in its own group (one launch per
+ * instance per step), a budget above the total state puts all instances in
+ * one group (one launch per step); threads is 64, 128, 256 or 512;
+ * use_graph = 0 launches every step directly instead of replaying recorded
+ * graphs.  Keeps the state.
  */
 lb_status lb_batch_set_schedule(lb_batch *b, double budget_bytes, int threads, int use_graph);
 
-/* Current schedule: {budget_bytes, threads_per_block, groups, total nodes}. */
+/* Current schedule (host, 7 values): {budget_bytes, threads_per_block, groups, total nodes, steps per launch
+ * (0: one launch per step), tile edge, tiles}. */
 lb_status lb_batch_schedule(const lb_batch *b, double *info);
 
 const char *lb_batch_last_error(const lb_batch *b);

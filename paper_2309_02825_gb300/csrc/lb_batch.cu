@@ -72,6 +72,236 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_sweep_kernel(const Ins
     for (int i = 0; i < L::Q; ++i) st_vec(dp + (int64_t)i * D.g.slab, f[i]);
 }
 
+// ---------------------------------------------------------------------------
+// Temporally blocked sweep: K steps per launch with the state in shared
+// memory.  One block owns one tile (tx x ty nodes) of one instance.  It
+// loads the tile plus a K-node halo on every side (periodic wrap at the
+// instance's edges; a tile wider than its instance wraps onto itself) into
+// shared memory, runs K steps there and stores the tile.  Blocks only read
+// the source buffer and write disjoint tiles of the destination buffer, and
+// the launch boundary orders launches: there is no wait between blocks.
+//
+// One shared buffer serves all K steps (the "AA" access pattern): a pull
+// step reads node x's pre-collision values from the neighbours, f_i(x) in
+// slot opp(i) of x - e_i, and writes f*_i(x) into slot i of x + e_i; a local
+// step reads f_i(x) from x's own slot i and writes f*_i(x) into its own slot
+// opp(i).  In either step the slots a node reads are exactly the slots it
+// writes, and no two nodes share a slot, so the update is in place without
+// races; steps alternate pull, local, pull, ...  The stored P form, f*_i(y)
+// held as P_i(y), is loaded into slot opp(i) of y, which is the state a pull
+// step expects; after an even number of steps it is in that form again,
+// after an odd number P_i(y) sits in slot i of y + e_i.  Step s updates the
+// nodes s or more away from the loaded region's border: their K-step
+// dependency cone (one node per step) lies inside it, and after K steps the
+// tile itself is valid; nodes nearer the border only ever hand garbage to
+// nodes that are not valid either.
+// HBM traffic per lattice update falls from 2 q sizeof(T) to
+// q sizeof(T) [(tx + 2K)(ty + 2K) + tx ty] / (K tx ty); the halo nodes'
+// recomputation is the price.  The arithmetic per node is the single-grid
+// collision on the same inputs, so results are bit-identical to it.
+// ---------------------------------------------------------------------------
+struct TileDesc {
+    int inst;      // instance
+    int x0, y0;    // tile origin (nodes)
+    int tx, ty;    // tile size (nodes)
+};
+
+// Asynchronous global -> shared copies at 32-bit shared addresses: one value,
+// or one 16-byte chunk (both addresses 16-byte aligned).
+template <typename T> __device__ __forceinline__ void cp_async_elem(unsigned dst, const T *src)
+{
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(unsigned dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// Shared-memory loads and stores at 32-bit shared addresses.
+template <typename T> __device__ __forceinline__ T lds(unsigned a);
+template <> __device__ __forceinline__ float lds<float>(unsigned a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
+template <> __device__ __forceinline__ double lds<double>(unsigned a)
+{
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+    return v;
+}
+template <> __device__ __forceinline__ long long lds<long long>(unsigned a)
+{
+    long long v;
+    asm volatile("ld.shared.s64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts(unsigned a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory"); }
+__device__ __forceinline__ void sts(unsigned a, double v) { asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory"); }
+__device__ __forceinline__ void sts(unsigned a, long long v)
+{
+    asm volatile("st.shared.s64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+// 16 bytes from shared memory to global memory (both 16-byte aligned).
+__device__ __forceinline__ void copy16_shared_to_global(void *g, unsigned a)
+{
+    unsigned x, y, z, w;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(a) : "memory");
+    asm volatile("st.global.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(g), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+
+__device__ __forceinline__ int wrap_index(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// Shared-memory layout of a blocked tile: rows of W = tx + 2K values (the
+// tile with its halo) at a pitch of Wp values, shifted by s0 values so that
+// every row has the same alignment modulo 16 bytes as its source row in
+// global memory (the middle of each row then moves in 16-byte chunks).
+__host__ __device__ inline int tb_pitch(int W, int elem)
+{
+    const int V4 = 16 / elem;
+    return (W + V4 - 1 + V4 - 1) / V4 * V4;  // room for any shift s0 < V4
+}
+// Dynamic shared memory of a blocked launch: one Q-population buffer.
+__host__ __device__ inline size_t tb_smem_bytes(int q, int elem, int W, int H)
+{
+    return (size_t)q * tb_pitch(W, elem) * H * elem;
+}
+
+template <class L, typename T, int TH>
+__global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1) batch_tb_kernel(const InstDesc<T> *__restrict__ inst,
+                                                         const TileDesc *__restrict__ tiles, const T *__restrict__ src,
+                                                         T *__restrict__ dst, int K)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int Q = L::Q, NW = TH / 32;
+    constexpr unsigned E = sizeof(T);
+    constexpr int V4 = 16 / (int)E;  // values per 16-byte chunk
+    const TileDesc t = tiles[blockIdx.x];
+    const InstDesc<T> D = inst[t.inst];
+    const int W = t.tx + 2 * K, H = t.ty + 2 * K;
+    const int gx0 = t.x0 - K;                 // global column of shared column 0 (may be < 0)
+    const int s0 = ((gx0 % V4) + V4) % V4;    // shift: shared column c sits at s0 + c
+    const int Wp = (s0 + W + V4 - 1) / V4 * V4;
+    const unsigned planeB = (unsigned)(H * Wp) * E;
+    const unsigned smA = (unsigned)__cvta_generic_to_shared(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    (void)E;
+
+    // Load the tile and its halo, P_i(y) into slot opp(i) of y.  Columns
+    // [ca, cb) are contiguous in global memory (no wrap); from its first
+    // 16-byte boundary va they move as nv chunks, every other column as one
+    // value (wrapped periodically).
+    const int ca = max(0, -gx0), cb = min(W, D.g.N0 - gx0);
+    int va = ca, nv = 0;
+    if (cb > ca) {
+        va = ca + (V4 - (s0 + ca) % V4) % V4;
+        nv = va < cb ? (cb - va) / V4 : 0;
+    }
+    if (nv == 0) va = 0;
+    const int vb = va + nv * V4, nsc = va + (W - vb);  // scalar columns: [0, va) and [vb, W)
+    const T *s = src + D.off;
+    for (int r = warp; r < H; r += NW) {
+        const T *grow = s + (int64_t)wrap_index(t.y0 - K + r, D.g.N1) * D.g.pitch;
+        const unsigned srow = smA + (unsigned)(r * Wp + s0) * E;
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int o = reflect_pop<L>(i, 3);
+            const T *g = grow + (int64_t)i * D.g.slab;
+            const unsigned a = srow + (unsigned)o * planeB;
+            for (int v = lane; v < nv; v += 32) cp_async_16(a + (unsigned)(va + v * V4) * E, g + gx0 + va + v * V4);
+            for (int j = lane; j < nsc; j += 32) {
+                const int c = j < va ? j : vb + (j - va);
+                const int gx = gx0 + c;
+                cp_async_elem(a + (unsigned)c * E, g + ((gx >= 0 && gx < D.g.N0) ? gx : wrap_index(gx, D.g.N0)));
+            }
+        });
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+
+    // K steps in place, alternating pull and local.  A slot's byte address is
+    // formed from the node's: population * planeB +- one row (rowB) +- one value.
+    const unsigned rowB = (unsigned)Wp * E;
+    for (int st = 0; st < K; ++st) {
+        // this thread's nodes of the RW x RH region: flat indices tid, tid + TH, ...
+        // walked as (row, column) without a division per node
+        const int m = st + 1, RW = W - 2 * m, RH = H - 2 * m;
+        const int dr = TH / RW, dc = TH - dr * RW;
+        const bool pull = (st & 1) == 0;
+        int r = (int)threadIdx.x / RW, c = (int)threadIdx.x - r * RW;
+        for (; r < RH; r += dr, c += dc) {
+            if (c >= RW) {
+                c -= RW;
+                ++r;
+                if (r >= RH) break;
+            }
+            const unsigned nb = smA + (unsigned)((r + m) * Wp + (c + m) + s0) * E;
+            T f[Q];
+            if (pull) {  // load from slot opp(i) of x - e_i, store to slot i of x + e_i
+                static_for<0, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    constexpr int ex = L::E[i][0], ey = L::E[i][1], o = reflect_pop<L>(i, 3);
+                    f[i] = lds<T>(nb + (unsigned)o * planeB - (unsigned)(ey * (int)rowB) - (unsigned)(ex * (int)E));
+                });
+                collide(L{}, f, D.k);
+                static_for<0, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    constexpr int ex = L::E[i][0], ey = L::E[i][1];
+                    sts(nb + (unsigned)i * planeB + (unsigned)(ey * (int)rowB) + (unsigned)(ex * (int)E), f[i]);
+                });
+            } else {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) f[i] = lds<T>(nb + (unsigned)i * planeB);
+                collide(L{}, f, D.k);
+                static_for<0, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    sts(nb + (unsigned)reflect_pop<L>(i, 3) * planeB, f[i]);
+                });
+            }
+        }
+        __syncthreads();
+    }
+
+    // Store the tile, P_i(z) for z in the tile: after an even number of steps
+    // from slot opp(i) of z, after an odd number from slot i of z + e_i.
+    // Populations read without an x shift move in 16-byte chunks from the
+    // first boundary on (global columns x0 .. x0 + tx share the alignment of
+    // buffer columns K .. K + tx), single values at the ends.
+    T *d = dst + D.off;
+    const bool odd = (K & 1) != 0;
+    const int wa = K + (V4 - (s0 + K) % V4) % V4;
+    const int nw = wa < K + t.tx ? (K + t.tx - wa) / V4 : 0;
+    const int wb = nw ? wa + nw * V4 : K, nse = nw ? (wa - K) + (K + t.tx - wb) : t.tx;
+    for (int r = warp; r < t.ty; r += NW) {
+        T *grow = d + (int64_t)(t.y0 + r) * D.g.pitch - K + t.x0;  // global row, indexed by buffer column
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int ex = L::E[i][0], ey = L::E[i][1], o = reflect_pop<L>(i, 3);
+            T *g = grow + (int64_t)i * D.g.slab;
+            const int sy = odd ? ey : 0, sx = odd ? ex : 0;
+            const unsigned a = smA + (unsigned)(odd ? i : o) * planeB + (unsigned)((r + K + sy) * Wp + s0 + sx) * E;
+            if (sx == 0) {
+                for (int v = lane; v < nw; v += 32)
+                    copy16_shared_to_global(g + wa + v * V4, a + (unsigned)(wa + v * V4) * E);
+                for (int j = lane; j < nse; j += 32) {
+                    const int c = nw ? (j < wa - K ? K + j : wb + (j - (wa - K))) : K + j;
+                    g[c] = lds<T>(a + (unsigned)c * E);
+                }
+            } else {
+                for (int c = K + lane; c < K + t.tx; c += 32) g[c] = lds<T>(a + (unsigned)c * E);
+            }
+        });
+    }
+}
+
 // Per-instance error sums: one block per instance, FP64, fixed order.
 __global__ void __launch_bounds__(kRedThreads) batch_errors_kernel(const int64_t *__restrict__ node_off,
                                                                    const double *__restrict__ th,
@@ -177,6 +407,11 @@ struct lb_batch {
     int threads = 256;
     bool use_graph = true;
     std::vector<Group> groups;
+    // temporal blocking (lb_batch_set_blocking): tb_k steps per launch; 0 = one launch per step
+    int tb_k = 0, tb_tile = 0, tb_threads = 512;
+    int ntiles = 0, tb_maxw = 0, tb_maxh = 0;  // tile count, largest tile (without halo)
+    lbk::TileDesc *d_tiles = nullptr;
+    cudaGraphExec_t tb_graph[2] = {nullptr, nullptr};  // kTbGraphLaunches blocked launches, by starting buffer
     bool initialized = false;
     std::string err;
 };
@@ -206,10 +441,24 @@ void free_groups(lb_batch *b)
     b->groups.clear();
 }
 
+void free_tiles(lb_batch *b)
+{
+    cudaFree(b->d_tiles);
+    b->d_tiles = nullptr;
+    for (auto &ge : b->tb_graph)
+        if (ge) {
+            cudaGraphExecDestroy(ge);
+            ge = nullptr;
+        }
+    b->ntiles = 0;
+    b->tb_k = 0;
+}
+
 void free_batch(lb_batch *b)
 {
     if (!b) return;
     free_groups(b);
+    free_tiles(b);
     cudaFree(b->buf[0]);
     cudaFree(b->buf[1]);
     cudaFree(b->d_desc);
@@ -253,6 +502,103 @@ cudaError_t launch_group(lb_batch *b, const Group &g, int from, cudaStream_t s)
             (const lbk::InstDesc<float> *)b->d_desc, g.d_blk_inst, g.d_blk_seg0, (const float *)b->buf[from],
             (float *)b->buf[from ^ 1]);
     return cudaGetLastError();
+}
+
+constexpr int kTbGraphLaunches = 16;  // blocked launches per recorded graph (even)
+
+template <typename T, int TH> const void *tb_kernel()
+{
+    return (const void *)lbk::batch_tb_kernel<lbk::D2Q9, T, TH>;
+}
+
+template <typename T> const void *tb_kernel_for(int threads)
+{
+    return threads == 256 ? tb_kernel<T, 256>() : (threads == 512 ? tb_kernel<T, 512>() : tb_kernel<T, 1024>());
+}
+
+const void *tb_kernel_of(const lb_batch *b, int threads)
+{
+    if (b->precision == LB_FP64) return tb_kernel_for<double>(threads);
+    if (b->precision == LB_FX64) return tb_kernel_for<long long>(threads);
+    return tb_kernel_for<float>(threads);
+}
+
+size_t tb_smem(const lb_batch *b, int K)
+{
+    return lbk::tb_smem_bytes(9, (int)b->elem, b->tb_maxw + 2 * K, b->tb_maxh + 2 * K);
+}
+
+// One blocked launch of K steps over every tile, from buffer `from`.
+cudaError_t launch_tb(lb_batch *b, int from, int K, cudaStream_t s)
+{
+    void *args[] = {&b->d_desc, &b->d_tiles, &b->buf[from], &b->buf[from ^ 1], &K};
+    return cudaLaunchKernel(tb_kernel_of(b, b->tb_threads), dim3((unsigned)b->ntiles), dim3((unsigned)b->tb_threads),
+                            args, tb_smem(b, K), s);
+}
+
+// Tile every instance for blocked launches of K steps: an axis of N nodes is
+// cut into ceil(N / tile) near-equal tiles.  The largest tile plus its halo
+// must fit the device's shared memory per block.
+lb_status build_tiles(lb_batch *b, int K, int tile, int threads)
+{
+    cudaError_t e = cudaStreamSynchronize(b->stream);  // tables and graphs may be in use
+    if (e != cudaSuccess) return bcuda(b, e, "lb_batch_set_blocking");
+    free_tiles(b);
+    if (K == 0) return LB_OK;
+    std::vector<lbk::TileDesc> tv;
+    int maxw = 0, maxh = 0;
+    for (int j = 0; j < b->count; ++j) {
+        const int n0 = (int)b->inst[j].N[0], n1 = (int)b->inst[j].N[1];
+        const int ntx = (n0 + tile - 1) / tile, nty = (n1 + tile - 1) / tile;
+        const int tx = (n0 + ntx - 1) / ntx, ty = (n1 + nty - 1) / nty;
+        maxw = std::max(maxw, tx);
+        maxh = std::max(maxh, ty);
+        for (int y0 = 0; y0 < n1; y0 += ty)
+            for (int x0 = 0; x0 < n0; x0 += tx) tv.push_back({j, x0, y0, std::min(tx, n0 - x0), std::min(ty, n1 - y0)});
+    }
+    if (tv.size() > 0x7fffffff) return bfail(b, LB_EINVAL, "lb_batch_set_blocking: too many tiles");
+    int optin = 0;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device)) != cudaSuccess)
+        return bcuda(b, e, "lb_batch_set_blocking");
+    const size_t need = lbk::tb_smem_bytes(9, (int)b->elem, maxw + 2 * K, maxh + 2 * K);
+    if (need > (size_t)optin)
+        return bfail(b, LB_EINVAL, "lb_batch_set_blocking: tile plus halo exceeds the shared memory per block");
+    if ((e = cudaFuncSetAttribute(tb_kernel_of(b, threads), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)need)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_tiles, sizeof(lbk::TileDesc) * tv.size())) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_tiles, tv.data(), sizeof(lbk::TileDesc) * tv.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+        return bcuda(b, e, "lb_batch_set_blocking: tile table");
+    b->ntiles = (int)tv.size();
+    b->tb_maxw = maxw;
+    b->tb_maxh = maxh;
+    b->tb_k = K;
+    b->tb_tile = tile;
+    b->tb_threads = threads;
+    return LB_OK;
+}
+
+// Record kTbGraphLaunches blocked launches of tb_k steps starting from buffer `from`.
+cudaError_t record_tb_graph(lb_batch *b, int from)
+{
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        int p = from;
+        for (int k = 0; k < kTbGraphLaunches && e == cudaSuccess; ++k) {
+            e = launch_tb(b, p, b->tb_k, cs);
+            p ^= 1;
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->tb_graph[from], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    return e;
 }
 
 // Build groups and block tables for (budget, threads).  budget <= 0: every
@@ -333,6 +679,27 @@ cudaError_t record_graph(lb_batch *b, Group &g, int from)
 cudaError_t run_steps(lb_batch *b, int64_t n)
 {
     cudaError_t e = cudaSuccess;
+    if (b->tb_k > 0) {
+        // blocked: launches of tb_k steps (recorded in graphs), then one launch for the remainder
+        int64_t launches = n / b->tb_k;
+        const int rem = (int)(n % b->tb_k);
+        if (b->use_graph) {
+            while (launches >= kTbGraphLaunches) {
+                if (!b->tb_graph[b->cur] && (e = record_tb_graph(b, b->cur)) != cudaSuccess) return e;
+                if ((e = cudaGraphLaunch(b->tb_graph[b->cur], b->stream)) != cudaSuccess) return e;
+                launches -= kTbGraphLaunches;  // even: parity unchanged
+            }
+        }
+        for (; launches > 0; --launches) {
+            if ((e = launch_tb(b, b->cur, b->tb_k, b->stream)) != cudaSuccess) return e;
+            b->cur ^= 1;
+        }
+        if (rem > 0) {
+            if ((e = launch_tb(b, b->cur, rem, b->stream)) != cudaSuccess) return e;
+            b->cur ^= 1;
+        }
+        return cudaSuccess;
+    }
     for (Group &g : b->groups) {
         int p = b->cur;
         int64_t left = n;
@@ -576,50 +943,81 @@ lb_status lb_batch_autotune(lb_batch *b, int trial_steps, double *choice)
 {
     lbk::NvtxRange nvtx_range("lb_batch_autotune");
     if (!b || trial_steps < 2) return LB_EINVAL;
-    // one instance per group is the naive baseline and never the fastest; it is
-    // left out of the search (lb_batch_set_schedule can still select it)
-    const double budgets[] = {48e6, 96e6, 128e6, 1e18};
-    const int threads[] = {64, 128, 256, 512};
-    double best = 1e300, best_b = b->budget;
-    int best_t = b->threads;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, LB_ECUDA, "lb_batch_autotune: sync");
+    // Candidates: (a) one launch per step per group (byte budget x block
+    // size); one instance per group is the naive baseline and never the
+    // fastest, so it is left out (lb_batch_set_schedule can still select it);
+    // (b) blocked launches: K steps per launch x tile edge (the largest that
+    // fits one, or two, blocks per SM with a K-node halo) x block size.
+    struct Cand {
+        double budget;
+        int threads, K, tile;
+    };
+    std::vector<Cand> cands;
+    for (double bud : {48e6, 96e6, 128e6, 1e18})
+        for (int th : {64, 128, 256, 512}) cands.push_back({bud, th, 0, 0});
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess)
+        return bfail(b, LB_ECUDA, "lb_batch_autotune: device attribute");
+    for (int K : {2, 4, 6, 8, 12})
+        for (int per_sm : {1, 2}) {
+            const size_t avail = per_sm == 1 ? (size_t)optin : (size_t)optin / 2 - 1024;
+            int edge = 1;  // largest square tile + halo whose buffers fit
+            while (lbk::tb_smem_bytes(9, (int)b->elem, edge + 1, edge + 1) <= avail) ++edge;
+            const int tile = edge - 2 * K;
+            if (tile < 8) continue;
+            for (int th : {256, 512, 1024}) cands.push_back({b->budget, th, K, tile});
+        }
+    double best = 1e300;
+    Cand win = {b->budget, b->threads, b->tb_k, b->tb_tile};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bfail(b, LB_ECUDA, "lb_batch_autotune: events");
     lb_status st = LB_OK;
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, LB_ECUDA, "lb_batch_autotune: sync");
-    for (double bud : budgets) {
-        for (int th : threads) {
-            if ((st = build_schedule(b, bud, th, true)) != LB_OK) break;
-            cudaError_t e = run_steps(b, trial_steps);  // warm-up: records the graphs, fills L2
-            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-            if (e == cudaSuccess) e = run_steps(b, trial_steps);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                st = bcuda(b, e, "lb_batch_autotune");
+    for (const Cand &cd : cands) {
+        if (cd.K == 0) {
+            if ((st = build_tiles(b, 0, 0, 0)) != LB_OK || (st = build_schedule(b, cd.budget, cd.threads, true)) != LB_OK)
                 break;
-            }
-            if (ms < best) {
-                best = ms;
-                best_b = bud;
-                best_t = th;
-            }
+        } else if ((st = build_tiles(b, cd.K, cd.tile, cd.threads)) != LB_OK) {
+            st = LB_OK;  // a tile that does not fit this device is skipped
+            continue;
         }
-        if (st != LB_OK) break;
+        const int64_t n = cd.K ? (trial_steps + cd.K - 1) / cd.K * cd.K : trial_steps;
+        cudaError_t e = run_steps(b, n);  // warm-up: records the graphs, fills L2
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) e = run_steps(b, n);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            st = bcuda(b, e, "lb_batch_autotune");
+            break;
+        }
+        const double per_step = ms / (double)n;
+        if (per_step < best) {
+            best = per_step;
+            win = cd;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != LB_OK) return st;
     b->initialized = false;  // the trials overwrote the state
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, LB_ECUDA, "lb_batch_autotune: sync");
-    if ((st = build_schedule(b, best_b, best_t, true)) != LB_OK) return st;
+    if (win.K == 0) {
+        if ((st = build_tiles(b, 0, 0, 0)) != LB_OK) return st;
+        if ((st = build_schedule(b, win.budget, win.threads, true)) != LB_OK) return st;
+    } else if ((st = build_tiles(b, win.K, win.tile, win.threads)) != LB_OK) {
+        return st;
+    }
     if (choice) {
-        choice[0] = best_b;
-        choice[1] = best_t;
+        choice[0] = b->budget;
+        choice[1] = win.K ? win.threads : b->threads;
         choice[2] = (double)b->groups.size();
-        choice[3] = 1e3 * best / trial_steps;
+        choice[3] = 1e3 * best;
+        choice[4] = win.K;
+        choice[5] = win.tile;
     }
     return LB_OK;
 }
@@ -630,16 +1028,31 @@ lb_status lb_batch_set_schedule(lb_batch *b, double budget, int threads, int use
         return LB_EINVAL;
     cudaError_t e = cudaStreamSynchronize(b->stream);  // tables in use by queued launches
     if (e != cudaSuccess) return bcuda(b, e, "lb_batch_set_schedule");
+    free_tiles(b);
     return build_schedule(b, budget, threads, use_graph != 0);
+}
+
+lb_status lb_batch_set_blocking(lb_batch *b, int steps_per_launch, int tile, int threads, int use_graph)
+{
+    if (!b) return LB_EINVAL;
+    if (steps_per_launch < 0 || steps_per_launch > 64 || (steps_per_launch > 0 && (tile < 1 || tile > 4096)) ||
+        (steps_per_launch > 0 && !(threads == 256 || threads == 512 || threads == 1024)))
+        return bfail(b, LB_EINVAL, "lb_batch_set_blocking: steps per launch in 0..64, tile >= 1, threads 256, 512 or 1024");
+    lb_status st = build_tiles(b, steps_per_launch, tile, threads);
+    if (st == LB_OK) b->use_graph = use_graph != 0;
+    return st;
 }
 
 lb_status lb_batch_schedule(const lb_batch *b, double *info)
 {
     if (!b || !info) return LB_EINVAL;
     info[0] = b->budget;
-    info[1] = b->threads;
+    info[1] = b->tb_k ? b->tb_threads : b->threads;
     info[2] = (double)b->groups.size();
     info[3] = (double)b->total_nodes;
+    info[4] = b->tb_k;
+    info[5] = b->tb_k ? b->tb_tile : 0;
+    info[6] = b->ntiles;
     return LB_OK;
 }
 

@@ -411,6 +411,7 @@ _batch_sigs = {
     "lb_batch_autotune": (["vp", "i", "pd"], "i"),
     "lb_batch_set_schedule": (["vp", "d", "i", "i"], "i"),
     "lb_batch_schedule": (["vp", "pd"], "i"),
+    "lb_batch_set_blocking": (["vp", "i", "i", "i", "i"], "i"),
     "lb_batch_last_error": (["vp"], "s"),
 }
 
@@ -502,17 +503,22 @@ class Batch:
         return np.array(list(buf)).reshape(self.count, 4)
 
     def autotune(self, trial_steps=10):
-        buf = (ctypes.c_double * 4)()
+        buf = (ctypes.c_double * 6)()
         self._call("lb_batch_autotune", int(trial_steps), buf)
-        return {"budget_bytes": buf[0], "threads": int(buf[1]), "groups": int(buf[2]), "us_per_step": buf[3]}
+        return {"budget_bytes": buf[0], "threads": int(buf[1]), "groups": int(buf[2]), "us_per_step": buf[3],
+                "steps_per_launch": int(buf[4]), "tile": int(buf[5])}
 
     def set_schedule(self, budget_bytes, threads=256, use_graph=True):
         self._call("lb_batch_set_schedule", float(budget_bytes), int(threads), int(bool(use_graph)))
 
+    def set_blocking(self, steps_per_launch, tile=40, threads=512, use_graph=True):
+        self._call("lb_batch_set_blocking", int(steps_per_launch), int(tile), int(threads), int(bool(use_graph)))
+
     def schedule(self):
-        buf = (ctypes.c_double * 4)()
+        buf = (ctypes.c_double * 7)()
         self._call("lb_batch_schedule", buf)
-        return {"budget_bytes": buf[0], "threads": int(buf[1]), "groups": int(buf[2]), "nodes": int(buf[3])}
+        return {"budget_bytes": buf[0], "threads": int(buf[1]), "groups": int(buf[2]), "nodes": int(buf[3]),
+                "steps_per_launch": int(buf[4]), "tile": int(buf[5]), "tiles": int(buf[6])}
 
     def split(self, flat, comps=1):
         """Per-instance views (shape (comps, N1, N0) or (N1, N0)) of a concatenated field."""

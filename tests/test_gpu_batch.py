@@ -57,6 +57,50 @@ def test_batch_equals_single_instance_bitwise(precision, sched):
         assert torch.equal(us[j], u1), j
 
 
+# blocked launches (steps per launch, tile edge, threads): tiles wider and
+# narrower than the instances, tiles that do not divide them, a remainder
+# launch (37 = 9 x 4 + 1, 12 x 3 + 1, 4 x 8 + 5), graphs of 16 launches
+# (1 step per launch)
+BLOCKED = [(4, 28, 512), (3, 17, 256), (8, 22, 1024), (1, 33, 256), (2, 5, 512)]
+
+
+@pytest.mark.parametrize("precision,blk", [(p, b) for p in ("fp32s", "fp64", "fx64") for b in BLOCKED]
+                         + [("fp32s", (4, 48, 1024)), ("fp32s", (6, 40, 512))])
+def test_blocked_batch_equals_single_instance_bitwise(precision, blk):
+    """K steps per launch in shared memory: every instance still evolves bit
+    for bit as the single-grid solver does, across remainder launches, graph
+    replays and a switch back to one launch per step."""
+    probs, dxs, dts, th0, g0 = _setup()
+    b = lb.Batch(SIZES, NUS, dxs, dts, precision=precision, theta_ref=[1.5] * len(SIZES))
+    b.set_blocking(*blk)
+    sch = b.schedule()
+    assert sch["steps_per_launch"] == blk[0] and sch["tile"] == blk[1] and sch["tiles"] > 0
+    b.set_theta0(torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda())
+    b.step(37)
+    b.set_schedule(96e6, 128, True)
+    b.step(3)
+    b.set_blocking(*blk)
+    b.step(20)
+    n = 60
+    th, u = b.macros()
+    ths, us = b.split(th), b.split(u, 2)
+    for j in range(len(SIZES)):
+        t1, u1 = _single(j, probs[j], dxs[j], dts[j], n, precision, 1.5)
+        assert torch.equal(ths[j], t1), j
+        assert torch.equal(us[j], u1), j
+
+
+def test_blocked_rejects_tiles_beyond_shared_memory():
+    probs, dxs, dts, th0, g0 = _setup()
+    b = lb.Batch(SIZES, NUS, dxs, dts, precision="fx64")
+    with pytest.raises(lb.LBError) as ei:
+        b.set_blocking(8, 200, 512)
+    assert ei.value.status == lb.LB_EINVAL
+    with pytest.raises(lb.LBError) as ei:
+        b.set_blocking(4, 20, 300)
+    assert ei.value.status == lb.LB_EINVAL
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fx64"])
 def test_batch_fp64_matches_oracle(precision):
     probs, dxs, dts, th0, g0 = _setup(11)
@@ -78,7 +122,8 @@ def test_batch_autotune_and_errors():
     probs, dxs, dts, th0, g0 = _setup(3)
     b = lb.Batch(SIZES, NUS, dxs, dts, precision="fp32s", theta_ref=[1.5] * len(SIZES))
     choice = b.autotune(4)
-    assert choice["threads"] in (64, 128, 256, 512) and choice["groups"] >= 1 and choice["us_per_step"] > 0
+    assert choice["threads"] in (64, 128, 256, 512, 1024) and choice["groups"] >= 1 and choice["us_per_step"] > 0
+    assert choice["steps_per_launch"] in (0, 2, 4, 6, 8, 12)
     b.set_theta0(torch.from_numpy(th0).cuda(), torch.from_numpy(g0).cuda())
     n = 40
     b.step(n)
