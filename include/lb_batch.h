@@ -92,8 +92,8 @@ lb_status lb_batch_errors(lb_batch *b, const double *theta, const double *u, con
  *  - one launch per step: group byte budget 48, 96, 128 MB or all instances
  *    in one group, x 64, 128, 256 or 512 threads per block;
  *  - blocked: K = 2, 4, 6, 8 or 12 steps per launch x the largest square tile
- *    whose two buffers (with the K-node halo) fit one, or two, blocks per SM
- *    x 256, 512 or 1024 threads per block.
+ *    whose buffer (with the K-node halo) fits one, two, three or four blocks
+ *    per SM x 256, 512 or 1024 threads per block.
  * Must be called before lb_batch_set_theta0 (it overwrites the state).
  * choice (host, may be NULL) receives {budget_bytes, threads_per_block,
  * groups, microseconds per step of the winner, steps per launch (0: one

@@ -106,8 +106,7 @@ struct TileDesc {
     int tx, ty;    // tile size (nodes)
 };
 
-// Asynchronous global -> shared copies at 32-bit shared addresses: one value,
-// or one 16-byte chunk (both addresses 16-byte aligned).
+// Asynchronous global -> shared copy of one value at a 32-bit shared address.
 template <typename T> __device__ __forceinline__ void cp_async_elem(unsigned dst, const T *src)
 {
     if constexpr (sizeof(T) == 4)
@@ -115,43 +114,31 @@ template <typename T> __device__ __forceinline__ void cp_async_elem(unsigned dst
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_16(unsigned dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
 
-// Shared-memory loads and stores at 32-bit shared addresses.
-template <typename T> __device__ __forceinline__ T lds(unsigned a);
-template <> __device__ __forceinline__ float lds<float>(unsigned a)
+// Shared-memory loads and stores at a 32-bit shared address plus a
+// compile-time byte offset.
+template <typename T, int OFF> __device__ __forceinline__ T lds(unsigned a)
 {
-    float v;
-    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    T v;
+    if constexpr (std::is_same<T, float>::value)
+        asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF) : "memory");
+    else if constexpr (std::is_same<T, double>::value)
+        asm volatile("ld.shared.f64 %0, [%1+%2];" : "=d"(v) : "r"(a), "n"(OFF) : "memory");
+    else
+        asm volatile("ld.shared.s64 %0, [%1+%2];" : "=l"(v) : "r"(a), "n"(OFF) : "memory");
     return v;
 }
-template <> __device__ __forceinline__ double lds<double>(unsigned a)
+template <int OFF> __device__ __forceinline__ void sts(unsigned a, float v)
 {
-    double v;
-    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
-    return v;
+    asm volatile("st.shared.f32 [%0+%1], %2;" ::"r"(a), "n"(OFF), "f"(v) : "memory");
 }
-template <> __device__ __forceinline__ long long lds<long long>(unsigned a)
+template <int OFF> __device__ __forceinline__ void sts(unsigned a, double v)
 {
-    long long v;
-    asm volatile("ld.shared.s64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
-    return v;
+    asm volatile("st.shared.f64 [%0+%1], %2;" ::"r"(a), "n"(OFF), "d"(v) : "memory");
 }
-__device__ __forceinline__ void sts(unsigned a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory"); }
-__device__ __forceinline__ void sts(unsigned a, double v) { asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory"); }
-__device__ __forceinline__ void sts(unsigned a, long long v)
+template <int OFF> __device__ __forceinline__ void sts(unsigned a, long long v)
 {
-    asm volatile("st.shared.s64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
-}
-// 16 bytes from shared memory to global memory (both 16-byte aligned).
-__device__ __forceinline__ void copy16_shared_to_global(void *g, unsigned a)
-{
-    unsigned x, y, z, w;
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(a) : "memory");
-    asm volatile("st.global.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(g), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+    asm volatile("st.shared.s64 [%0+%1], %2;" ::"r"(a), "n"(OFF), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ int wrap_index(int v, int n)
@@ -160,110 +147,98 @@ __device__ __forceinline__ int wrap_index(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-// Shared-memory layout of a blocked tile: rows of W = tx + 2K values (the
-// tile with its halo) at a pitch of Wp values, shifted by s0 values so that
-// every row has the same alignment modulo 16 bytes as its source row in
-// global memory (the middle of each row then moves in 16-byte chunks).
-__host__ __device__ inline int tb_pitch(int W, int elem)
-{
-    const int V4 = 16 / elem;
-    return (W + V4 - 1 + V4 - 1) / V4 * V4;  // room for any shift s0 < V4
-}
-// Dynamic shared memory of a blocked launch: one Q-population buffer.
+// Shared-memory layout of a blocked tile: W = tx + 2K by H = ty + 2K nodes,
+// row-major, each node's Q values contiguous (Q sizeof(T) bytes: an odd
+// number of 4-byte words for D2Q9, so a warp's 32 consecutive nodes hit 32
+// different banks).  Every slot of a node and of its row neighbours is then
+// a compile-time offset from one of three row bases.
 __host__ __device__ inline size_t tb_smem_bytes(int q, int elem, int W, int H)
 {
-    return (size_t)q * tb_pitch(W, elem) * H * elem;
+    return (size_t)q * W * H * elem;
 }
 
 template <class L, typename T, int TH>
 __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1) batch_tb_kernel(const InstDesc<T> *__restrict__ inst,
-                                                         const TileDesc *__restrict__ tiles, const T *__restrict__ src,
-                                                         T *__restrict__ dst, int K)
+                                                                     const TileDesc *__restrict__ tiles,
+                                                                     const T *__restrict__ src, T *__restrict__ dst,
+                                                                     int K)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int Q = L::Q, NW = TH / 32;
-    constexpr unsigned E = sizeof(T);
-    constexpr int V4 = 16 / (int)E;  // values per 16-byte chunk
+    constexpr int E = (int)sizeof(T), NB = Q * E;  // bytes per value, per node
     const TileDesc t = tiles[blockIdx.x];
     const InstDesc<T> D = inst[t.inst];
     const int W = t.tx + 2 * K, H = t.ty + 2 * K;
-    const int gx0 = t.x0 - K;                 // global column of shared column 0 (may be < 0)
-    const int s0 = ((gx0 % V4) + V4) % V4;    // shift: shared column c sits at s0 + c
-    const int Wp = (s0 + W + V4 - 1) / V4 * V4;
-    const unsigned planeB = (unsigned)(H * Wp) * E;
+    const int gx0 = t.x0 - K;  // global column of tile column 0 (may be < 0)
     const unsigned smA = (unsigned)__cvta_generic_to_shared(smem_raw);
+    const unsigned rowB = (unsigned)(W * NB);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    (void)E;
 
-    // Load the tile and its halo, P_i(y) into slot opp(i) of y.  Columns
-    // [ca, cb) are contiguous in global memory (no wrap); from its first
-    // 16-byte boundary va they move as nv chunks, every other column as one
-    // value (wrapped periodically).
-    const int ca = max(0, -gx0), cb = min(W, D.g.N0 - gx0);
-    int va = ca, nv = 0;
-    if (cb > ca) {
-        va = ca + (V4 - (s0 + ca) % V4) % V4;
-        nv = va < cb ? (cb - va) / V4 : 0;
-    }
-    if (nv == 0) va = 0;
-    const int vb = va + nv * V4, nsc = va + (W - vb);  // scalar columns: [0, va) and [vb, W)
+    // Load the tile and its halo, P_i(y) into slot opp(i) of y (periodic wrap).
     const T *s = src + D.off;
+    const bool inner = gx0 >= 0 && gx0 + W <= D.g.N0;  // no column of this tile wraps
     for (int r = warp; r < H; r += NW) {
         const T *grow = s + (int64_t)wrap_index(t.y0 - K + r, D.g.N1) * D.g.pitch;
-        const unsigned srow = smA + (unsigned)(r * Wp + s0) * E;
-        static_for<0, Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            constexpr int o = reflect_pop<L>(i, 3);
-            const T *g = grow + (int64_t)i * D.g.slab;
-            const unsigned a = srow + (unsigned)o * planeB;
-            for (int v = lane; v < nv; v += 32) cp_async_16(a + (unsigned)(va + v * V4) * E, g + gx0 + va + v * V4);
-            for (int j = lane; j < nsc; j += 32) {
-                const int c = j < va ? j : vb + (j - va);
-                const int gx = gx0 + c;
-                cp_async_elem(a + (unsigned)c * E, g + ((gx >= 0 && gx < D.g.N0) ? gx : wrap_index(gx, D.g.N0)));
-            }
-        });
+        const unsigned srow = smA + (unsigned)r * rowB;
+        for (int c = lane; c < W; c += 32) {
+            int gx = gx0 + c;
+            if (!inner) gx = wrap_index(gx, D.g.N0);
+            const unsigned a = srow + (unsigned)(c * NB);
+            static_for<0, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                cp_async_elem(a + (unsigned)(reflect_pop<L>(i, 3) * E), grow + (int64_t)i * D.g.slab + gx);
+            });
+        }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
 
-    // K steps in place, alternating pull and local.  A slot's byte address is
-    // formed from the node's: population * planeB +- one row (rowB) +- one value.
-    const unsigned rowB = (unsigned)Wp * E;
+    // K steps in place, alternating pull and local.
     for (int st = 0; st < K; ++st) {
-        // this thread's nodes of the RW x RH region: flat indices tid, tid + TH, ...
-        // walked as (row, column) without a division per node
+        // this thread's nodes of the RW x RH region: flat indices tid, tid + TH,
+        // ... walked as (row, column) without a division per node
         const int m = st + 1, RW = W - 2 * m, RH = H - 2 * m;
         const int dr = TH / RW, dc = TH - dr * RW;
-        const bool pull = (st & 1) == 0;
         int r = (int)threadIdx.x / RW, c = (int)threadIdx.x - r * RW;
-        for (; r < RH; r += dr, c += dc) {
-            if (c >= RW) {
-                c -= RW;
-                ++r;
-                if (r >= RH) break;
-            }
-            const unsigned nb = smA + (unsigned)((r + m) * Wp + (c + m) + s0) * E;
-            T f[Q];
-            if (pull) {  // load from slot opp(i) of x - e_i, store to slot i of x + e_i
+        if ((st & 1) == 0) {  // pull: load from slot opp(i) of x - e_i, store to slot i of x + e_i
+            for (; r < RH; r += dr, c += dc) {
+                if (c >= RW) {
+                    c -= RW;
+                    ++r;
+                    if (r >= RH) break;
+                }
+                const unsigned nb = smA + (unsigned)((r + m) * W + (c + m)) * NB;
+                const unsigned rb[3] = {nb - rowB, nb, nb + rowB};  // rows y - 1, y, y + 1
+                T f[Q];
                 static_for<0, Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
                     constexpr int ex = L::E[i][0], ey = L::E[i][1], o = reflect_pop<L>(i, 3);
-                    f[i] = lds<T>(nb + (unsigned)o * planeB - (unsigned)(ey * (int)rowB) - (unsigned)(ex * (int)E));
+                    f[i] = lds<T, (-ex * Q + o) * E>(rb[1 - ey]);
                 });
                 collide(L{}, f, D.k);
                 static_for<0, Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
                     constexpr int ex = L::E[i][0], ey = L::E[i][1];
-                    sts(nb + (unsigned)i * planeB + (unsigned)(ey * (int)rowB) + (unsigned)(ex * (int)E), f[i]);
+                    sts<(ex * Q + i) * E>(rb[1 + ey], f[i]);
                 });
-            } else {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) f[i] = lds<T>(nb + (unsigned)i * planeB);
+            }
+        } else {  // local: load from slot i of x, store to slot opp(i) of x
+            for (; r < RH; r += dr, c += dc) {
+                if (c >= RW) {
+                    c -= RW;
+                    ++r;
+                    if (r >= RH) break;
+                }
+                const unsigned nb = smA + (unsigned)((r + m) * W + (c + m)) * NB;
+                T f[Q];
+                static_for<0, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    f[i] = lds<T, i * E>(nb);
+                });
                 collide(L{}, f, D.k);
                 static_for<0, Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
-                    sts(nb + (unsigned)reflect_pop<L>(i, 3) * planeB, f[i]);
+                    sts<reflect_pop<L>(i, 3) * E>(nb, f[i]);
                 });
             }
         }
@@ -272,33 +247,21 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1) batch_tb_kernel(const I
 
     // Store the tile, P_i(z) for z in the tile: after an even number of steps
     // from slot opp(i) of z, after an odd number from slot i of z + e_i.
-    // Populations read without an x shift move in 16-byte chunks from the
-    // first boundary on (global columns x0 .. x0 + tx share the alignment of
-    // buffer columns K .. K + tx), single values at the ends.
     T *d = dst + D.off;
     const bool odd = (K & 1) != 0;
-    const int wa = K + (V4 - (s0 + K) % V4) % V4;
-    const int nw = wa < K + t.tx ? (K + t.tx - wa) / V4 : 0;
-    const int wb = nw ? wa + nw * V4 : K, nse = nw ? (wa - K) + (K + t.tx - wb) : t.tx;
     for (int r = warp; r < t.ty; r += NW) {
-        T *grow = d + (int64_t)(t.y0 + r) * D.g.pitch - K + t.x0;  // global row, indexed by buffer column
-        static_for<0, Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            constexpr int ex = L::E[i][0], ey = L::E[i][1], o = reflect_pop<L>(i, 3);
-            T *g = grow + (int64_t)i * D.g.slab;
-            const int sy = odd ? ey : 0, sx = odd ? ex : 0;
-            const unsigned a = smA + (unsigned)(odd ? i : o) * planeB + (unsigned)((r + K + sy) * Wp + s0 + sx) * E;
-            if (sx == 0) {
-                for (int v = lane; v < nw; v += 32)
-                    copy16_shared_to_global(g + wa + v * V4, a + (unsigned)(wa + v * V4) * E);
-                for (int j = lane; j < nse; j += 32) {
-                    const int c = nw ? (j < wa - K ? K + j : wb + (j - (wa - K))) : K + j;
-                    g[c] = lds<T>(a + (unsigned)c * E);
-                }
-            } else {
-                for (int c = K + lane; c < K + t.tx; c += 32) g[c] = lds<T>(a + (unsigned)c * E);
-            }
-        });
+        T *grow = d + (int64_t)(t.y0 + r) * D.g.pitch + t.x0;
+        const unsigned rb[3] = {smA + (unsigned)(r + K - 1) * rowB, smA + (unsigned)(r + K) * rowB,
+                                smA + (unsigned)(r + K + 1) * rowB};
+        for (int c = lane; c < t.tx; c += 32) {
+            const unsigned cb = (unsigned)((c + K) * NB);
+            static_for<0, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int ex = L::E[i][0], ey = L::E[i][1], o = reflect_pop<L>(i, 3);
+                const T v = odd ? lds<T, (ex * Q + i) * E>(rb[1 + ey] + cb) : lds<T, o * E>(rb[1] + cb);
+                grow[(int64_t)i * D.g.slab + c] = v;
+            });
+        }
     }
 }
 
@@ -948,7 +911,8 @@ lb_status lb_batch_autotune(lb_batch *b, int trial_steps, double *choice)
     // size); one instance per group is the naive baseline and never the
     // fastest, so it is left out (lb_batch_set_schedule can still select it);
     // (b) blocked launches: K steps per launch x tile edge (the largest that
-    // fits one, or two, blocks per SM with a K-node halo) x block size.
+    // fits one, two, three or four blocks per SM with a K-node halo) x block
+    // size.
     struct Cand {
         double budget;
         int threads, K, tile;
@@ -960,8 +924,8 @@ lb_status lb_batch_autotune(lb_batch *b, int trial_steps, double *choice)
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess)
         return bfail(b, LB_ECUDA, "lb_batch_autotune: device attribute");
     for (int K : {2, 4, 6, 8, 12})
-        for (int per_sm : {1, 2}) {
-            const size_t avail = per_sm == 1 ? (size_t)optin : (size_t)optin / 2 - 1024;
+        for (int per_sm : {1, 2, 3, 4}) {
+            const size_t avail = per_sm == 1 ? (size_t)optin : (size_t)optin / per_sm - 1024;
             int edge = 1;  // largest square tile + halo whose buffers fit
             while (lbk::tb_smem_bytes(9, (int)b->elem, edge + 1, edge + 1) <= avail) ++edge;
             const int tile = edge - 2 * K;
