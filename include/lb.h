@@ -184,6 +184,45 @@ lb_status lb_set_theta0(lb_ctx *ctx, const double *theta0, const double *grad_th
  */
 lb_status lb_step(lb_ctx *ctx, int64_t nsteps);
 
+/*
+ * Temporally blocked sweeps (periodic 2D grids).  The sweep of lb_step reads
+ * and writes the whole state every step, so it is bound by HBM bandwidth.
+ * With blocking, each launch advances K steps: a block loads one tile of
+ * the grid with a K-node periodic halo into shared memory, runs the same
+ * pull + collide K times there (one shared buffer, updated in place: steps
+ * alternate between pulling from the neighbours' slots and updating a
+ * node's own slots, and each node reads exactly the slots it writes) and
+ * stores the tile, so HBM is read and written once per K steps; the halo
+ * nodes are recomputed.  Results are bit-identical to lb_step's one sweep per
+ * launch.  For LB_FX64 the range check (|f| < 2^61) covers the values
+ * stored at the end of every launch.
+ *   steps_per_launch  K in 1..64, or 0 for one sweep per launch (default).
+ *   tile     each axis of N nodes is cut into ceil(N / tile) near-equal tiles;
+ *            the largest tile plus its halo, 9 values per node, must fit the
+ *            device's shared memory per block.
+ *   threads  256, 512 or 1024 per block.
+ * Synchronises the stream; keeps the state.  lb_set_boundary with a mirror
+ * axis returns the context to one sweep per launch.
+ * Errors: LB_EINVAL (out of range, d != 2, walls, or a tile too large), LB_ECUDA.
+ */
+lb_status lb_set_blocking(lb_ctx *ctx, int steps_per_launch, int tile, int threads);
+
+/* Current blocking, info[0..3] (host): {steps per launch (0: none), tile, threads, tiles}. */
+lb_status lb_get_blocking(const lb_ctx *ctx, int *info);
+
+/*
+ * Times about trial_steps steps (rounded up to whole launches) for one sweep
+ * per launch and for blocked sweeps (K = 2, 4, 6, 8, 12 x the largest square
+ * tile that fits one to four blocks per SM x 256, 512, 1024 threads) on this
+ * grid and keeps the fastest (lb_set_blocking).  The trials overwrite the
+ * state: call lb_set_theta0 afterwards.  A grid that blocking does not cover
+ * (d != 2, walls) keeps one sweep per launch.  choice (host, may be NULL)
+ * receives {steps per launch (0: one sweep per launch), tile, threads,
+ * microseconds per step of the winner}.  Synchronises the stream.
+ * Errors: LB_EINVAL, LB_ECUDA.
+ */
+lb_status lb_autotune(lb_ctx *ctx, int trial_steps, double *choice);
+
 /* Number of steps taken since the last lb_set_theta0 (host, no sync). */
 lb_status lb_get_step(const lb_ctx *ctx, int64_t *nsteps);
 

@@ -7,6 +7,7 @@
 
 #include <new>
 #include <string>
+#include <vector>
 
 #include "lb_internal.cuh"
 
@@ -35,6 +36,7 @@ bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 void free_ctx(lb_ctx *c)
 {
     if (!c) return;
+    lbk::blocked_release(c);
     for (auto &g : c->graph)
         if (g) cudaGraphExecDestroy(g);
     cudaFree(c->f[0]);
@@ -112,6 +114,31 @@ lb_status read_flags(lb_ctx *c, const char *who)
     }
     if (fl[0]) return fail(c, LB_ENONPOS, w + ": theta <= 0 or non-finite at some node");
     return LB_OK;
+}
+
+constexpr int64_t kTbGraphLaunches = 16;  // blocked launches per recorded graph (even)
+
+// Record kTbGraphLaunches blocked launches of tb_k steps starting from buffer `from`.
+cudaError_t record_blocked(lb_ctx *c, int from)
+{
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        int p = from;
+        for (int64_t k = 0; k < kTbGraphLaunches && e == cudaSuccess; ++k) {
+            e = lbk::blocked_launch(c, c->f[p], c->f[p ^ 1], c->tb_k, cs);
+            p ^= 1;
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->tb_graph[from], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    return e;
 }
 
 bool capturing(cudaStream_t s)
@@ -282,6 +309,7 @@ lb_status lb_set_boundary(lb_ctx *c, const int *kind)
         }
     c->geom.mirror = mask;
     c->initialized = false;  // the stored state follows the old walls: initialise again
+    if (mask) lbk::blocked_release(c);  // blocked sweeps are periodic only
     ++c->gen;
     return LB_OK;
 }
@@ -321,6 +349,123 @@ lb_status lb_set_viscosity(lb_ctx *c, double nu)
     c->sigma = trial.sigma;
     c->cs2 = trial.cs2;
     ++c->gen;
+    if (c->tb_k > 0) {  // the blocked descriptor carries the collision constants
+        bool fits = true;
+        if ((e = lbk::blocked_setup(c, c->tb_k, c->tb_tile, c->tb_threads, &fits)) != cudaSuccess)
+            return cuda_fail(c, e, "lb_set_viscosity: blocked sweeps");
+    }
+    return LB_OK;
+}
+
+lb_status lb_set_blocking(lb_ctx *c, int steps_per_launch, int tile, int threads)
+{
+    lbk::NvtxRange nvtx_range("lb_set_blocking");
+    if (!c) return LB_EINVAL;
+    if (steps_per_launch < 0 || steps_per_launch > 64 ||
+        (steps_per_launch > 0 && (tile < 1 || tile > 4096 || !(threads == 256 || threads == 512 || threads == 1024))))
+        return fail(c, LB_EINVAL, "lb_set_blocking: steps per launch in 0..64, tile in 1..4096, threads 256, 512 or 1024");
+    if (steps_per_launch > 0 && (c->d != 2 || c->geom.mirror))
+        return fail(c, LB_EINVAL, "lb_set_blocking: blocked sweeps are built for periodic 2D grids");
+    DeviceGuard dg(c);
+    cudaError_t e = cudaStreamSynchronize(c->stream);  // tables and graphs may be in use
+    if (e != cudaSuccess) return cuda_fail(c, e, "lb_set_blocking");
+    bool fits = true;
+    if ((e = lbk::blocked_setup(c, steps_per_launch, tile, threads, &fits)) != cudaSuccess)
+        return cuda_fail(c, e, "lb_set_blocking");
+    if (!fits) return fail(c, LB_EINVAL, "lb_set_blocking: tile plus halo exceeds the shared memory per block");
+    return LB_OK;
+}
+
+lb_status lb_get_blocking(const lb_ctx *c, int *info)
+{
+    if (!c || !info) return LB_EINVAL;
+    info[0] = c->tb_k;
+    info[1] = c->tb_tile;
+    info[2] = c->tb_threads;
+    info[3] = c->tb_ntiles;
+    return LB_OK;
+}
+
+lb_status lb_autotune(lb_ctx *c, int trial_steps, double *choice)
+{
+    lbk::NvtxRange nvtx_range("lb_autotune");
+    if (!c || trial_steps < 2) return LB_EINVAL;
+    if (c->d != 2 || c->geom.mirror) {  // one sweep per launch is the only schedule here
+        if (choice) {
+            choice[0] = 0;
+            choice[1] = choice[2] = choice[3] = 0;
+        }
+        return LB_OK;
+    }
+    DeviceGuard dg(c);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lb_autotune");
+    struct Cand {
+        int K, tile, threads;
+    };
+    std::vector<Cand> cands = {{0, 0, 0}};
+    int optin = 0;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device)) != cudaSuccess)
+        return cuda_fail(c, e, "lb_autotune");
+    const int node_bytes = 9 * (int)c->elem;
+    for (int K : {2, 4, 6, 8, 12})
+        for (int per_sm : {1, 2, 3, 4}) {
+            const long avail = per_sm == 1 ? optin : optin / per_sm - 1024;
+            int edge = (int)floor(sqrt((double)avail / node_bytes));
+            while ((long)edge * edge * node_bytes > avail) --edge;
+            const int tile = edge - 2 * K;
+            if (tile < 8) continue;
+            for (int th : {256, 512, 1024}) cands.push_back({K, tile, th});
+        }
+    const bool was_init = c->initialized;
+    c->initialized = true;  // the trials step whatever the buffers hold
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(c, LB_ECUDA, "lb_autotune: events");
+    double best = 1e300;
+    Cand win = cands[0];
+    lb_status st = LB_OK;
+    for (const Cand &cd : cands) {
+        bool fits = true;
+        if ((e = lbk::blocked_setup(c, cd.K, cd.tile, cd.threads, &fits)) != cudaSuccess) {
+            st = cuda_fail(c, e, "lb_autotune");
+            break;
+        }
+        if (!fits) continue;
+        const int64_t n = cd.K ? (trial_steps + cd.K - 1) / cd.K * cd.K : trial_steps;
+        if ((st = lb_step(c, n)) != LB_OK) break;  // warm-up
+        if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) {
+            st = cuda_fail(c, e, "lb_autotune");
+            break;
+        }
+        if ((st = lb_step(c, n)) != LB_OK) break;
+        float ms = 0.f;
+        if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+            st = cuda_fail(c, e, "lb_autotune");
+            break;
+        }
+        if (ms / n < best) {
+            best = ms / n;
+            win = cd;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(c->stream);
+    c->initialized = false;  // the trials overwrote the state: set it again
+    c->step = 0;
+    (void)was_init;
+    if (st != LB_OK) return st;
+    bool fits = true;
+    if ((e = lbk::blocked_setup(c, win.K, win.tile, win.threads, &fits)) != cudaSuccess)
+        return cuda_fail(c, e, "lb_autotune");
+    if (choice) {
+        choice[0] = win.K;
+        choice[1] = win.tile;
+        choice[2] = win.threads;
+        choice[3] = 1e3 * best;
+    }
     return LB_OK;
 }
 
@@ -393,6 +538,32 @@ lb_status lb_step(lb_ctx *c, int64_t nsteps)
     // directly so that they land in the caller's graph.
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(c->stream, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
+    if (c->tb_k > 0) {
+        // blocked: launches of tb_k steps (recorded in graphs), then one launch for the remainder
+        int64_t launches = nsteps / c->tb_k;
+        const int rem = (int)(nsteps % c->tb_k);
+        cudaError_t e = cudaSuccess;
+        while (cap == cudaStreamCaptureStatusNone && launches >= kTbGraphLaunches) {
+            if (!c->tb_graph[c->cur]) e = record_blocked(c, c->cur);
+            if (e == cudaSuccess) e = cudaGraphLaunch(c->tb_graph[c->cur], c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "lb_step: blocked graph");
+            launches -= kTbGraphLaunches;
+            c->step += kTbGraphLaunches * c->tb_k;
+        }
+        for (; launches > 0; --launches) {
+            if ((e = lbk::blocked_launch(c, c->f[c->cur], c->f[c->cur ^ 1], c->tb_k, c->stream)) != cudaSuccess)
+                return cuda_fail(c, e, "lb_step: blocked launch");
+            c->cur ^= 1;
+            c->step += c->tb_k;
+        }
+        if (rem > 0) {
+            if ((e = lbk::blocked_launch(c, c->f[c->cur], c->f[c->cur ^ 1], rem, c->stream)) != cudaSuccess)
+                return cuda_fail(c, e, "lb_step: blocked launch");
+            c->cur ^= 1;
+            c->step += rem;
+        }
+        return LB_OK;
+    }
     while (cap == cudaStreamCaptureStatusNone && nsteps >= kGraphSteps) {
         cudaError_t e = cudaSuccess;
         if (!c->graph[c->cur]) e = record_sweeps(c, c->cur);

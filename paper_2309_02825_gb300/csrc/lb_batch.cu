@@ -161,7 +161,7 @@ template <class L, typename T, int TH>
 __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1) batch_tb_kernel(const InstDesc<T> *__restrict__ inst,
                                                                      const TileDesc *__restrict__ tiles,
                                                                      const T *__restrict__ src, T *__restrict__ dst,
-                                                                     int K)
+                                                                     int K, int *__restrict__ range)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int Q = L::Q, NW = TH / 32;
@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1) batch_tb_kernel(const I
     // from slot opp(i) of z, after an odd number from slot i of z + e_i.
     T *d = dst + D.off;
     const bool odd = (K & 1) != 0;
+    unsigned acc = 0u;  // fixed point: OR of the high words + 2^29 of the stored values (|v| < 2^61 check)
     for (int r = warp; r < t.ty; r += NW) {
         T *grow = d + (int64_t)(t.y0 + r) * D.g.pitch + t.x0;
         const unsigned rb[3] = {smA + (unsigned)(r + K - 1) * rowB, smA + (unsigned)(r + K) * rowB,
@@ -259,9 +260,14 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1) batch_tb_kernel(const I
                 constexpr int i = decltype(I)::value;
                 constexpr int ex = L::E[i][0], ey = L::E[i][1], o = reflect_pop<L>(i, 3);
                 const T v = odd ? lds<T, (ex * Q + i) * E>(rb[1 + ey] + cb) : lds<T, o * E>(rb[1] + cb);
+                if constexpr (std::is_same<T, long long>::value)
+                    acc |= (unsigned)((unsigned long long)v >> 32) + 0x20000000u;
                 grow[(int64_t)i * D.g.slab + c] = v;
             });
         }
+    }
+    if constexpr (std::is_same<T, long long>::value) {
+        if (range && __any_sync(0xffffffffu, acc >= 0x40000000u) && lane == 0) atomicOr(range, 1);
     }
 }
 
@@ -467,6 +473,18 @@ cudaError_t launch_group(lb_batch *b, const Group &g, int from, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Tiles of one N0 x N1 instance: each axis cut into ceil(N / tile)
+// near-equal tiles.
+void append_tiles(std::vector<lbk::TileDesc> &tv, int inst, int n0, int n1, int tile, int &maxw, int &maxh)
+{
+    const int ntx = (n0 + tile - 1) / tile, nty = (n1 + tile - 1) / tile;
+    const int tx = (n0 + ntx - 1) / ntx, ty = (n1 + nty - 1) / nty;
+    maxw = std::max(maxw, tx);
+    maxh = std::max(maxh, ty);
+    for (int y0 = 0; y0 < n1; y0 += ty)
+        for (int x0 = 0; x0 < n0; x0 += tx) tv.push_back({inst, x0, y0, std::min(tx, n0 - x0), std::min(ty, n1 - y0)});
+}
+
 constexpr int kTbGraphLaunches = 16;  // blocked launches per recorded graph (even)
 
 template <typename T, int TH> const void *tb_kernel()
@@ -479,12 +497,14 @@ template <typename T> const void *tb_kernel_for(int threads)
     return threads == 256 ? tb_kernel<T, 256>() : (threads == 512 ? tb_kernel<T, 512>() : tb_kernel<T, 1024>());
 }
 
-const void *tb_kernel_of(const lb_batch *b, int threads)
+const void *tb_kernel_prec(int precision, int threads)
 {
-    if (b->precision == LB_FP64) return tb_kernel_for<double>(threads);
-    if (b->precision == LB_FX64) return tb_kernel_for<long long>(threads);
+    if (precision == LB_FP64) return tb_kernel_for<double>(threads);
+    if (precision == LB_FX64) return tb_kernel_for<long long>(threads);
     return tb_kernel_for<float>(threads);
 }
+
+const void *tb_kernel_of(const lb_batch *b, int threads) { return tb_kernel_prec(b->precision, threads); }
 
 size_t tb_smem(const lb_batch *b, int K)
 {
@@ -494,7 +514,8 @@ size_t tb_smem(const lb_batch *b, int K)
 // One blocked launch of K steps over every tile, from buffer `from`.
 cudaError_t launch_tb(lb_batch *b, int from, int K, cudaStream_t s)
 {
-    void *args[] = {&b->d_desc, &b->d_tiles, &b->buf[from], &b->buf[from ^ 1], &K};
+    int *range = nullptr;
+    void *args[] = {&b->d_desc, &b->d_tiles, &b->buf[from], &b->buf[from ^ 1], &K, &range};
     return cudaLaunchKernel(tb_kernel_of(b, b->tb_threads), dim3((unsigned)b->ntiles), dim3((unsigned)b->tb_threads),
                             args, tb_smem(b, K), s);
 }
@@ -510,15 +531,7 @@ lb_status build_tiles(lb_batch *b, int K, int tile, int threads)
     if (K == 0) return LB_OK;
     std::vector<lbk::TileDesc> tv;
     int maxw = 0, maxh = 0;
-    for (int j = 0; j < b->count; ++j) {
-        const int n0 = (int)b->inst[j].N[0], n1 = (int)b->inst[j].N[1];
-        const int ntx = (n0 + tile - 1) / tile, nty = (n1 + tile - 1) / tile;
-        const int tx = (n0 + ntx - 1) / ntx, ty = (n1 + nty - 1) / nty;
-        maxw = std::max(maxw, tx);
-        maxh = std::max(maxh, ty);
-        for (int y0 = 0; y0 < n1; y0 += ty)
-            for (int x0 = 0; x0 < n0; x0 += tx) tv.push_back({j, x0, y0, std::min(tx, n0 - x0), std::min(ty, n1 - y0)});
-    }
+    for (int j = 0; j < b->count; ++j) append_tiles(tv, j, (int)b->inst[j].N[0], (int)b->inst[j].N[1], tile, maxw, maxh);
     if (tv.size() > 0x7fffffff) return bfail(b, LB_EINVAL, "lb_batch_set_blocking: too many tiles");
     int optin = 0;
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device)) != cudaSuccess)
@@ -688,6 +701,88 @@ cudaError_t run_steps(lb_batch *b, int64_t n)
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Blocked sweeps of a single 2D periodic grid: the batched blocked kernel on
+// a batch of one instance (the context's own buffers, offset 0).
+// ---------------------------------------------------------------------------
+namespace lbk {
+
+template <typename T> static cudaError_t upload_single_desc(lb_ctx *c)
+{
+    InstDesc<T> h;
+    h.g = c->geom;
+    if constexpr (std::is_same<T, long long>::value)
+        h.k = make_coll_fx(c);
+    else
+        h.k = make_coll<T>(*c);
+    h.off = 0;
+    cudaError_t e = cudaSuccess;
+    if (!c->tb_desc) e = cudaMalloc(&c->tb_desc, sizeof(InstDesc<long long>) > sizeof(InstDesc<double>)
+                                                       ? sizeof(InstDesc<long long>)
+                                                       : sizeof(InstDesc<double>));
+    if (e == cudaSuccess) e = cudaMemcpy(c->tb_desc, &h, sizeof(h), cudaMemcpyHostToDevice);
+    return e;
+}
+
+void blocked_release(lb_ctx *c)
+{
+    for (auto &ge : c->tb_graph)
+        if (ge) {
+            cudaGraphExecDestroy(ge);
+            ge = nullptr;
+        }
+    cudaFree(c->tb_tiles);
+    cudaFree(c->tb_desc);
+    c->tb_tiles = nullptr;
+    c->tb_desc = nullptr;
+    c->tb_k = c->tb_tile = c->tb_threads = c->tb_ntiles = 0;
+}
+
+cudaError_t blocked_setup(lb_ctx *c, int K, int tile, int threads, bool *fits)
+{
+    *fits = true;
+    blocked_release(c);
+    if (K == 0) return cudaSuccess;
+    std::vector<TileDesc> tv;
+    int maxw = 0, maxh = 0;
+    append_tiles(tv, 0, (int)c->N[0], (int)c->N[1], tile, maxw, maxh);
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (e != cudaSuccess) return e;
+    const size_t need = tb_smem_bytes(9, (int)c->elem, maxw + 2 * K, maxh + 2 * K);
+    if (need > (size_t)optin || tv.size() > 0x7fffffff) {
+        *fits = false;
+        return cudaSuccess;
+    }
+    if ((e = cudaFuncSetAttribute(tb_kernel_prec(c->precision, threads), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)need)) != cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(&c->tb_tiles, sizeof(TileDesc) * tv.size())) != cudaSuccess ||
+        (e = cudaMemcpy(c->tb_tiles, tv.data(), sizeof(TileDesc) * tv.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    e = c->precision == LB_FP64 ? upload_single_desc<double>(c)
+                                : (c->precision == LB_FX64 ? upload_single_desc<long long>(c) : upload_single_desc<float>(c));
+    if (e != cudaSuccess) return e;
+    c->tb_k = K;
+    c->tb_tile = tile;
+    c->tb_threads = threads;
+    c->tb_ntiles = (int)tv.size();
+    c->tb_maxw = maxw;
+    c->tb_maxh = maxh;
+    return cudaSuccess;
+}
+
+cudaError_t blocked_launch(lb_ctx *c, const void *src, void *dst, int K, cudaStream_t s)
+{
+    int *range = c->precision == LB_FX64 ? c->dflag + kFlagRange : nullptr;
+    void *args[] = {&c->tb_desc, &c->tb_tiles, (void *)&src, &dst, &K, &range};
+    const size_t smem = tb_smem_bytes(9, (int)c->elem, c->tb_maxw + 2 * K, c->tb_maxh + 2 * K);
+    return cudaLaunchKernel(tb_kernel_prec(c->precision, c->tb_threads), dim3((unsigned)c->tb_ntiles),
+                            dim3((unsigned)c->tb_threads), args, smem, s);
+}
+
+}  // namespace lbk
 
 extern "C" {
 

@@ -223,6 +223,11 @@ struct lb_ctx {
     int64_t step = 0;
     int device = 0;
     uint64_t gen = 0;  // bumped whenever the walls or the viscosity change (recorded launches go stale)
+    // temporally blocked sweeps (lb_set_blocking, 2D periodic): tb_k steps per launch, 0 = one sweep per launch
+    int tb_k = 0, tb_tile = 0, tb_threads = 0, tb_ntiles = 0, tb_maxw = 0, tb_maxh = 0;
+    void *tb_desc = nullptr;   // instance descriptor of the grid (device)
+    void *tb_tiles = nullptr;  // tile table (device)
+    cudaGraphExec_t tb_graph[2] = {nullptr, nullptr};  // recorded blocked launches, by starting buffer
     std::string err;
 };
 
@@ -265,5 +270,13 @@ cudaError_t launch_maxabs(lb_ctx *c, const double *x, int64_t n, double *out_dev
 cudaError_t launch_sweep_fx(lb_ctx *c, const void *src, void *dst);
 cudaError_t launch_norms(lb_ctx *c, const double *theta, const double *u, const double *ex_theta,
                          const double *ex_u, double *out_dev);
+// Temporally blocked sweeps of one 2D periodic grid (lb_batch.cu, the batched
+// blocked kernel on a batch of one): set up the tile table and descriptor for
+// K steps per launch (K = 0 releases them), and launch K steps from src to dst.
+// The fixed-point path checks the values it stores (|f| < 2^61) into
+// ctx->dflag[kFlagRange].
+cudaError_t blocked_setup(lb_ctx *c, int K, int tile, int threads, bool *fits);
+cudaError_t blocked_launch(lb_ctx *c, const void *src, void *dst, int K, cudaStream_t s);
+void blocked_release(lb_ctx *c);
 
 }  // namespace lbk

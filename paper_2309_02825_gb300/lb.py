@@ -73,6 +73,9 @@ def load():
             "lb_macros": ([vp, vp, vp, vp], ctypes.c_int),
             "lb_check": ([vp], ctypes.c_int),
             "lb_set_viscosity": ([vp, dbl], ctypes.c_int),
+            "lb_set_blocking": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "lb_get_blocking": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "lb_autotune": ([vp, ctypes.c_int, pd], ctypes.c_int),
             "lb_sum_theta": ([vp, pd], ctypes.c_int),
             "lb_reduce": ([vp, vp, vp, vp, vp, pd], ctypes.c_int),
             "lb_state_layout": ([vp, p64, p64, p64], ctypes.c_int),
@@ -203,6 +206,25 @@ def lb_check(ctx):
 def lb_set_viscosity(ctx, nu):
     lib = load()
     _check(lib, ctx, lib.lb_set_viscosity(ctx, float(nu)), "lb_set_viscosity")
+
+
+def lb_set_blocking(ctx, steps_per_launch, tile=64, threads=512):
+    lib = load()
+    _check(lib, ctx, lib.lb_set_blocking(ctx, int(steps_per_launch), int(tile), int(threads)), "lb_set_blocking")
+
+
+def lb_get_blocking(ctx):
+    lib = load()
+    buf = (ctypes.c_int * 4)()
+    _check(lib, ctx, lib.lb_get_blocking(ctx, buf), "lb_get_blocking")
+    return {"steps_per_launch": buf[0], "tile": buf[1], "threads": buf[2], "tiles": buf[3]}
+
+
+def lb_autotune(ctx, trial_steps=16):
+    lib = load()
+    buf = (ctypes.c_double * 4)()
+    _check(lib, ctx, lib.lb_autotune(ctx, int(trial_steps), buf), "lb_autotune")
+    return {"steps_per_launch": int(buf[0]), "tile": int(buf[1]), "threads": int(buf[2]), "us_per_step": buf[3]}
 
 
 def lb_sum_theta(ctx):
@@ -374,6 +396,16 @@ class Solver:
 
     def check(self):
         lb_check(self.ctx)
+
+    def set_blocking(self, steps_per_launch, tile=64, threads=512):
+        lb_set_blocking(self.ctx, steps_per_launch, tile, threads)
+
+    def blocking(self):
+        return lb_get_blocking(self.ctx)
+
+    def autotune(self, trial_steps=16):
+        """Pick one sweep per launch or blocked sweeps by timing; overwrites the state."""
+        return lb_autotune(self.ctx, trial_steps)
 
     def set_viscosity(self, nu):
         lb_set_viscosity(self.ctx, nu)

@@ -382,3 +382,76 @@ def test_fx64_range_overflow_is_reported_not_wrapped():
     with pytest.raises(lb.LBError) as ei:
         f64.macros()
     assert ei.value.status == lb.LB_ENONPOS
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fx64", "fp32s"])
+@pytest.mark.parametrize("N,blk", [((70, 45), (4, 24, 512)), ((130, 33), (3, 40, 256)), ((64, 64), (8, 20, 1024)),
+                                   ((5, 9), (2, 4, 256)), ((200, 17), (12, 30, 512))])
+def test_blocked_sweeps_equal_single_sweeps(N, blk, precision):
+    """lb_set_blocking (K steps per launch in shared memory) gives the same
+    state bit for bit as one sweep per launch, over remainder launches,
+    recorded graphs of 16 launches, a viscosity change in between and a
+    return to one sweep per launch."""
+    d = 2
+    prob, dx, dt = _problem(d, N, 23)
+    th0, g0 = _dev(prob.theta(N, dx)), _dev(prob.grad(N, dx))
+    out = []
+    for mode in ("blocked", "single"):
+        s = lb.Solver(d, N, prob.nu, dx, dt, precision=precision, theta_ref=1.5)
+        if mode == "blocked":
+            s.set_blocking(*blk)
+            assert s.blocking()["steps_per_launch"] == blk[0]
+        s.set_theta0(th0, g0)
+        s.step(16 * blk[0] + 3)
+        s.set_viscosity(0.027)
+        s.step(7)
+        if mode == "blocked":
+            s.set_blocking(0)
+        s.step(2)
+        assert s.nsteps == 16 * blk[0] + 12
+        out.append(s.macros())
+        s.check()
+    torch.cuda.synchronize()
+    for a, b in zip(out[0], out[1]):
+        assert torch.equal(a, b)
+
+
+def test_blocking_refused_where_not_built_and_autotune():
+    prob, dx, dt = _problem(3, (20, 12, 10), 3)
+    s3 = lb.Solver(3, (20, 12, 10), prob.nu, dx, dt)
+    with pytest.raises(lb.LBError) as ei:
+        s3.set_blocking(4, 16, 512)
+    assert ei.value.status == lb.LB_EINVAL
+    prob, dx, dt = _problem(2, (96, 80), 3)
+    s = lb.Solver(2, (96, 80), prob.nu, dx, dt, precision="fx64", boundary=["mirror", "periodic"])
+    with pytest.raises(lb.LBError) as ei:
+        s.set_blocking(4, 16, 512)
+    assert ei.value.status == lb.LB_EINVAL
+    s = lb.Solver(2, (96, 80), prob.nu, dx, dt, precision="fx64")
+    with pytest.raises(lb.LBError) as ei:
+        s.set_blocking(8, 300, 512)  # tile plus halo beyond shared memory
+    assert ei.value.status == lb.LB_EINVAL
+    choice = s.autotune(8)
+    assert choice["steps_per_launch"] in (0, 2, 4, 6, 8, 12) and choice["us_per_step"] > 0
+    with pytest.raises(lb.LBError) as ei:
+        s.step(1)  # the trials overwrote the state
+    assert ei.value.status == lb.LB_ESTATE
+    s.set_theta0(_dev(prob.theta((96, 80), dx)), _dev(prob.grad((96, 80), dx)))
+    s.step(5)
+    s.macros()
+
+
+def test_blocked_fx64_range_overflow_is_reported():
+    """The blocked FX64 sweep checks the values it stores: an unstable
+    relaxation set is reported (LB_EINVAL), not wrapped."""
+    d, N = 2, (40, 30)
+    prob, dx, dt = _problem(d, N, 11)
+    fx = lb.Solver(d, N, prob.nu, dx, dt, relax=UNSTABLE, precision="fx64")
+    fx.set_blocking(4, 16, 256)
+    fx.set_theta0(_dev(prob.theta(N, dx)), _dev(prob.grad(N, dx)))
+    fx.step(20)
+    fx.macros()
+    fx.step(400)
+    with pytest.raises(lb.LBError) as ei:
+        fx.macros()
+    assert ei.value.status == lb.LB_EINVAL
