@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--sweeps", type=int, default=100, help="sweeps per benchmark step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-blocking", action="store_true",
+                   help="one sweep per launch only (skip the autotuner's blocked candidates)")
     p.add_argument("--no-variant", action="store_true", help="skip the other precisions' sub-results")
     p.add_argument("--no-batched", action="store_true", help="skip the batched 512-instance measurement")
     p.add_argument("--no-adjoint", action="store_true", help="skip the 512^2 adjoint measurement")
@@ -75,6 +77,8 @@ def parse():
                    help="minimal command for ncu: forward + seed + T reverse steps at N^2, then exit")
     p.add_argument("--profile-sweep", default=None, metavar="D,PREC,N,STEPS",
                    help="run STEPS sweeps of one D-dimensional N^D grid at PREC and exit (for ncu captures)")
+    p.add_argument("--blocking", default=None, metavar="K,TILE,THREADS",
+                   help="with --profile-sweep: blocked sweeps of K steps per launch")
     return p.parse_args()
 
 
@@ -101,6 +105,42 @@ def kernel_source_sha():
         text = re.sub(r"//[^\n]*", " ", text)
         h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
+
+
+def blocked_source_sha():
+    """sha256 (16 hex digits) of the blocked kernel's sources (comments and
+    whitespace removed)."""
+    import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_2309_02825_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("lb_internal.cuh", "lb_device.cuh", "lb_batch.cu"):
+        text = open(os.path.join(csrc, name)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()[:16]
+
+
+def profile_blocked(kernel_key):
+    """(warp instructions, DRAM bytes) per launch of a blocked configuration,
+    from a committed ncu summary of the same kernel source; (None, None) if
+    the kernel changed since or the configuration was not captured."""
+    try:
+        sha = blocked_source_sha()
+        for line in open(os.path.join(ROOT, "profiles", "blocked.txt")):
+            parts = line.split()
+            if len(parts) >= 4 and parts[0] == kernel_key and parts[1] == sha:
+                return float(parts[2]), float(parts[3])
+    except OSError:
+        pass
+    return None, None
+
+
+def blocked_launch_bytes(N0, N1, K, tile, elem, q=9):
+    """HBM bytes one blocked launch must move: every tile read with its
+    K-node halo and written once."""
+    return blocked_bytes_per_lu([(N0, N1)], K, tile, elem, q) * N0 * N1 * K
 
 
 def profile_fp64_inst(kernel_key):
@@ -223,7 +263,7 @@ def aggregate(units, seconds, world):
 # Our implementation.
 # ---------------------------------------------------------------------------
 
-def run_ours(args, precision, world, rank, local, peaks, with_e2e, label_main):
+def run_ours(args, precision, world, rank, local, peaks, with_e2e, label_main, blocking=True):
     import torch
     from paper_2309_02825_gb300 import lb
 
@@ -244,6 +284,11 @@ def run_ours(args, precision, world, rank, local, peaks, with_e2e, label_main):
     stream = torch.cuda.Stream()
     theta_ref = 2.0 if precision == "fp32s" else 0.0
     s = lb.Solver(d, N, case.nu, case.dx, case.dt, precision=precision, theta_ref=theta_ref, stream=stream)
+    # one sweep per launch, or K sweeps per launch in shared memory: the
+    # autotuner times both on this grid (outside the timed region)
+    with torch.cuda.stream(stream):
+        tune = s.autotune(24) if blocking and not args.no_blocking else {"steps_per_launch": 0}
+    K = tune["steps_per_launch"]
     th = torch.empty(tuple(reversed(N)), dtype=torch.float64, device="cuda")
     gr = torch.empty((d,) + tuple(reversed(N)), dtype=torch.float64, device="cuda")
     u = torch.empty_like(gr)
@@ -293,37 +338,65 @@ def run_ours(args, precision, world, rank, local, peaks, with_e2e, label_main):
     q = 9
     elem = 4 if precision == "fp32s" else 8
     bytes_lu = 2 * q * elem
-    achieved = bytes_lu * nodes / (sweep_ms / 1e3) / 1e9
     norms = out["norms"]
     ctype = {"fp64": "double", "fp32s": "float", "fx64": "long long"}[precision]
-    res = {
-        "value": value,
-        "ms_per_step": elapsed / args.steps * 1e3,
-        "sweep_ms": sweep_ms,
-        "bytes_per_lu": bytes_lu,
-        "roofline": {
+    sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    if K == 0:
+        # one sweep per launch: HBM-bound, 2 q sizeof(T) bytes per update
+        achieved = bytes_lu * nodes / (sweep_ms / 1e3) / 1e9
+        roofline = {
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"],
             "traffic": profile_traffic("sweep_d2q9_%s_%d" % (precision, args.N)),
             "kernel": "sweep_kernel<D2Q9,%s>" % ctype,
             "algorithmic_bytes_per_launch": bytes_lu * nodes,
             "peak_source": peaks["source"],
-        },
+        }
+    else:
+        # blocked: K sweeps per launch in shared memory, bound by instruction
+        # issue (4 warp instructions per SM per clock); its HBM traffic is the
+        # tiles with their halos
+        launch_s = sweep_ms / 1e3 * K
+        key = "blocked_d2q9_%s_%d_K%d_T%d_TH%d" % (precision, args.N, K, tune["tile"], tune["threads"])
+        inst, dram = profile_blocked(key)
+        peak_issue = 4 * sms * sm_mhz * 1e6 / 1e9
+        ach_issue = None if inst is None else inst / launch_s / 1e9
+        blk_bytes = blocked_launch_bytes(N[0], N[1], K, tune["tile"], elem)
+        roofline = {
+            "bound": "alu", "achieved": ach_issue, "peak": peak_issue, "unit": "G warp-inst/s",
+            "frac": None if ach_issue is None else ach_issue / peak_issue,
+            "traffic": dram,
+            "kernel": "batch_tb_kernel<D2Q9,%s,%d> (%d sweeps per launch, tiles of %d)" % (
+                ctype, tune["threads"], K, tune["tile"]),
+            "warp_inst_per_launch": inst, "sms": sms, "sm_mhz": sm_mhz,
+            "peak_source": "4 warp instructions per SM per clock x SMs x sampled SM clock",
+            "algorithmic_bytes_per_launch": blk_bytes,
+            "hbm_gbs_of_algorithmic_bytes": blk_bytes / launch_s / 1e9,
+            "hbm_frac_of_algorithmic_bytes": blk_bytes / launch_s / 1e9 / peaks["hbm_gbs"],
+            "per_step_equivalent_hbm_frac": bytes_lu * nodes / (sweep_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+            "counters_source": "profiles/blocked.txt (ncu at this size, same kernel source)",
+        }
+    res = {
+        "value": value,
+        "ms_per_step": elapsed / args.steps * 1e3,
+        "sweep_ms": sweep_ms,
+        "bytes_per_lu": bytes_lu,
+        "blocking": tune,
+        "roofline": roofline,
         "error": {"t": T, "theta_rmse": norms["theta"]["rmse"],
                   "u_rmse": math.sqrt(sum(norms["u%d" % a]["rmse"] ** 2 for a in range(d)) / d),
                   "u_linf": max(norms["u%d" % a]["linf"] for a in range(d)),
                   "u_rel_l2": math.sqrt(sum(norms["u%d" % a]["rel_l2"] ** 2 for a in range(d)) / d),
                   "sum_theta_drift": abs(out["total"] - float(th0_h.sum())) / float(th0_h.sum())},
         "clocks": clk,
-        "gpu_launches": args.steps * (S + 6 + (2 if precision == "fx64" else 0)),
+        "gpu_launches": args.steps * ((S // K + (1 if S % K else 0) if K else S) + 6 + (2 if precision == "fx64" else 0)),
     }
-    if precision == "fp64":
+    if precision == "fp64" and K == 0:
         # The FP64 sweep is bound by the FP64 pipe: GB300 issues 2 FP64 lane
         # operations per SM per clock (1/64 of FP32).  The instructions per
         # update come from an ncu capture of this kernel source (null when the
         # kernel changed since), the SM count from the device.
-        sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
         peak_inst = sms * 2 * sm_mhz * 1e6 / 1e9
         ipl = profile_fp64_inst("sweep_d2q9_fp64")
         ach_inst = None if ipl is None else ipl * nodes / (sweep_ms / 1e3) / 1e9
@@ -858,7 +931,7 @@ def run_profile_adjoint(local, spec):
     print(json.dumps({"profile_adjoint": spec, "ok": True}))
 
 
-def run_profile_sweep(local, spec):
+def run_profile_sweep(local, spec, blocking=None):
     """Minimal, repeatable command for ncu: init + STEPS sweeps of one grid,
     then one recovery, one state sum and the error norms."""
     import torch
@@ -874,10 +947,13 @@ def run_profile_sweep(local, spec):
     else:
         prob, N, nu, dx, dt = case.problem, case.N, case.nu, case.dx, case.dt
     s = lb.Solver(d, N, nu, dx, dt, precision=prec, theta_ref=1.5)
+    blk = [int(v) for v in blocking.split(",")] if blocking else None
+    if blk:
+        s.set_blocking(*blk)
     s.set_theta0(torch.from_numpy(prob.theta(N, dx)).cuda(),
                  torch.from_numpy(np.ascontiguousarray(prob.grad(N, dx))).cuda())
-    for _ in range(steps):
-        s.step(1)
+    for _ in range(steps // blk[0] if blk else steps):
+        s.step(blk[0] if blk else 1)
     th, _, u = s.macros(want=("theta", "u"))
     s.sum_theta()
     T = steps * dt
@@ -1002,7 +1078,7 @@ def main():
         run_profile_adjoint(local, args.profile_adjoint)
         return 0
     if args.profile_sweep:
-        run_profile_sweep(local, args.profile_sweep)
+        run_profile_sweep(local, args.profile_sweep, args.blocking)
         return 0
     if args.accuracy:
         if rank == 0:
@@ -1015,6 +1091,11 @@ def main():
         dist.init_process_group("nccl")
     peaks = load_peaks()
     main_res = run_ours(args, args.precision, world, rank, local, peaks, not args.no_e2e, True)
+    per_step = None
+    if main_res["blocking"]["steps_per_launch"]:
+        # the same step with one sweep per launch (the HBM-bound sweep)
+        v = run_ours(args, args.precision, world, rank, local, peaks, False, False, blocking=False)
+        per_step = {"value": v["value"], "unit": UNIT, "sweep_ms": v["sweep_ms"], "roofline": v["roofline"]}
     variants = []
     if not args.no_variant:
         for other in ("fx64", "fp64", "fp32s"):
@@ -1022,7 +1103,7 @@ def main():
                 continue
             v = run_ours(args, other, world, rank, local, peaks, False, False)
             entry = {"precision": other, "value": v["value"], "unit": UNIT, "roofline": v["roofline"],
-                     "error": v["error"], "sweep_ms": v["sweep_ms"]}
+                     "error": v["error"], "sweep_ms": v["sweep_ms"], "blocking": v["blocking"]}
             if "roofline_fp64_pipe" in v:
                 entry["roofline_fp64_pipe"] = v["roofline_fp64_pipe"]
             variants.append(entry)
@@ -1072,6 +1153,9 @@ def main():
             "error": main_res["error"],
             "sweep_ms": main_res["sweep_ms"],
         }
+        line["blocking"] = main_res["blocking"]
+        if per_step:
+            line["one_sweep_per_launch"] = per_step
         if "roofline_fp64_pipe" in main_res:
             line["roofline_fp64_pipe"] = main_res["roofline_fp64_pipe"]
         if variants:
