@@ -505,6 +505,11 @@ lb_status lb_set_theta0(lb_ctx *c, const double *theta0, const double *grad)
             (e = cudaMemcpyAsync(&mx, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
             (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
             return cuda_fail(c, e, "lb_set_theta0: max|theta0|");
+        if (c->fx_max > 0.0) {  // a slab: the scale of the whole grid (at least this part's maximum)
+            if (!isfinite(mx) || mx > c->fx_max)
+                return fail(c, LB_EINVAL, "lb_set_theta0: max|theta0| of this part exceeds the grid's maximum");
+            mx = c->fx_max;
+        }
         if (!(mx > 0.0) || !isfinite(mx)) return fail(c, LB_ENONPOS, "lb_set_theta0: theta0 must be finite and > 0");
         int ex = 0;
         frexp(mx, &ex);  // mx < 2^ex

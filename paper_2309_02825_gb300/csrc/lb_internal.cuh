@@ -207,6 +207,7 @@ struct lb_ctx {
     double nu = 0, dx = 0, dt = 0, c = 0, eps = 0, cs2 = 0, sigma = 0;
     double s1 = 0, s2x = 0, s22 = 1, w0 = 0, w1 = 0, wd = 0, theta_ref = 0;
     int fx_bits = 0;          // LB_FX64: stored value = round(f * 2^fx_bits)
+    double fx_max = 0.0;      // LB_FX64: if > 0, the max |theta0| that fixes fx_bits (a slab's global maximum)
     bool paper = true;        // relaxation set from Theorem 2 (eps-derivatives known)
     cudaStream_t stream = nullptr;
     lbk::Geom geom{};
@@ -265,6 +266,12 @@ cudaError_t launch_sweep(lb_ctx *c, const void *src, void *dst);
 // Recovery (lb_recover.cu); flag bit 0: theta <= 0 seen, bit 2: a staging wait timed out.
 cudaError_t launch_macros(lb_ctx *c, const void *src, double *theta, double *grad, double *u, int *flag);
 cudaError_t launch_sum_state(lb_ctx *c, const void *src, double *out_dev);
+// The same on rows row0 .. row0 + nrow - 1 of the grid only (rows = the
+// products of all axes but x, slowest last); the recovery's outputs then hold
+// those rows only.
+cudaError_t launch_sum_state_rows(lb_ctx *c, const void *src, double *out_dev, int64_t row0, int64_t nrow);
+cudaError_t launch_macros_rows(lb_ctx *c, const void *src, double *theta, double *grad, double *u, int *flag,
+                               int64_t row0, int64_t nrow);
 cudaError_t launch_maxabs(lb_ctx *c, const double *x, int64_t n, double *out_dev);
 // 64-bit fixed-point path (lb_fx.cu).
 cudaError_t launch_sweep_fx(lb_ctx *c, const void *src, void *dst);

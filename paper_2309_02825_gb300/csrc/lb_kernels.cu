@@ -326,11 +326,14 @@ __global__ void __launch_bounds__(kRedThreads) sum_state_kernel(const T *__restr
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // rows of the sum: g.rows per population (a sub-range of the grid's rows
+    // when src starts past row 0), populations g.slab values apart
     const int64_t nrows = (int64_t)q * g.rows;
     constexpr int U = 4;  // vectors in flight per lane
     for (int64_t r = warp; r < nrows; r += nwarps) {
-        const T *rowp = src + r * g.pitch;
-        const double rw = g.mirror ? row_wall_weight(g, r % g.rows) : 1.0;
+        const int64_t pop = r / g.rows, row = r - pop * g.rows;
+        const T *rowp = src + pop * g.slab + row * g.pitch;
+        const double rw = g.mirror ? row_wall_weight(g, row) : 1.0;
         for (int x0 = lane * V; x0 < g.N0; x0 += U * 32 * V) {
             T a[U][V];
 #pragma unroll
@@ -554,22 +557,31 @@ cudaError_t launch_init(lb_ctx *c, const double *theta0, const double *grad, int
     }
 }
 
-cudaError_t launch_sum_state(lb_ctx *c, const void *src, double *out_dev)
+cudaError_t launch_sum_state_rows(lb_ctx *c, const void *src, double *out_dev, int64_t row0, int64_t nrow)
 {
     const int nb = c->scratch_blocks;
+    Geom g = c->geom;  // rows row0 .. row0 + nrow - 1 of every population (no walls on a sub-range)
+    g.rows = nrow;
+    if (row0 != 0 || nrow != c->geom.rows) g.mirror = 0;
+    const int64_t off = row0 * g.pitch;
     if (c->precision == LB_FP64)
-        sum_state_kernel<double><<<nb, kRedThreads, 0, c->stream>>>((const double *)src, c->geom, c->q, 1.0,
+        sum_state_kernel<double><<<nb, kRedThreads, 0, c->stream>>>((const double *)src + off, g, c->q, 1.0,
                                                                      c->scratch);
     else if (c->precision == LB_FX64)
         sum_state_kernel<long long><<<nb, kRedThreads, 0, c->stream>>>(
-            (const long long *)src, c->geom, c->q, ldexp(1.0, -c->fx_bits), c->scratch);
+            (const long long *)src + off, g, c->q, ldexp(1.0, -c->fx_bits), c->scratch);
     else
-        sum_state_kernel<float><<<nb, kRedThreads, 0, c->stream>>>((const float *)src, c->geom, c->q, 1.0,
+        sum_state_kernel<float><<<nb, kRedThreads, 0, c->stream>>>((const float *)src + off, g, c->q, 1.0,
                                                                     c->scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     fold_kernel<<<1, kRedThreads, 0, c->stream>>>(c->scratch, nb, 1, 0u, out_dev);
     return cudaGetLastError();
+}
+
+cudaError_t launch_sum_state(lb_ctx *c, const void *src, double *out_dev)
+{
+    return launch_sum_state_rows(c, src, out_dev, 0, c->geom.rows);
 }
 
 cudaError_t launch_maxabs(lb_ctx *c, const double *x, int64_t n, double *out_dev)

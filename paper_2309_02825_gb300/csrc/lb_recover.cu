@@ -67,10 +67,13 @@ template <> struct RecAcc<long long> {
     using type = long long;  // exact integer moment sums
 };
 
+// Rows row0 .. row0 + nrow - 1 of the grid (all rows in a plain recovery);
+// the outputs hold those rows only, node (row - row0) * N0 + x.
 template <class L, typename T, bool MIR>
 __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ src, Geom g, Recov r, double scale,
                                                        double *__restrict__ theta, double *__restrict__ grad,
-                                                       double *__restrict__ u, int *__restrict__ flag)
+                                                       double *__restrict__ u, int *__restrict__ flag, int64_t row0,
+                                                       int64_t nrow)
 {
     constexpr int H = 16 / (int)sizeof(T);  // halo = one 16-byte vector
     constexpr int TW = kTile + 2 * H;        // tile width per population
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ sr
     __shared__ __align__(8) unsigned long long bar;
 
     const int tiles_per_row = (g.N0 + kTile - 1) / kTile;
-    const int64_t row = blockIdx.x / tiles_per_row;
+    const int64_t row = row0 + blockIdx.x / tiles_per_row;
     const int x0 = (int)(blockIdx.x % tiles_per_row) * kTile;
     const RowPos rpos = row_pos<L::D>(g, row);
     // copy window: multiples of H elements, i.e. 16-byte aligned and sized
@@ -146,8 +149,8 @@ __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ sr
             if constexpr (e == -1) J[a] -= fv;
         });
     });
-    const int64_t nodes = (int64_t)g.N0 * g.rows;
-    const int64_t node = row * g.N0 + x;
+    const int64_t nodes = (int64_t)g.N0 * nrow;
+    const int64_t node = (row - row0) * g.N0 + x;
     const double thd = (double)th * scale + r.theta_ref;
     if (theta) theta[node] = thd;
     {  // theta > 0 and finite, as bit tests on the integer pipes
@@ -164,7 +167,8 @@ __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ sr
 }
 
 template <class L, typename T, bool MIR>
-static cudaError_t recover_t(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
+static cudaError_t recover_t(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag, int64_t row0,
+                             int64_t nrow)
 {
     constexpr int H = 16 / (int)sizeof(T);
     const size_t smem = (size_t)L::Q * (kTile + 2 * H) * sizeof(T);
@@ -178,25 +182,30 @@ static cudaError_t recover_t(lb_ctx *c, const void *src, double *th, double *gr,
     r.ucoef = (2.0 - c->s1) * c->c * scale;
     r.gcoef = -c->s1 / (c->sigma * c->dx) * scale;
     r.theta_ref = (c->precision == LB_FP32_SHIFTED) ? c->theta_ref : 0.0;
-    const int64_t blocks = c->geom.rows * ((c->geom.N0 + kTile - 1) / kTile);
+    const int64_t blocks = nrow * ((c->geom.N0 + kTile - 1) / kTile);
+    if (blocks == 0) return cudaSuccess;
     recover_kernel<L, T, MIR><<<(unsigned)blocks, kTile, smem, c->stream>>>((const T *)src, c->geom, r, scale, th,
-                                                                             gr, u, flag);
+                                                                             gr, u, flag, row0, nrow);
     return cudaGetLastError();
 }
 
 template <class L, bool MIR>
-static cudaError_t recover_m(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
+static cudaError_t recover_m(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag, int64_t row0,
+                             int64_t nrow)
 {
     switch (c->precision) {
-    case LB_FX64: return recover_t<L, long long, MIR>(c, src, th, gr, u, flag);
-    case LB_FP32_SHIFTED: return recover_t<L, float, MIR>(c, src, th, gr, u, flag);
-    default: return recover_t<L, double, MIR>(c, src, th, gr, u, flag);
+    case LB_FX64: return recover_t<L, long long, MIR>(c, src, th, gr, u, flag, row0, nrow);
+    case LB_FP32_SHIFTED: return recover_t<L, float, MIR>(c, src, th, gr, u, flag, row0, nrow);
+    default: return recover_t<L, double, MIR>(c, src, th, gr, u, flag, row0, nrow);
     }
 }
 
-template <class L> static cudaError_t recover_l(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
+template <class L>
+static cudaError_t recover_l(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag, int64_t row0,
+                             int64_t nrow)
 {
-    return c->geom.mirror ? recover_m<L, true>(c, src, th, gr, u, flag) : recover_m<L, false>(c, src, th, gr, u, flag);
+    return c->geom.mirror ? recover_m<L, true>(c, src, th, gr, u, flag, row0, nrow)
+                          : recover_m<L, false>(c, src, th, gr, u, flag, row0, nrow);
 }
 
 // Self-test of the bounded wait: a barrier that nothing completes.
@@ -212,14 +221,20 @@ __global__ void staging_timeout_selftest_kernel(int *flag, unsigned long long li
     if (!mbar_wait_bounded(barp, 0, limit_ns) && threadIdx.x == 0) atomicOr(flag, 4);
 }
 
-cudaError_t launch_macros(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
+cudaError_t launch_macros_rows(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag, int64_t row0,
+                               int64_t nrow)
 {
     switch (c->d) {
-    case 1: return recover_l<D1Q3>(c, src, th, gr, u, flag);
-    case 2: return recover_l<D2Q9>(c, src, th, gr, u, flag);
-    case 3: return recover_l<D3Q19>(c, src, th, gr, u, flag);
-    default: return recover_l<D4Q33>(c, src, th, gr, u, flag);
+    case 1: return recover_l<D1Q3>(c, src, th, gr, u, flag, row0, nrow);
+    case 2: return recover_l<D2Q9>(c, src, th, gr, u, flag, row0, nrow);
+    case 3: return recover_l<D3Q19>(c, src, th, gr, u, flag, row0, nrow);
+    default: return recover_l<D4Q33>(c, src, th, gr, u, flag, row0, nrow);
     }
+}
+
+cudaError_t launch_macros(lb_ctx *c, const void *src, double *th, double *gr, double *u, int *flag)
+{
+    return launch_macros_rows(c, src, th, gr, u, flag, 0, c->geom.rows);
 }
 
 }  // namespace lbk

@@ -643,3 +643,112 @@ class Adjoint:
         self._call("lb_adjoint_info", buf)
         return {"T": int(buf[0]), "checkpoint": int(buf[1]), "checkpoints": int(buf[2]), "done": int(buf[3]),
                 "bytes": int(buf[4])}
+
+
+# --------------------------------------------------------------------------
+# One slab of a grid cut along its slowest axis (include/lb_slab.h).
+# --------------------------------------------------------------------------
+
+_slab_sigs = {
+    "lb_slab_create": (["i", "p64", "i", "i", "d", "d", "d", "relax", "i", "vp", "pvp"], "i"),
+    "lb_slab_destroy": (["vp"], "i"),
+    "lb_slab_info": (["vp", "p64"], "i"),
+    "lb_slab_ctx": (["vp"], "vp"),
+    "lb_slab_set_theta0": (["vp", "vp", "vp", "d"], "i"),
+    "lb_slab_pack": (["vp", "vp", "vp"], "i"),
+    "lb_slab_unpack": (["vp", "vp", "vp"], "i"),
+    "lb_slab_step": (["vp"], "i"),
+    "lb_slab_macros": (["vp", "vp", "vp", "vp"], "i"),
+    "lb_slab_sum_theta": (["vp", "pd"], "i"),
+}
+
+
+def _load_slab():
+    lib = load()
+    if getattr(lib, "_slab_ready", False):
+        return lib
+    m = {"i": ctypes.c_int, "d": ctypes.c_double, "vp": ctypes.c_void_p, "p64": ctypes.POINTER(ctypes.c_int64),
+         "pd": ctypes.POINTER(ctypes.c_double), "relax": ctypes.POINTER(lb_relax), "pvp": ctypes.POINTER(ctypes.c_void_p)}
+    for name, (args, res) in _slab_sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = [m[a] for a in args]
+        fn.restype = m[res]
+    lib._slab_ready = True
+    return lib
+
+
+class Slab:
+    """Part ``part`` of ``nparts`` of the periodic grid ``N``, cut along its
+    slowest axis; see include/lb_slab.h.  A step is ``pack`` -> move the two
+    buffers to the neighbours -> ``unpack`` -> ``step``; ``SlabRunner`` in
+    ``slab.py`` does the moving between processes."""
+
+    def __init__(self, d, N, part, nparts, nu, dx, dt, precision="fx64", theta_ref=0.0, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the slab solver needs a CUDA GPU; no CPU fallback exists")
+        self._lib = _load_slab()
+        self.d, self.N, self.part, self.nparts = int(d), tuple(int(n) for n in N), int(part), int(nparts)
+        arr = (ctypes.c_int64 * 4)(*(list(self.N) + [1] * (4 - self.d)))
+        rs = lb_relax(1, 0, 0, 0, 0, 0, float(theta_ref))
+        self.precision = {"fp64": LB_FP64, "fp32s": LB_FP32_SHIFTED, "fx64": LB_FX64}[precision]
+        out = ctypes.c_void_p()
+        st = self._lib.lb_slab_create(self.d, arr, self.part, self.nparts, float(nu), float(dx), float(dt),
+                                      ctypes.byref(rs), self.precision, _stream_handle(stream), ctypes.byref(out))
+        if st != LB_OK:
+            raise LBError(st, "lb_slab_create: %s" % (self._lib.lb_last_error(None) or b"").decode())
+        self.h = out
+        info = (ctypes.c_int64 * 6)()
+        self._lib.lb_slab_info(self.h, info)
+        self.z0, self.nz, self.halo_count, self.elem, self.crossing, self.layer_nodes = list(info)
+        self.ctx = ctypes.c_void_p(self._lib.lb_slab_ctx(self.h))
+        self.dtype = {8: torch.int64 if self.precision == LB_FX64 else torch.float64, 4: torch.float32}[self.elem]
+        # owned layers (lowest first) of a scalar field: shape (nz, ..., N0)
+        self.shape = (self.nz,) + tuple(reversed(self.N[:-1]))
+
+    def _call(self, name, *args):
+        _check(self._lib, self.ctx, getattr(self._lib, name)(self.h, *args), name)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lb_slab_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def halo_buffers(self, n=2):
+        """n device buffers of one pack's size, in the storage type."""
+        return [torch.empty(self.halo_count, dtype=self.dtype, device="cuda") for _ in range(n)]
+
+    def set_theta0(self, theta0_ext, grad_ext, max_abs_theta0):
+        """theta0 / grad theta0 on the owned layers plus one layer on each side."""
+        n = (self.nz + 2) * self.layer_nodes
+        self._call("lb_slab_set_theta0", _ptr(theta0_ext, "theta0", numel=n), _ptr(grad_ext, "grad", numel=self.d * n),
+                   float(max_abs_theta0))
+
+    def pack(self, send_down, send_up):
+        self._call("lb_slab_pack", _ptr(send_down, "send_down", self.dtype, self.halo_count),
+                   _ptr(send_up, "send_up", self.dtype, self.halo_count))
+
+    def unpack(self, recv_down, recv_up):
+        self._call("lb_slab_unpack", _ptr(recv_down, "recv_down", self.dtype, self.halo_count),
+                   _ptr(recv_up, "recv_up", self.dtype, self.halo_count))
+
+    def step(self):
+        self._call("lb_slab_step")
+
+    def macros(self):
+        """(theta, grad theta, u) on the owned layers."""
+        th = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        g = torch.empty((self.d,) + self.shape, dtype=torch.float64, device="cuda")
+        u = torch.empty_like(g)
+        self._call("lb_slab_macros", _ptr(th, "theta"), _ptr(g, "grad"), _ptr(u, "u"))
+        return th, g, u
+
+    def sum_theta(self):
+        v = ctypes.c_double()
+        self._call("lb_slab_sum_theta", ctypes.byref(v))
+        return v.value
