@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--sweeps", type=int, default=100, help="sweeps per benchmark step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--slab", action="store_true",
+                   help="one N^2 FX64 grid cut into one slab per rank (ghost-layer exchange every step) instead of "
+                        "independent replicas: strong scaling")
     p.add_argument("--no-blocking", action="store_true",
                    help="one sweep per launch only (skip the autotuner's blocked candidates)")
     p.add_argument("--no-variant", action="store_true", help="skip the other precisions' sub-results")
@@ -688,6 +691,36 @@ def run_adjoint(local, precision="fp64"):
     }
 
 
+def run_slab(args, world, rank, local, steps, warmup):
+    """One 2D sine grid (args.N^2, FX64) cut along y into one slab per rank;
+    every sweep is preceded by the ghost-layer exchange (NCCL point-to-point
+    between ranks; with one rank the buffers wrap onto the part itself).
+    Returns (whole-grid MLUPS, ms per sweep, bytes sent per rank and sweep)."""
+    import torch
+    from paper_2309_02825_gb300 import slab as SL
+    torch.cuda.set_device(local)
+    case = W.sine_2d(args.N)
+    N = case.N
+    th0 = torch.from_numpy(case.problem.theta(N, case.dx))
+    g0 = torch.from_numpy(np.ascontiguousarray(case.problem.grad(N, case.dx)))
+    r = SL.SlabRunner(2, N, case.nu, case.dx, case.dt, "fx64", rank=rank, world=world)
+    r.set_theta0(th0, g0)
+    r.step(warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    t = barrier_max(e0.elapsed_time(e1) / 1e3, world)
+    sent = 2 * r.slab.halo_count * r.slab.elem
+    return {"mlups": N[0] * N[1] * steps / t / 1e6, "ms_per_sweep": t / steps * 1e3, "parts": world,
+            "bytes_sent_per_rank_per_sweep": sent, "owned_layers_rank0": r.slab.nz}
+
+
 def _run_case(case, precision, theta_ref, stream, th0=None, g0=None, nsteps=None, exact=None):
     """Run one workload case to its end time; return the error norms."""
     import torch
@@ -1089,6 +1122,20 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
+    if args.slab:
+        res = run_slab(args, world, rank, local, 100 * args.steps, 10 * args.warmup)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": res["mlups"], "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_sweep"] * 100,
+                              "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int64",
+                              "data": "synthetic",
+                              "config": {"workload": "2D D2Q9 periodic %d^2 sine, FX64, one grid cut into %d slabs "
+                                                     "(step = 100 sweeps, each after a ghost-layer exchange)"
+                                                     % (args.N, world), "parallelism": "slab%d" % world},
+                              "slab": res}))
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
     peaks = load_peaks()
     main_res = run_ours(args, args.precision, world, rank, local, peaks, not args.no_e2e, True)
     per_step = None
@@ -1129,6 +1176,10 @@ def main():
     walls = None
     if not args.no_walls:
         walls = run_walls(local, peaks)
+    slab_one = None
+    if world == 1 and not args.no_walls:
+        # the slab path's exchange on one GPU: one part whose buffers wrap onto itself
+        slab_one = run_slab(args, 1, 0, local, 200, 20)
     base = None
     if rank == 0 and not args.no_cpu_baseline:
         base = cpu_baseline(args)
@@ -1170,6 +1221,8 @@ def main():
             line["sweeps_4d"] = sweeps4d
         if walls:
             line["walls"] = walls
+        if slab_one:
+            line["slab_one_part"] = slab_one
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -325,16 +325,27 @@ __device__ __forceinline__ A adj_node(A *l, const T *fv, const AdjK &K)
     return eterm;
 }
 
+// The eps-term of fixed-point nodes, before its last conversions: the FP64
+// part theta * (c0' l0 + cA' sum_a + wd' sum_diag), and the exact 128-bit
+// dot products S2 = sum P_aa s2_a, S1 = sum J_a dd_a, S3 = sum P_ab P_p of
+// the state's integer moments with the integer lambda channels.  A lane sums
+// its nodes' S (each below 6 * 2^122 in magnitude for channels below 2^59 and
+// moments below 2^63, so two nodes' sum stays far inside 2^127) and converts
+// each sum once: eps-term = d + k2' S2 + k1' S1 + k3' S3.
+struct EpsFx {
+    double d = 0.0;
+    __int128 S2 = 0, S1 = 0, S3 = 0;
+};
+
 // The node update of the fixed-point reverse pass (64-bit fixed-point states):
 // K^T from exact integer channel sums and rounded 64x62-bit products; with
-// NU, lambda . (dK/deps) f from exact 128-bit dot products of the integer
-// channels with the state's integer moments, each converted to FP64 once (on
-// the integer pipes; the int64 channel and moment values by the hardware
-// conversion, which keeps the FP64 and integer pipes in balance) and
-// combined with the FP64 eps-derivatives.  Sets
-// `range` when an output leaves |v| < 2^59 (the fields start below 2^56).
+// NU, the eps-term lambda . (dK/deps) f as EpsFx (the int64 channel and
+// moment values of its FP64 part by the hardware conversion, which keeps the
+// FP64 and integer pipes in balance).  ORs into `rng` the high words of the
+// outputs plus 2^27: an output is inside |v| < 2^59 (the fields start below
+// 2^56) exactly when that sum stays below 2^28.
 template <class L, bool NU>
-__device__ __forceinline__ double adj_node_fx(long long *l, const long long *fv, const AdjK &K, bool &range)
+__device__ __forceinline__ void adj_node_fx(long long *l, const long long *fv, const AdjK &K, unsigned &rng, EpsFx &ep)
 {
     constexpr int D = L::D, NP = D * (D - 1) / 2, B0 = 1 + 2 * D;
     const long long l0 = l[0];
@@ -353,23 +364,22 @@ __device__ __forceinline__ double adj_node_fx(long long *l, const long long *fv,
         P[p] = pl.P;
         sdg += pl.F;
     }
-    double eterm = 0.0;
     if constexpr (NU) {
         const NodeMoments<L, long long> m = node_moments<L, long long>(fv);
-        __int128 S2 = 0, S1 = 0, S3 = 0;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            S2 += (__int128)m.Paa[a] * s2[a];
-            S1 += (__int128)m.J[a] * dd[a];
+            ep.S2 += (__int128)m.Paa[a] * s2[a];
+            ep.S1 += (__int128)m.J[a] * dd[a];
         }
 #pragma unroll
-        for (int p = 0; p < NP; ++p) S3 += (__int128)m.Pab[p] * P[p];
+        for (int p = 0; p < NP; ++p) ep.S3 += (__int128)m.Pab[p] * P[p];
         const Coll<double> &kd = K.kdx;
         const double lt = fma(kd.c0, (double)l0, fma(kd.cA, (double)sax, kd.wd * (double)sdg));
-        eterm = fma((double)m.th, lt,
-                    fma(kd.k2, i128_to_f64_rn(S2), fma(kd.k1, i128_to_f64_rn(S1), kd.k3 * i128_to_f64_rn(S3))));
+        ep.d = fma((double)m.th, lt, ep.d);
     }
-    const long long Lt = mulfx(l0, K.c0k) + mulfx(sax, K.cAk) + mulfx(sdg, K.wdk);
+    // the rest channel: one rounding of the exact sum of its three products
+    const __int128 lts = (__int128)l0 * K.c0k + (__int128)sax * K.cAk + (__int128)sdg * K.wdk;
+    const long long Lt = (long long)((lts + ((__int128)1 << (kFxCoefBits - 1))) >> kFxCoefBits);
     long long LP[D], LJ[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -395,12 +405,9 @@ __device__ __forceinline__ double adj_node_fx(long long *l, const long long *fv,
         l[B0 + 4 * p + 2] = Xp - U;  // (-1, -1)
         l[B0 + 4 * p + 3] = Xm + W;  // (+1, -1)
     });
-    constexpr long long kLim = 1ll << 59;  // next step's channel sums (<= 12 terms) stay below 2^63
-    // -kLim < v < kLim as one unsigned comparison of v + (kLim - 1)
+    // next step's channel sums (<= 12 terms below 2^59) stay below 2^63
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i)
-        range |= (unsigned long long)l[i] + (unsigned long long)(kLim - 1) > (unsigned long long)(2 * kLim - 2);
-    return eterm;
+    for (int i = 0; i < L::Q; ++i) rng |= (unsigned)((unsigned long long)l[i] >> 32) + (1u << 27);
 }
 
 // The integer -> FP64 conversions of the fixed-point eps-term, for their self-test.
@@ -504,13 +511,14 @@ __global__ void __launch_bounds__(kSweepThreads) adj_seed_kernel(const T *__rest
     if (lane == 0) slot[seg] += acc;
 }
 
-// Threads per block of the reverse step: 128 for floating-point arithmetic
-// (FP32: its early-issued gathers need 72 registers, and at 256 threads a
-// 512^2 step would no longer fit one wave; FP64: at about 90 registers 128-thread
-// blocks keep 20 warps per SM resident instead of 16), 256 for fixed point.
+// Threads per block of the reverse step: 128 (FP32: its early-issued gathers
+// need 72 registers, and at 256 threads a 512^2 step would no longer fit one
+// wave; FP64: at about 90 registers 128-thread blocks keep 20 warps per SM
+// resident instead of 16; fixed point: measured 20.9 against 21.7 us per
+// 512^2 step with 256).
 template <typename A> __host__ __device__ constexpr int adj_threads()
 {
-    return std::is_same<A, long long>::value ? kSweepThreads : 128;
+    return 128;
 }
 
 // One reverse step: phi_out = K^T lambda(phi_in); eps-term if NU.
@@ -546,6 +554,7 @@ __global__ void __launch_bounds__(adj_threads<A>()) adj_step_kernel(const A *__r
     }
     EpsAcc<A> acc = 0;  // this lane's dL/deps terms
     bool range = false;
+    EpsFx ep;  // fixed point: the lane's eps-term sums, converted once below
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         A l[L::Q];
@@ -555,19 +564,30 @@ __global__ void __launch_bounds__(adj_threads<A>()) adj_step_kernel(const A *__r
             l[i] = lam[i][v];
             if constexpr (NU) fv[i] = f[i][v];
         }
-        EpsAcc<A> e;
+        // lanes past the row end hold values of the allocation's slack (never
+        // initialised): only the grid's own nodes may set the flag or add terms
+        const bool own = x0 + V * lane + v < g.N0;
         if constexpr (std::is_same<A, long long>::value) {
-            // lanes past the row end hold values of the allocation's slack
-            // (never initialised): only the grid's own nodes may set the flag
-            bool r = false;
-            e = adj_node_fx<L, NU>(l, fv, K, r);
-            if (x0 + V * lane + v < g.N0) range |= r;
+            unsigned rng = 0u;
+            EpsFx e;
+            adj_node_fx<L, NU>(l, fv, K, rng, e);
+            if (own) {
+                range |= rng >= (1u << 28);
+                ep.d += e.d;
+                ep.S2 += e.S2;
+                ep.S1 += e.S1;
+                ep.S3 += e.S3;
+            }
         } else {
-            e = adj_node<L, T, NU, A>(l, fv, K);
+            const EpsAcc<A> e = adj_node<L, T, NU, A>(l, fv, K);
+            if (NU && own) acc += e;
         }
-        if (NU && x0 + V * lane + v < g.N0) acc += e;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) lam[i][v] = l[i];
+    }
+    if constexpr (std::is_same<A, long long>::value && NU) {
+        const Coll<double> &kd = K.kdx;
+        acc = ep.d + fma(kd.k2, i128_to_f64_rn(ep.S2), fma(kd.k1, i128_to_f64_rn(ep.S1), kd.k3 * i128_to_f64_rn(ep.S3)));
     }
     if (x0 + V * lane < g.pitch) {  // lanes beyond the row only loaded
         A *dp = phi_out + row * g.pitch + x0 + V * lane;
