@@ -81,7 +81,8 @@ def parse():
     p.add_argument("--profile-sweep", default=None, metavar="D,PREC,N,STEPS",
                    help="run STEPS sweeps of one D-dimensional N^D grid at PREC and exit (for ncu captures)")
     p.add_argument("--blocking", default=None, metavar="K,TILE,THREADS",
-                   help="with --profile-sweep: blocked sweeps of K steps per launch")
+                   help="blocked sweeps of K steps per launch for the headline step (instead of the autotuner's "
+                        "pick) or for --profile-sweep")
     return p.parse_args()
 
 
@@ -290,7 +291,16 @@ def run_ours(args, precision, world, rank, local, peaks, with_e2e, label_main, b
     # one sweep per launch, or K sweeps per launch in shared memory: the
     # autotuner times both on this grid (outside the timed region)
     with torch.cuda.stream(stream):
-        tune = s.autotune(24) if blocking and not args.no_blocking else {"steps_per_launch": 0}
+        if blocking and args.blocking and label_main:
+            # pinned (K, tile, threads): the autotuner's timings are not
+            # trustworthy under a profiler, so profiled runs pin its pick
+            k_, t_, th_ = (int(v) for v in args.blocking.split(","))
+            s.set_blocking(k_, t_, th_)
+            tune = {"steps_per_launch": k_, "tile": t_, "threads": th_, "pinned": True}
+        elif blocking and not args.no_blocking:
+            tune = s.autotune(24)
+        else:
+            tune = {"steps_per_launch": 0}
     K = tune["steps_per_launch"]
     th = torch.empty(tuple(reversed(N)), dtype=torch.float64, device="cuda")
     gr = torch.empty((d,) + tuple(reversed(N)), dtype=torch.float64, device="cuda")
