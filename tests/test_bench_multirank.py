@@ -31,7 +31,7 @@ def _worker(rank, world, port, out):
 
 def test_two_gloo_ranks_aggregate_as_replicas():
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)

@@ -67,7 +67,7 @@ def _worker(rank, world, port, d, N, T, out):
                                          (2, 3, (6, 5, 2), 4)])
 def test_gloo_slabs_equal_one_grid(world, d, N, T):
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_worker, args=(world, port, d, N, T, out), nprocs=world, join=True)
         parts = dict(out)
