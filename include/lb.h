@@ -89,7 +89,13 @@ typedef struct {
  *   stream   a cudaStream_t (NULL = the legacy default stream).
  *   out      receives the context; set to NULL on failure.
  * Allocates 2*q*pitch*N[1]*N[2] distribution values on the current device.
- * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA.
+ * LB_FX64 holds the collision constants k1 = (1-s1)/2, k2 = (1-s2x)/2,
+ * k3 = (1-s22)/4, cA = s2x sigma/2 - 2(d-1) wd and wd with 64 fraction bits
+ * and needs each inside (-1/2, 1/2) (by a margin of 2^-30): k1, k2, k3
+ * always are; the paper's set keeps cA and wd inside for eps below 1.66
+ * (d = 2), 0.88 (d = 3), 0.61 (d = 4) and for every eps when d = 1.
+ * Errors: LB_EINVAL (also a constant outside that range for LB_FX64),
+ * LB_ENOMEM, LB_ECUDA.
  */
 lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt,
                     const lb_relax *rs, int precision, void *stream, lb_ctx **out);
@@ -149,7 +155,9 @@ lb_status lb_set_boundary(lb_ctx *ctx, const int *kind);
  * after synchronising the stream.  An adjoint workspace whose forward pass
  * predates the change refuses reverse steps (LB_ESTATE) until
  * lb_adjoint_forward runs again.
- * Errors: LB_EINVAL (nu not finite and > 0), LB_ECUDA.
+ * Errors: LB_EINVAL (nu not finite and > 0, a rate leaving (0, 2), or for
+ * LB_FX64 a collision constant leaving (-1/2, 1/2), as in lb_create),
+ * LB_ECUDA.
  */
 lb_status lb_set_viscosity(lb_ctx *ctx, double nu);
 
@@ -354,6 +362,20 @@ lb_status lb_selftest_staging_timeout(double limit_s, void *stream, double *wait
  */
 lb_status lb_selftest_int_to_f64(const long long *hi, const unsigned long long *lo, int64_t n, double *out128,
                                  double *out64, void *stream);
+
+/*
+ * Self-test of the fixed-point collision product: for i < n,
+ * out_split[i] = the split-word product the LB_FX64 collisions use and
+ * out_wide[i] = the same value from a 128-bit product, both
+ * floor((a[i] k[i] + 2^63) / 2^64), i.e. a[i] k[i] / 2^64 rounded to nearest
+ * with ties upward (k[i] a constant with 64 fraction bits).  The split form
+ * is exact for |k[i]| <= 2^63 - 2^34 (the range lb_create admits for the
+ * constants) and |a[i]| < 2^63 - 2^31 (the fields stay far below 2^61).  All five arrays are caller-owned device arrays
+ * of n entries; the call is ordered on `stream` and synchronises it.
+ * LB_EINVAL for n < 0 or a NULL array with n > 0.  No paper counterpart.
+ */
+lb_status lb_selftest_mulfx(const long long *a, const long long *k, int64_t n, long long *out_split,
+                            long long *out_wide, void *stream);
 
 /* Message for the last failing call on ctx (or of lb_create, with ctx == NULL). */
 const char *lb_last_error(const lb_ctx *ctx);

@@ -229,6 +229,11 @@ lb_status lb_create(int d, const int64_t *N, double nu, double dx, double dt, co
         free_ctx(c);
         return fail(nullptr, LB_EINVAL, "lb_create: relaxation rates must lie in (0, 2) and weights be finite");
     }
+    if (precision == LB_FX64 && !lbk::fx_constants_ok(*c)) {
+        free_ctx(c);
+        return fail(nullptr, LB_EINVAL, "lb_create: a fixed-point collision constant leaves (-1, 1) (weights too large "
+                                        "for LB_FX64; use LB_FP64)");
+    }
 
     // Layout.
     const int V = (precision == LB_FP32_SHIFTED) ? lbk::Vec<float>::V : lbk::Vec<double>::V;
@@ -329,6 +334,8 @@ lb_status lb_set_viscosity(lb_ctx *c, double nu)
     const lb_relax rs = {c->paper ? 1 : 0, c->s1, c->s2x, c->s22, c->w1, c->wd, c->theta_ref};
     if (!lbk::derive_params(trial, &rs))
         return fail(c, LB_EINVAL, "lb_set_viscosity: the relaxation set leaves (0, 2) at this nu");
+    if (c->precision == LB_FX64 && !lbk::fx_constants_ok(trial))
+        return fail(c, LB_EINVAL, "lb_set_viscosity: a fixed-point collision constant leaves (-1, 1) at this nu");
     DeviceGuard dg(c);
     // recorded sweeps carry the old collision constants; drain the stream before dropping them
     cudaError_t e = cudaStreamSynchronize(c->stream);

@@ -22,7 +22,7 @@
 
 namespace lbk {
 
-// Collision constants of a storage type: floating point, or 62-bit fixed point.
+// Collision constants of a storage type: floating point, or 64-bit fixed point.
 template <typename T> struct CollOf {
     using type = Coll<T>;
 };
@@ -827,7 +827,7 @@ lb_status lb_batch_create(int count, const int64_t *N, const double *nu, const d
         c.dt = dt[j];
         c.c = dx[j] / dt[j];
         c.eps = nu[j] * dt[j] / (dx[j] * dx[j]);
-        if (!lbk::derive_params(c, rs ? &rs[j] : nullptr)) {
+        if (!lbk::derive_params(c, rs ? &rs[j] : nullptr) || (precision == LB_FX64 && !lbk::fx_constants_ok(c))) {
             free_batch(b);
             return LB_EINVAL;
         }

@@ -1,6 +1,6 @@
 // Device-side building blocks shared by the sweep, recovery, fixed-point,
 // batched and adjoint kernels: compile-time loops, periodic wrap, vector
-// access, the 64x62-bit fixed-point product, the shifted pull of one
+// access, the fixed-point products, the shifted pull of one
 // population along x, where a pull reads from on periodic and mirror-wall
 // grids (pop_source), the two gather orders, and the closed-form
 // moment-space collision for D1Q3, D2Q9, D3Q19 and D4Q33
@@ -72,6 +72,29 @@ __device__ __forceinline__ long long mulfx(long long a, long long k)
 {
     const __int128 p = (__int128)a * (__int128)k;
     return (long long)((p + ((__int128)1 << (kFxCoefBits - 1))) >> kFxCoefBits);
+}
+
+// The collision product: round(a k / 2^64) = floor((a k + 2^63) / 2^64) for
+// a collision constant k with 64 fraction bits (a value in (-1/2, 1/2):
+// |k| <= 2^63 - 2^34), from four 32 x 32-bit products in place of a 128-bit
+// one.  Write a = ah 2^32 + al and k = kh 2^32 + kl with signed low words al,
+// kl in [-2^31, 2^31).  Every term of a k + 2^63 but al kl is a multiple of
+// 2^32, so
+//   floor((a k + 2^63) / 2^32) = ah kh 2^32 + m,
+//   m = ah kl + al kh + 2^31 + floor(al kl / 2^32),
+// and the result is ah kh + floor(m / 2^32).  The last two terms of m,
+// 2^31 + floor(al kl / 2^32), lie in [2^30, 3 2^30] and so fit one unsigned
+// word; |m| <= 2^62 + 2^31 (2^31 - 4) + 3 2^30 < 2^63 (|ah| <= 2^31,
+// |kh| <= 2^31 - 4).  Exact for every |a| < 2^63 - 2^31 (ah fits int32).
+__device__ __forceinline__ long long mulfx_c(long long a, long long k)
+{
+    const int kl = (int)(unsigned)(unsigned long long)k;
+    const int kh = (int)(k >> 32) + (int)((unsigned)kl >> 31);
+    const int al = (int)(unsigned)(unsigned long long)a;
+    const int ah = (int)(a >> 32) + (int)((unsigned)al >> 31);
+    const unsigned c = (unsigned)__mulhi(al, kl) + 0x80000000u;
+    const long long m = (long long)ah * kl + (long long)al * kh + (long long)(unsigned long long)c;
+    return (long long)ah * kh + (m >> 32);
 }
 
 // Integer -> FP64 with round-to-nearest-even, assembled from the IEEE 754
@@ -590,16 +613,17 @@ template <typename T> __device__ __forceinline__ void collide(D4Q33, T *f, const
 constexpr int kSweepThreads = 256;
 
 // 64-bit fixed-point collisions (precision LB_FX64): exact integer moment
-// sums, each product with a 62-fraction-bit relaxation constant rounded once
-// (mulfx), and the rest population formed as theta minus the others, so the
-// collision conserves sum f exactly.
+// sums, each product with a 64-fraction-bit relaxation constant rounded once
+// (mulfx_c; the host admits only constants in (-1/2, 1/2)), and the rest
+// population formed as theta minus the others, so the collision conserves
+// sum f exactly.
 __device__ __forceinline__ void collide(D1Q3, long long *f, const CollFx &k)
 {
     const long long P = f[1] + f[2];
     const long long th = f[0] + P;
     const long long J = f[1] - f[2];
-    const long long A = mulfx(P, k.k2) + mulfx(th, k.cA);
-    const long long B = mulfx(J, k.k1);
+    const long long A = mulfx_c(P, k.k2) + mulfx_c(th, k.cA);
+    const long long B = mulfx_c(J, k.k1);
     f[1] = A + B;
     f[2] = A - B;
     f[0] = th - 2 * A;
@@ -615,11 +639,11 @@ __device__ __forceinline__ void collide(D2Q9, long long *f, const CollFx &k)
     const long long g = f[5] - f[7], h = f[8] - f[6];
     const long long Jx = (f[1] - f[3]) + (g + h);
     const long long Jy = (f[2] - f[4]) + (g - h);
-    const long long cth = mulfx(th, k.cA);
-    const long long Ax = mulfx(Pxx, k.k2) + cth, Bx = mulfx(Jx, k.k1);
-    const long long Ay = mulfx(Pyy, k.k2) + cth, By = mulfx(Jy, k.k1);
-    const long long wth = mulfx(th, k.wd);
-    const long long B3 = mulfx(Pxy, k.k3);
+    const long long cth = mulfx_c(th, k.cA);
+    const long long Ax = mulfx_c(Pxx, k.k2) + cth, Bx = mulfx_c(Jx, k.k1);
+    const long long Ay = mulfx_c(Pyy, k.k2) + cth, By = mulfx_c(Jy, k.k1);
+    const long long wth = mulfx_c(th, k.wd);
+    const long long B3 = mulfx_c(Pxy, k.k3);
     const long long dp = wth + B3, dm = wth - B3;
     f[1] = Ax + Bx;
     f[3] = Ax - Bx;
@@ -645,39 +669,39 @@ __device__ __forceinline__ void collide(D3Q19, long long *f, const CollFx &k)
     const long long Jx = (f[1] - f[4]) + (xy.Ja + xz.Ja);
     const long long Jy = (f[2] - f[5]) + (xy.Jb + yz.Ja);
     const long long Jz = (f[3] - f[6]) + (xz.Jb + yz.Jb);
-    const long long cth = mulfx(th, k.cA);
-    const long long wth = mulfx(th, k.wd);
+    const long long cth = mulfx_c(th, k.cA);
+    const long long wth = mulfx_c(th, k.wd);
     long long axis = 0, diag = 0;
     {
-        const long long A = mulfx(Pxx, k.k2) + cth, B = mulfx(Jx, k.k1);
+        const long long A = mulfx_c(Pxx, k.k2) + cth, B = mulfx_c(Jx, k.k1);
         f[1] = A + B;
         f[4] = A - B;
         axis += A;
     }
     {
-        const long long A = mulfx(Pyy, k.k2) + cth, B = mulfx(Jy, k.k1);
+        const long long A = mulfx_c(Pyy, k.k2) + cth, B = mulfx_c(Jy, k.k1);
         f[2] = A + B;
         f[5] = A - B;
         axis += A;
     }
     {
-        const long long A = mulfx(Pzz, k.k2) + cth, B = mulfx(Jz, k.k1);
+        const long long A = mulfx_c(Pzz, k.k2) + cth, B = mulfx_c(Jz, k.k1);
         f[3] = A + B;
         f[6] = A - B;
         axis += A;
     }
     {
-        const long long B = mulfx(xy.P, k.k3), dp = wth + B, dm = wth - B;
+        const long long B = mulfx_c(xy.P, k.k3), dp = wth + B, dm = wth - B;
         f[7] = dp; f[9] = dp; f[8] = dm; f[10] = dm;
         diag += dp + dm;
     }
     {
-        const long long B = mulfx(xz.P, k.k3), dp = wth + B, dm = wth - B;
+        const long long B = mulfx_c(xz.P, k.k3), dp = wth + B, dm = wth - B;
         f[11] = dp; f[13] = dp; f[12] = dm; f[14] = dm;
         diag += dp + dm;
     }
     {
-        const long long B = mulfx(yz.P, k.k3), dp = wth + B, dm = wth - B;
+        const long long B = mulfx_c(yz.P, k.k3), dp = wth + B, dm = wth - B;
         f[15] = dp; f[17] = dp; f[16] = dm; f[18] = dm;
         diag += dp + dm;
     }
@@ -709,18 +733,18 @@ __device__ __forceinline__ void collide(D4Q33, long long *f, const CollFx &k)
         J[a] += pl[p].Ja;
         J[b] += pl[p].Jb;
     });
-    const long long cth = mulfx(th, k.cA), wth = mulfx(th, k.wd);
+    const long long cth = mulfx_c(th, k.cA), wth = mulfx_c(th, k.wd);
     long long rest = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const long long A = mulfx(P[a], k.k2) + cth, Bq = mulfx(J[a], k.k1);
+        const long long A = mulfx_c(P[a], k.k2) + cth, Bq = mulfx_c(J[a], k.k1);
         f[1 + a] = A + Bq;
         f[1 + D + a] = A - Bq;
         rest += A;
     }
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        const long long Bq = mulfx(pl[p].P, k.k3), dp = wth + Bq, dm = wth - Bq;
+        const long long Bq = mulfx_c(pl[p].P, k.k3), dp = wth + Bq, dm = wth - Bq;
         f[B0 + 4 * p] = dp;
         f[B0 + 4 * p + 1] = dm;
         f[B0 + 4 * p + 2] = dp;

@@ -154,8 +154,9 @@ template <typename T> struct Coll {
     T k1, k2, k3, c0, cA, wd;
 };
 
-// The same constants in 64-bit fixed point with 62 fractional bits (every
-// constant lies in (-2, 2)); products are rounded to nearest.  The rest
+// The same constants in 64-bit fixed point with 64 fractional bits (every
+// constant must lie in (-1/2, 1/2): fx_constants_ok); products are rounded
+// to nearest.  The rest
 // population is formed as theta minus the others, so the collision
 // conserves sum f exactly.
 struct CollFx {
@@ -170,7 +171,8 @@ struct CollFx {
 struct CollFxR : CollFx {
     int *range;
 };
-constexpr int kFxCoefBits = 62;
+constexpr int kFxCoefBits = 62;  // initialisation and adjoint constants
+constexpr int kFxCollBits = 64;  // collision constants (CollFx)
 
 // Recovery constants (Sec. III.C): u_a = ucoef * J_a / theta with
 // ucoef = (2 - s1) c; grad_a = gcoef * J_a with gcoef = -s1 / (sigma dx);
@@ -249,7 +251,13 @@ struct NvtxRange {
 // Returns false if a rate leaves (0, 2) or a weight is not finite.
 bool derive_params(lb_ctx &c, const lb_relax *rs);
 template <typename T> Coll<T> make_coll(const lb_ctx &c);
-CollFx make_coll_fx(const lb_ctx *c);  // the same constants in 62-bit fixed point
+CollFx make_coll_fx(const lb_ctx *c);  // the same constants in 64-bit fixed point
+// True when every fixed-point collision constant of c (k1, k2, k3, cA, wd)
+// lies in (-1/2 + 2^-30, 1/2 - 2^-30), the range of the collision's
+// split-word product.  Any relaxation rate in (0, 2) gives |k1|, |k2| < 1/2
+// and |k3| < 1/4; wd and cA grow with the weights (the paper's set leaves
+// the range only for eps above 1.66 in 2D, 0.88 in 3D and 0.61 in 4D).
+bool fx_constants_ok(const lb_ctx &c);
 // Device flags of a context (ctx->dflag): 0 initialisation, 1 recovery
 // (bit 0: theta <= 0 or non-finite, bit 2: a staging wait timed out),
 // 2 fixed-point sweep range (CollFxR).

@@ -85,6 +85,7 @@ def load():
             "lb_reduce_static": ([ctypes.c_int, i64, vp, vp, vp, vp, vp, vp], ctypes.c_int),
             "lb_selftest_staging_timeout": ([dbl, vp, pd], ctypes.c_int),
             "lb_selftest_int_to_f64": ([vp, vp, i64, vp, vp, vp], ctypes.c_int),
+            "lb_selftest_mulfx": ([vp, vp, i64, vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -299,6 +300,25 @@ def lb_selftest_int_to_f64(hi, lo, stream=None):
     if st != LB_OK:
         raise LBError(st, "lb_selftest_int_to_f64")
     return o128, o64
+
+
+def lb_selftest_mulfx(a, k, stream=None):
+    """(split, wide): the fixed-point collision product round(a * k / 2^62)
+    from the split-word form the collisions use and from a 128-bit product
+    (contiguous CUDA int64 tensors of equal length)."""
+    lib = load()
+    if not (isinstance(a, torch.Tensor) and isinstance(k, torch.Tensor) and a.is_cuda and k.is_cuda
+            and a.dtype == torch.int64 and k.dtype == torch.int64 and a.is_contiguous() and k.is_contiguous()
+            and a.numel() == k.numel()):
+        raise TypeError("a and k must be contiguous CUDA int64 tensors of equal length")
+    split = torch.empty_like(a)
+    wide = torch.empty_like(a)
+    st = lib.lb_selftest_mulfx(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(k.data_ptr()), a.numel(),
+                               ctypes.c_void_p(split.data_ptr()), ctypes.c_void_p(wide.data_ptr()),
+                               _stream_handle(stream))
+    if st != LB_OK:
+        raise LBError(st, "lb_selftest_mulfx")
+    return split, wide
 
 
 def lb_state_layout(ctx):
