@@ -48,9 +48,11 @@ typedef struct lb_adj lb_adj;
  *   want_nu  nonzero to also compute dL/dnu (needs the paper's relaxation
  *            set; keeps checkpoints and recomputes segments); zero computes
  *            dL/dtheta0 only and keeps no forward states.
- * Allocates ceil(T/C) + C state copies (want_nu) and two adjoint fields
- * (8 bytes per value, 4 for LB_FP32_SHIFTED).  The context must outlive the
- * workspace.
+ * Allocates ceil(T/C) + 2C state copies (want_nu; ceil(T/C) + C when there
+ * is one segment): the checkpoints and two segment buffers, so that the
+ * recomputation of one segment runs beside the reverse steps of the next;
+ * and two adjoint fields (8 bytes per value, 4 for LB_FP32_SHIFTED).  The
+ * context must outlive the workspace.
  * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA.
  */
 lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_adj **out);

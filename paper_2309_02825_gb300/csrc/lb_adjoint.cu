@@ -734,9 +734,10 @@ struct lb_adj {
     int64_t T = 0, C = 0, nck = 0;
     bool want_nu = false;
     size_t state_bytes = 0;
-    std::vector<void *> ck;   // checkpoints P_{kC}
-    std::vector<void *> seg;  // recomputed segment P_{kC + m}
-    int64_t seg_loaded = -1;
+    std::vector<void *> ck;      // checkpoints P_{kC}
+    std::vector<void *> seg[2];  // recomputed segments P_{kC + m}: segment k in seg[k & 1] (seg[0] alone if one)
+    int nseg_buf = 1;            // 2 when the next segment is recomputed while the current one is reversed
+    int64_t seg_loaded[2] = {-1, -1};
     void *phi[2] = {nullptr, nullptr};  // adjoint fields: float (FP32s), int64 fixed point (fx), else double
     bool fx = false;                     // fixed-point reverse pass (64-bit fixed-point states)
     int *dflag = nullptr;                // fixed-point range flag
@@ -748,16 +749,18 @@ struct lb_adj {
     bool forward_done = false, seeded = false;
     lbk::AdjK K{};
     size_t bytes = 0;
-    // Recorded graphs, by the parity of the buffer they start from: C forward
-    // sweeps (valid for the walls they were recorded with), and one whole
-    // reverse segment, C - 1 recompute sweeps then C reverse steps (valid for
-    // the constants K and walls they were recorded with).
+    // Recorded graphs.  fgraph[p]: C forward sweeps from buffer p (valid for
+    // the walls they were recorded with).  rgraph[p][b][pre]: one whole
+    // reverse segment, C reverse steps from adjoint buffer p over the segment
+    // held in seg[b], and with pre = 1 beside them, on a second branch, the
+    // C - 1 recompute sweeps of the previous segment into seg[b ^ 1] (valid
+    // for the constants K and walls they were recorded with).
     cudaGraphExec_t fgraph[2] = {nullptr, nullptr};
     uint64_t fgen[2] = {0, 0};  // the context's generation (walls, viscosity) each was recorded in
     uint64_t fwd_gen = 0;       // the context's generation at the last forward pass
-    cudaGraphExec_t rgraph[2] = {nullptr, nullptr};
-    lbk::AdjK rK[2]{};
-    unsigned rmirror[2] = {0u, 0u};
+    cudaGraphExec_t rgraph[2][2][2] = {};
+    lbk::AdjK rK[2][2][2]{};
+    unsigned rmirror[2][2][2] = {};
 };
 
 namespace {
@@ -778,7 +781,8 @@ void free_adj(lb_adj *a)
 {
     if (!a) return;
     for (void *p : a->ck) cudaFree(p);
-    for (void *p : a->seg) cudaFree(p);
+    for (auto &sb : a->seg)
+        for (void *p : sb) cudaFree(p);
     cudaFree(a->phi[0]);
     cudaFree(a->phi[1]);
     cudaFree(a->th0);
@@ -790,7 +794,9 @@ void free_adj(lb_adj *a)
     cudaFree(a->dflag);
     for (int p = 0; p < 2; ++p) {
         if (a->fgraph[p]) cudaGraphExecDestroy(a->fgraph[p]);
-        if (a->rgraph[p]) cudaGraphExecDestroy(a->rgraph[p]);
+        for (auto &gb : a->rgraph[p])
+            for (cudaGraphExec_t g : gb)
+                if (g) cudaGraphExecDestroy(g);
     }
     delete a;
 }
@@ -1056,22 +1062,34 @@ cudaError_t do_init(lb_adj *a, double *dth0)
     }
 }
 
-// Make P_n available (n < T): checkpoint segment k = n / C recomputed into seg.
-cudaError_t state_at(lb_adj *a, int64_t n, const void **out)
+// The segment buffer that holds (or will hold) checkpoint segment k.
+int seg_buf(const lb_adj *a, int64_t k) { return a->nseg_buf == 2 ? (int)(k & 1) : 0; }
+
+// Recompute checkpoint segment k into its buffer, on the context's stream.
+cudaError_t load_segment(lb_adj *a, int64_t k)
 {
     lb_ctx *c = a->ctx;
+    const int b = seg_buf(a, k);
+    std::vector<void *> &sg = a->seg[b];
+    cudaError_t e = cudaMemcpyAsync(sg[0], a->ck[k], a->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    const int64_t len = std::min<int64_t>(a->C, a->T - k * a->C);
+    for (int64_t m = 1; m < len; ++m)
+        if ((e = lbk::launch_sweep(c, sg[m - 1], sg[m])) != cudaSuccess) return e;
+    a->seg_loaded[b] = k;
+    return cudaSuccess;
+}
+
+// Make P_n available (n < T): checkpoint segment k = n / C recomputed into its buffer.
+cudaError_t state_at(lb_adj *a, int64_t n, const void **out)
+{
     const int64_t k = n / a->C;
-    if (a->seg_loaded != k) {
-        cudaError_t e = cudaMemcpyAsync(a->seg[0], a->ck[k], a->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    const int b = seg_buf(a, k);
+    if (a->seg_loaded[b] != k) {
+        cudaError_t e = load_segment(a, k);
         if (e != cudaSuccess) return e;
-        const int64_t len = std::min<int64_t>(a->C, a->T - k * a->C);
-        for (int64_t m = 1; m < len; ++m) {
-            e = lbk::launch_sweep(c, a->seg[m - 1], a->seg[m]);
-            if (e != cudaSuccess) return e;
-        }
-        a->seg_loaded = k;
     }
-    *out = a->seg[n - k * a->C];
+    *out = a->seg[b][n - k * a->C];
     return cudaSuccess;
 }
 
@@ -1128,13 +1146,16 @@ lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_a
     const size_t sbytes = a->state_bytes + lbk::kSlackElems * ctx->elem;  // allocation incl. slack
     if (a->want_nu) {
         a->nck = (T + C - 1) / C;
+        a->nseg_buf = a->nck >= 2 ? 2 : 1;
         a->ck.assign(a->nck, nullptr);
-        a->seg.assign(C, nullptr);
         for (auto &p : a->ck)
             if (e == cudaSuccess) e = cudaMalloc(&p, sbytes);
-        for (auto &p : a->seg)
-            if (e == cudaSuccess) e = cudaMalloc(&p, sbytes);
-        a->bytes += (a->nck + C) * sbytes;
+        for (int b = 0; b < a->nseg_buf; ++b) {
+            a->seg[b].assign(C, nullptr);
+            for (auto &p : a->seg[b])
+                if (e == cudaSuccess) e = cudaMalloc(&p, sbytes);
+        }
+        a->bytes += (a->nck + a->nseg_buf * C) * sbytes;
     }
     for (auto &p : a->phi)
         if (e == cudaSuccess) e = cudaMalloc(&p, pbytes);
@@ -1170,7 +1191,7 @@ lb_status lb_adjoint_forward(lb_adj *a, const double *theta0, double *theta, dou
     lb_ctx *c = a->ctx;
     a->ag.mirror = c->geom.mirror;  // the walls may have been set after the workspace was made
     a->forward_done = a->seeded = false;
-    a->seg_loaded = -1;
+    a->seg_loaded[0] = a->seg_loaded[1] = -1;
     lb_status st = lb_set_theta0(c, theta0, nullptr);  // FD4 gradient: a function of theta0 alone
     if (st != LB_OK) return st;
     make_adjk(a);  // after lb_set_theta0: the FX64 scale is known now
@@ -1248,31 +1269,56 @@ lb_status lb_adjoint_step(lb_adj *a, int64_t nsteps)
     for (int64_t s = 0; s < nsteps;) {
         const int64_t n = a->T - 1 - a->done;  // producing phi_n from phi_{n+1}
         const int64_t k = n / C;
-        if (a->want_nu && !cap && a->seg_loaded != k && n == k * C + C - 1 && nsteps - s >= C) {
-            // a whole segment as one recorded graph: the same launches, in the same order, as below
-            if ((e = cudaMemcpyAsync(a->seg[0], a->ck[k], a->state_bytes, cudaMemcpyDeviceToDevice, c->stream)) !=
-                cudaSuccess)
+        if (a->want_nu && !cap && n == k * C + C - 1 && nsteps - s >= C) {
+            // a whole segment as one recorded graph: its C reverse steps, the same
+            // launches in the same order as below, and beside them (two buffers)
+            // the recomputation of segment k - 1, which the next segment needs
+            const int b = seg_buf(a, k);
+            if (a->seg_loaded[b] != k && (e = load_segment(a, k)) != cudaSuccess)
+                return acuda(a, e, "lb_adjoint_step: recompute");
+            const int pre = (a->nseg_buf == 2 && k >= 1) ? 1 : 0;
+            if (pre && (e = cudaMemcpyAsync(a->seg[b ^ 1][0], a->ck[k - 1], a->state_bytes,
+                                            cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
                 return acuda(a, e, "lb_adjoint_step: checkpoint");
             const int p = a->pcur;
-            if (!a->rgraph[p] || a->rmirror[p] != a->ag.mirror || memcmp(&a->rK[p], &a->K, sizeof(a->K)) != 0) {
-                e = record_graph(c, &a->rgraph[p], [&]() {
-                    cudaError_t r = cudaSuccess;
-                    for (int64_t m = 1; m < C && r == cudaSuccess; ++m)
-                        r = lbk::launch_sweep(c, a->seg[m - 1], a->seg[m]);
-                    for (int64_t j = C - 1; j >= 0 && r == cudaSuccess; --j) {
-                        r = do_step(a, a->seg[j]);
-                        a->pcur ^= 1;
-                    }
-                    a->pcur = p;
-                    return r;
-                });
+            cudaGraphExec_t &g = a->rgraph[p][b][pre];
+            if (!g || a->rmirror[p][b][pre] != a->ag.mirror || memcmp(&a->rK[p][b][pre], &a->K, sizeof(a->K)) != 0) {
+                cudaStream_t s2 = nullptr;
+                cudaEvent_t fork = nullptr, join = nullptr;
+                e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+                if (e == cudaSuccess)
+                    e = record_graph(c, &g, [&]() {
+                        cudaError_t r = cudaSuccess;
+                        cudaStream_t main = c->stream;
+                        if (pre) {  // second branch: the C - 1 sweeps of segment k - 1
+                            if ((r = cudaEventRecord(fork, main)) != cudaSuccess ||
+                                (r = cudaStreamWaitEvent(s2, fork, 0)) != cudaSuccess)
+                                return r;
+                            c->stream = s2;
+                            for (int64_t m = 1; m < C && r == cudaSuccess; ++m)
+                                r = lbk::launch_sweep(c, a->seg[b ^ 1][m - 1], a->seg[b ^ 1][m]);
+                            c->stream = main;
+                            if (r == cudaSuccess) r = cudaEventRecord(join, s2);
+                        }
+                        for (int64_t j = C - 1; j >= 0 && r == cudaSuccess; --j) {
+                            r = do_step(a, a->seg[b][j]);
+                            a->pcur ^= 1;
+                        }
+                        a->pcur = p;
+                        if (pre && r == cudaSuccess) r = cudaStreamWaitEvent(main, join, 0);
+                        return r;
+                    });
+                if (join) cudaEventDestroy(join);
+                if (fork) cudaEventDestroy(fork);
+                if (s2) cudaStreamDestroy(s2);
                 if (e != cudaSuccess) return acuda(a, e, "lb_adjoint_step: record");
-                a->rK[p] = a->K;
-                a->rmirror[p] = a->ag.mirror;
+                a->rK[p][b][pre] = a->K;
+                a->rmirror[p][b][pre] = a->ag.mirror;
             }
-            if ((e = cudaGraphLaunch(a->rgraph[p], c->stream)) != cudaSuccess)
-                return acuda(a, e, "lb_adjoint_step: graph");
-            a->seg_loaded = k;
+            if ((e = cudaGraphLaunch(g, c->stream)) != cudaSuccess) return acuda(a, e, "lb_adjoint_step: graph");
+            if (pre) a->seg_loaded[b ^ 1] = k - 1;
             a->pcur ^= (int)(C & 1);
             a->done += C;
             s += C;
