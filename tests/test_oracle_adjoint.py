@@ -169,3 +169,73 @@ def test_oracle_results_do_not_depend_on_threads():
     for x, y in zip(a[2], b[2]):
         assert np.array_equal(x, y)
     assert a[4][0] == b[4][0] and np.array_equal(a[4][1], b[4][1]) and a[4][2] == b[4][2]
+
+
+def _complex_step_loss(d, N, nu, dx, dt, th0, ut, T):
+    """L = 1/2 sum (u(T) - ut)^2 of the forward map written out in complex
+    arithmetic, for the complex-step derivative dL/dnu = Im L(nu + ih) / h.
+    Independent of the oracle's code: the natural moments are the monomials
+    of the (pinned) velocity list, 1; e_a; e_a^2; e_a e_b; e_a e_b^2 and
+    e_a^2 e_b; e_a^2 e_b^2 (a < b), relaxed at 1, s1, s2x, s22, 1, 1
+    (Sec. III.A); the relaxation set and weights are Eq. (Bur-Sol) and
+    Eq. (d1-3-weight) in eps = nu dt / dx^2; f_0 = w theta0 - M^-1 S^-1 M g
+    with g_k = w_k e_k . dx grad theta0 (FD4 gradient, Sec. IV); each step
+    collides f* = f - M^-1 S M (f - w theta) and moves f*_i to x + e_i
+    (Eq. (distribution-f)); u_a = (2 - s1) c sum_i e_ia f_i / theta
+    (Eq. (ui-compute))."""
+    e = O.lattice(d).astype(float)
+    q = e.shape[0]
+    eps = nu * dt / (dx * dx)
+    a6 = 6.0 * eps + 1.0
+    s1, s2x = 2.0 / a6, 24.0 * eps / (a6 * a6)
+    if d == 1:
+        s22, w1, wd = 1.0, 1.0 / 6.0, 0.0
+    else:
+        s22, w1, wd = 4.0 / (6.0 * eps + 3.0), 1.0 / 6.0 - (d - 1) * eps / 3.0, eps / 6.0
+    nnz = np.count_nonzero(e, axis=1)
+    w = np.where(nnz == 0, 1.0 - 2 * d * w1 - 2 * d * (d - 1) * wd, np.where(nnz == 1, w1, wd)).astype(complex)
+    rows, rates = [np.ones(q)], [1.0]
+    for a in range(d):
+        rows.append(e[:, a])
+        rates.append(s1)
+    for a in range(d):
+        rows.append(e[:, a] ** 2)
+        rates.append(s2x)
+    for a in range(d):
+        for b in range(a + 1, d):
+            rows += [e[:, a] * e[:, b], e[:, a] * e[:, b] ** 2, e[:, a] ** 2 * e[:, b], e[:, a] ** 2 * e[:, b] ** 2]
+            rates += [s22, 1.0, 1.0, 1.0]
+    M = np.array(rows)
+    assert M.shape == (q, q)
+    Minv = np.linalg.inv(M)
+    S = np.array(rates, dtype=complex)
+    coll = Minv @ (S[:, None] * M)
+    init = Minv @ ((1.0 / S)[:, None] * M)
+    ax = lambda a: d - 1 - a  # axis a (x first) is numpy axis d-1-a
+    th0 = th0.astype(complex)
+    grad = [(-np.roll(th0, -2, ax(a)) + 8 * np.roll(th0, -1, ax(a)) - 8 * np.roll(th0, 1, ax(a)) + np.roll(th0, 2, ax(a)))
+            / (12.0 * dx) for a in range(d)]
+    g = np.stack([w[k] * dx * sum(e[k, a] * grad[a] for a in range(d)) for k in range(q)])
+    f = w.reshape((q,) + (1,) * d) * th0[None] - np.tensordot(init, g, axes=(1, 0))
+    for _ in range(T):
+        th = f.sum(axis=0)
+        fs = f - np.tensordot(coll, f - w.reshape((q,) + (1,) * d) * th[None], axes=(1, 0))
+        f = np.stack([np.roll(fs[i], tuple(int(e[i, a]) for a in range(d)), tuple(ax(a) for a in range(d)))
+                      for i in range(q)])
+    th = f.sum(axis=0)
+    u = np.stack([(2.0 - s1) * (dx / dt) * np.tensordot(e[:, a], f, axes=(0, 0)) / th for a in range(d)])
+    return 0.5 * np.sum((u - ut) ** 2)
+
+
+@pytest.mark.parametrize("d,N,T", [(1, (12,), 9), (2, (6, 5), 6), (3, (4, 4, 3), 4)])
+def test_oracle_dnu_matches_complex_step(d, N, T):
+    """dL/dnu of the oracle's adjoint against the complex-step derivative of an
+    independent complex-arithmetic forward map (no subtraction, so exact to
+    rounding at h = 1e-20 nu): the real part reproduces the oracle's loss, the
+    imaginary part its nu-gradient."""
+    th0, ut, nu, dx, dt = _case(d, N, T, 71 + d)
+    L, _, dnu = O.Model(d, N, nu, dx, dt).adjoint(th0, ut, T)
+    h = 1e-20 * nu
+    Lc = _complex_step_loss(d, N, nu + 1j * h, dx, dt, th0, ut, T)
+    assert Lc.real == pytest.approx(L, rel=1e-13)
+    assert Lc.imag / h == pytest.approx(dnu, rel=1e-12)
