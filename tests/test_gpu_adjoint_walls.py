@@ -5,8 +5,10 @@ dL/dtheta0 is checked against the exact dense Jacobian: theta0 -> f_T is
 linear (initialisation with the reflected fourth-order gradient, then T
 linear steps), so its columns are oracle runs of unit vectors, and
 u = (2 - s1) c J / theta is differentiated by hand.  dL/dnu is checked
-against central differences of the oracle's own loss.  The loss is
-L = 1/2 sum over the grid's nodes of |u(T) - u_target|^2.
+against the complex-step derivative of the same wall model (the complex
+forward map of the oracle tests, on the evenly doubled grid, restricted to
+the grid's nodes), whose real part must reproduce the oracle's loss.  The
+loss is L = 1/2 sum over the grid's nodes of |u(T) - u_target|^2.
 """
 import numpy as np
 import pytest
@@ -15,6 +17,7 @@ import torch
 import oracle as O
 from paper_2309_02825_gb300 import lb
 from paper_2309_02825_gb300 import workloads as W
+from tests.test_oracle_adjoint import complex_forward_u
 
 pytestmark = pytest.mark.gpu
 
@@ -43,6 +46,16 @@ def _oracle_loss(d, N, mirror, nu, dx, dt, th0, ut, T):
     m = O.MirrorModel(d, N, mirror, nu, dx, dt)
     _, _, u = m.recover(m.run(m.initialize(th0), T))
     return 0.5 * float(np.sum((u - ut) ** 2))
+
+
+def _complex_step_dnu(d, N, mirror, nu, dx, dt, th0, ut, T):
+    """(L, dL/dnu) of the wall model by the complex step h = 1e-20 nu."""
+    h = 1e-20 * nu
+    full = O.even_extension(th0, d, mirror)
+    Nf = tuple(reversed(full.shape))
+    u = O.restrict(complex_forward_u(d, Nf, nu + 1j * h, dx, dt, full, T), d, N, vector=True)
+    L = 0.5 * np.sum((u - ut) ** 2)
+    return L.real, L.imag / h
 
 
 def _dense_gradient(d, N, mirror, nu, dx, dt, th0, ut, T):
@@ -86,13 +99,12 @@ def test_wall_adjoint_matches_dense_jacobian_and_nu_differences(d, N, mirror, T,
     g_ref = _dense_gradient(d, N, mirror, nu, dx, dt, th0, ut, T)
     g, dnu = _gpu_gradient(d, N, mirror, nu, dx, dt, th0, ut, T, precision)
     rel = np.max(np.abs(g - g_ref)) / np.max(np.abs(g_ref))
-    h = 1e-6 * nu
-    fd = (_oracle_loss(d, N, mirror, nu + h, dx, dt, th0, ut, T)
-          - _oracle_loss(d, N, mirror, nu - h, dx, dt, th0, ut, T)) / (2 * h)
+    L_cs, dnu_cs = _complex_step_dnu(d, N, mirror, nu, dx, dt, th0, ut, T)
+    assert L_cs == pytest.approx(_oracle_loss(d, N, mirror, nu, dx, dt, th0, ut, T), rel=1e-13)
     print("wall adjoint %s d=%d N=%s walls=%s: dtheta0 rel %.2e, dnu rel %.2e"
-          % (precision, d, N, mirror, rel, abs(dnu / fd - 1)))
+          % (precision, d, N, mirror, rel, abs(dnu / dnu_cs - 1)))
     assert rel <= 1e-12
-    assert dnu == pytest.approx(fd, rel=1e-6)
+    assert dnu == pytest.approx(dnu_cs, rel=1e-12)
 
 
 def test_wall_adjoint_fp32_shifted_tracks_fp64():

@@ -171,9 +171,9 @@ def test_oracle_results_do_not_depend_on_threads():
     assert a[4][0] == b[4][0] and np.array_equal(a[4][1], b[4][1]) and a[4][2] == b[4][2]
 
 
-def _complex_step_loss(d, N, nu, dx, dt, th0, ut, T):
-    """L = 1/2 sum (u(T) - ut)^2 of the forward map written out in complex
-    arithmetic, for the complex-step derivative dL/dnu = Im L(nu + ih) / h.
+def complex_forward_u(d, N, nu, dx, dt, th0, T):
+    """u(T) of the forward map on a periodic grid, written out in complex
+    arithmetic, for complex-step derivatives in nu (L(nu + ih), Im L / h).
     Independent of the oracle's code: the natural moments are the monomials
     of the (pinned) velocity list, 1; e_a; e_a^2; e_a e_b; e_a e_b^2 and
     e_a^2 e_b; e_a^2 e_b^2 (a < b), relaxed at 1, s1, s2x, s22, 1, 1
@@ -223,8 +223,12 @@ def _complex_step_loss(d, N, nu, dx, dt, th0, ut, T):
         f = np.stack([np.roll(fs[i], tuple(int(e[i, a]) for a in range(d)), tuple(ax(a) for a in range(d)))
                       for i in range(q)])
     th = f.sum(axis=0)
-    u = np.stack([(2.0 - s1) * (dx / dt) * np.tensordot(e[:, a], f, axes=(0, 0)) / th for a in range(d)])
-    return 0.5 * np.sum((u - ut) ** 2)
+    return np.stack([(2.0 - s1) * (dx / dt) * np.tensordot(e[:, a], f, axes=(0, 0)) / th for a in range(d)])
+
+
+def _complex_step_loss(d, N, nu, dx, dt, th0, ut, T):
+    """L = 1/2 sum (u(T) - ut)^2 from complex_forward_u."""
+    return 0.5 * np.sum((complex_forward_u(d, N, nu, dx, dt, th0, T) - ut) ** 2)
 
 
 @pytest.mark.parametrize("d,N,T", [(1, (12,), 9), (2, (6, 5), 6), (3, (4, 4, 3), 4)])
