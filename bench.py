@@ -698,7 +698,20 @@ def run_adjoint(local, precision="fp64"):
         "gradient_total_cost_vs_forward": (t_fwd + t_bwd) / (T * t_sweep),
         "loss": L, "dL_dnu": dnu, "fd_rel_err_theta0_dirs": checks, "fd_rel_err_nu": abs(dnu / fd_nu - 1.0),
         "workspace_bytes": info["bytes"],
+        # per reverse step: the reverse kernel reads lambda_{n+1} and f_n and writes lambda_n (q values each per
+        # node), and the segment recompute runs one forward sweep (reads and writes q values per node)
+        "algorithmic_bytes_per_reverse_step": _adj_bytes(case, precision)[0],
+        "bytes_vs_forward_step": _adj_bytes(case, precision)[0] / _adj_bytes(case, precision)[1],
     }
+
+
+def _adj_bytes(case, precision):
+    """(algorithmic bytes of one reverse step incl. its recompute sweep, of one forward sweep)."""
+    q, nodes = 1 + 2 * case.d * case.d, int(np.prod(case.N))
+    es = 4 if precision == "fp32s" else 8  # stored state value
+    ea = 4 if precision == "fp32s" else 8  # adjoint field value (float, int64 fixed point or double)
+    fwd = 2 * q * es * nodes
+    return (2 * q * ea + q * es) * nodes + fwd, fwd
 
 
 def run_slab(args, world, rank, local, steps, warmup):
