@@ -90,3 +90,14 @@ def test_fx64_rejects_constants_outside_half_interval(d, eps_ok, eps_bad):
         s.set_viscosity(eps_bad * dx * dx / dt)
     assert ei.value.status == lb.LB_EINVAL
     s.close()
+
+
+def test_fx64_batch_refuses_an_instance_outside_the_range():
+    """lb_batch_create applies the same rule per instance."""
+    dx, dt = 0.1, 0.1
+    nus = [0.2 * dx * dx / dt, 1.7 * dx * dx / dt]  # eps = 0.2 and 1.7 (2D limit 1.66)
+    with pytest.raises(lb.LBError) as ei:
+        lb.Batch([(8, 8), (8, 8)], nus, [dx, dx], [dt, dt], precision="fx64")
+    assert ei.value.status == lb.LB_EINVAL
+    lb.Batch([(8, 8), (8, 8)], nus, [dx, dx], [dt, dt], precision="fp64").close()
+    lb.Batch([(8, 8)], nus[:1], [dx], [dt], precision="fx64").close()
