@@ -220,8 +220,9 @@ lb_status lb_get_blocking(const lb_ctx *ctx, int *info);
 
 /*
  * Times about trial_steps steps (rounded up to whole launches) for one sweep
- * per launch and for blocked sweeps (K = 2, 4, 6, 8, 12 x the largest square
- * tile that fits one to four blocks per SM x 256, 512, 1024 threads) on this
+ * per launch and for blocked sweeps (K = 2, 3, 4, 5, 6, 8, 12 x the largest
+ * square tile that fits one to four blocks per SM and that tile less 4 nodes
+ * x 256, 512, 1024 threads) on this
  * grid and keeps the fastest (lb_set_blocking).  The trials overwrite the
  * state: call lb_set_theta0 afterwards.  A grid that blocking does not cover
  * (d != 2, walls) keeps one sweep per launch.  choice (host, may be NULL)

@@ -415,14 +415,16 @@ lb_status lb_autotune(lb_ctx *c, int trial_steps, double *choice)
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device)) != cudaSuccess)
         return cuda_fail(c, e, "lb_autotune");
     const int node_bytes = 9 * (int)c->elem;
-    for (int K : {2, 4, 6, 8, 12})
+    for (int K : {2, 3, 4, 5, 6, 8, 12})
         for (int per_sm : {1, 2, 3, 4}) {
             const long avail = per_sm == 1 ? optin : optin / per_sm - 1024;
             int edge = (int)floor(sqrt((double)avail / node_bytes));
             while ((long)edge * edge * node_bytes > avail) --edge;
-            const int tile = edge - 2 * K;
-            if (tile < 8) continue;
-            for (int th : {256, 512, 1024}) cands.push_back({K, tile, th});
+            // the largest square tile for this many blocks per SM, and one 4 nodes smaller (less work per block)
+            for (int tile : {edge - 2 * K, edge - 2 * K - 4}) {
+                if (tile < 8) continue;
+                for (int th : {256, 512, 1024}) cands.push_back({K, tile, th});
+            }
         }
     const bool was_init = c->initialized;
     c->initialized = true;  // the trials step whatever the buffers hold

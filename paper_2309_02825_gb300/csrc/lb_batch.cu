@@ -1006,8 +1006,8 @@ lb_status lb_batch_autotune(lb_batch *b, int trial_steps, double *choice)
     // size); one instance per group is the naive baseline and never the
     // fastest, so it is left out (lb_batch_set_schedule can still select it);
     // (b) blocked launches: K steps per launch x tile edge (the largest that
-    // fits one, two, three or four blocks per SM with a K-node halo) x block
-    // size.
+    // fits one, two, three or four blocks per SM with a K-node halo, and that
+    // edge less 4) x block size.
     struct Cand {
         double budget;
         int threads, K, tile;
@@ -1018,14 +1018,16 @@ lb_status lb_batch_autotune(lb_batch *b, int trial_steps, double *choice)
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device) != cudaSuccess)
         return bfail(b, LB_ECUDA, "lb_batch_autotune: device attribute");
-    for (int K : {2, 4, 6, 8, 12})
+    for (int K : {2, 3, 4, 5, 6, 8, 12})
         for (int per_sm : {1, 2, 3, 4}) {
             const size_t avail = per_sm == 1 ? (size_t)optin : (size_t)optin / per_sm - 1024;
             int edge = 1;  // largest square tile + halo whose buffers fit
             while (lbk::tb_smem_bytes(9, (int)b->elem, edge + 1, edge + 1) <= avail) ++edge;
-            const int tile = edge - 2 * K;
-            if (tile < 8) continue;
-            for (int th : {256, 512, 1024}) cands.push_back({b->budget, th, K, tile});
+            // that tile, and one 4 nodes smaller (less work per block)
+            for (int tile : {edge - 2 * K, edge - 2 * K - 4}) {
+                if (tile < 8) continue;
+                for (int th : {256, 512, 1024}) cands.push_back({b->budget, th, K, tile});
+            }
         }
     double best = 1e300;
     Cand win = {b->budget, b->threads, b->tb_k, b->tb_tile};
