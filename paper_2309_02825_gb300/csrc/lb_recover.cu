@@ -124,34 +124,87 @@ __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ sr
 
     const int x = x0 + (int)threadIdx.x;
     if (x >= g.N0) return;
-    using A = typename RecAcc<T>::type;
-    A th = 0, J[4] = {0, 0, 0, 0};
+    T vals[L::Q];
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int ex = L::E[i][0];
         const int sx = x - ex;
-        T v;
         if (sx >= 0 && sx < g.N0) {
-            v = tile[i * TW + (sx - x0 + H)];
+            vals[i] = tile[i * TW + (sx - x0 + H)];
         } else {  // across the row end: a scalar from the other end, or the x-reflection
             const PopSrc ps = pop_source<L, i, MIR>(g, rpos);
             if (MIR && (g.mirror & 1u))
-                v = src[(int64_t)ps.popx * g.slab + ps.row * g.pitch + (sx < 0 ? 1 : g.N0 - 2)];
+                vals[i] = src[(int64_t)ps.popx * g.slab + ps.row * g.pitch + (sx < 0 ? 1 : g.N0 - 2)];
             else
-                v = src[(int64_t)ps.pop * g.slab + ps.row * g.pitch + (sx < 0 ? g.N0 - 1 : 0)];
+                vals[i] = src[(int64_t)ps.pop * g.slab + ps.row * g.pitch + (sx < 0 ? g.N0 - 1 : 0)];
         }
-        const A fv = (A)v;
-        th += fv;
-        static_for<0, L::D>([&](auto Ad) {
-            constexpr int a = decltype(Ad)::value;
-            constexpr int e = L::E[i][a];
-            if constexpr (e == 1) J[a] += fv;
-            if constexpr (e == -1) J[a] -= fv;
-        });
     });
+    double thm, Jd[4];  // theta - theta_ref and J in storage units
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 shifted storage: sums on the integer pipes instead of FP64
+        // additions (GB300 issues FP64 at 1/64 of its integer rate).  Each
+        // float is m 2^(e - 150) with a 24-bit m (e the biased exponent, 1 for
+        // subnormals); aligned to the node's largest exponent E with m placed at
+        // bit PB it is the integer m 2^(PB + e - E).  PB leaves room for the
+        // sum of Q such values below 2^62, and only bits below 2^-(PB + 23) of
+        // the largest value are dropped (at least 2^-55; FP64 addition rounds
+        // at 2^-53).  The sums are converted to FP64 once each and scaled by
+        // 2^(E - 150 - PB).
+        constexpr int PB = 62 - 24 - (L::Q <= 4 ? 2 : L::Q <= 16 ? 4 : L::Q <= 32 ? 5 : 6);
+        unsigned emax = 1;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const unsigned e = (__float_as_uint(vals[i]) >> 23) & 0xffu;
+            emax = e > emax ? e : emax;
+        }
+        long long thi = 0, Ji[4] = {0, 0, 0, 0};
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const unsigned b = __float_as_uint(vals[i]);
+            const unsigned e = (b >> 23) & 0xffu;
+            const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | (e ? 0x800000u : 0u)) << PB;
+            const unsigned sh = emax - (e ? e : 1u);
+            const long long mag = (long long)(sh < 64u ? (m >> sh) : 0ull);
+            const long long fv = (b >> 31) ? -mag : mag;
+            thi += fv;
+            static_for<0, L::D>([&](auto Ad) {
+                constexpr int a = decltype(Ad)::value;
+                constexpr int ev = L::E[i][a];
+                if constexpr (ev == 1) Ji[a] += fv;
+                if constexpr (ev == -1) Ji[a] -= fv;
+            });
+        });
+        const double sc = __longlong_as_double((long long)(emax + 1023u - 150u - PB) << 52);  // 2^(E - 150 - PB), normal
+        thm = emax == 0xffu ? __longlong_as_double(0x7ff8000000000000ll) : i64_to_f64_rn(thi) * sc;
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) Jd[a] = i64_to_f64_rn(Ji[a]) * sc;
+    } else {
+        using A = typename RecAcc<T>::type;
+        A th = 0, J[4] = {0, 0, 0, 0};
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const A fv = (A)vals[i];
+            th += fv;
+            static_for<0, L::D>([&](auto Ad) {
+                constexpr int a = decltype(Ad)::value;
+                constexpr int e = L::E[i][a];
+                if constexpr (e == 1) J[a] += fv;
+                if constexpr (e == -1) J[a] -= fv;
+            });
+        });
+        if constexpr (std::is_same<A, long long>::value) {  // exact integer sums, converted on the integer pipes
+            thm = i64_to_f64_rn(th) * scale;
+#pragma unroll
+            for (int a = 0; a < L::D; ++a) Jd[a] = i64_to_f64_rn(J[a]);
+        } else {
+            thm = th * scale;
+#pragma unroll
+            for (int a = 0; a < L::D; ++a) Jd[a] = J[a];
+        }
+    }
     const int64_t nodes = (int64_t)g.N0 * nrow;
     const int64_t node = (row - row0) * g.N0 + x;
-    const double thd = (double)th * scale + r.theta_ref;
+    const double thd = thm + r.theta_ref;
     if (theta) theta[node] = thd;
     {  // theta > 0 and finite, as bit tests on the integer pipes
         const long long tb = __double_as_longlong(thd);
@@ -160,7 +213,7 @@ __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ sr
     const double cu = r.ucoef / thd;  // the storage scale is folded into ucoef and gcoef
 #pragma unroll
     for (int a = 0; a < L::D; ++a) {
-        const double Ja = (double)J[a];
+        const double Ja = Jd[a];
         if (grad) grad[a * nodes + node] = r.gcoef * Ja;
         if (u) u[a * nodes + node] = cu * Ja;
     }

@@ -92,3 +92,52 @@ def test_fp32_shifted_tracks_exact_solution():
         errs.append(s.reduce(th, u, et, eu))
     assert errs[1]["u0"]["rmse"] < 3 * errs[0]["u0"]["rmse"]
     assert errs[1]["theta"]["rmse"] < 10 * errs[0]["theta"]["rmse"]
+
+
+@pytest.mark.parametrize("d,N", [(1, (37,)), (2, (20, 12)), (3, (9, 7, 5))])
+def test_fp32s_recovery_sums_match_exact_arithmetic(d, N):
+    """The FP32-shifted recovery sums the q stored floats of a node on the
+    integer pipes, aligned to the node's largest exponent.  On a loaded state
+    whose values span 12 decades, with zeros, subnormals and both signs,
+    theta = theta_ref + sum_i P_i(x - e_i), J_a = sum_i e_ia P_i(x - e_i) and
+    u = (2 - s1) c J / theta must equal exact arithmetic (math.fsum) to a few
+    units of the last place."""
+    import math
+
+    dx = 1.0 / max(N)
+    s = lb.Solver(d, N, 0.02, dx, 0.2 * dx * dx / 0.02, precision="fp32s", theta_ref=2.0)
+    pitch, slab, _ = s.state_layout()
+    e = O.lattice(d)
+    q = e.shape[0]
+    shape = tuple(reversed(N))
+    rng = np.random.default_rng(7 + d)
+    vals = rng.standard_normal((q,) + shape) * 10.0 ** rng.integers(-12, 0, (q,) + shape)
+    r = rng.random(vals.shape)
+    vals[r < 0.1] = 0.0
+    vals[(r >= 0.1) & (r < 0.15)] = 3e-40 * np.sign(rng.standard_normal(np.count_nonzero((r >= 0.1) & (r < 0.15))))
+    vals = vals.astype(np.float32)
+    state = np.zeros(q * slab, dtype=np.float32)
+    rows = int(np.prod(shape[:-1]))
+    for i in range(q):
+        plane = state[i * slab:(i + 1) * slab].reshape(rows, pitch)
+        plane[:, :N[0]] = vals[i].reshape(rows, N[0])
+    s.load_state(torch.from_numpy(state).cuda(), 0)
+    th, g, u = [t.cpu().numpy() for t in s.macros()]
+    p = s.params
+    ucoef = (2.0 - p["s1"]) * p["c"]
+    # the pulled values P_i(x - e_i): roll population i by +e_i along each axis (x is the last array axis)
+    pulled = [np.roll(vals[i].astype(np.float64), tuple(int(e[i, a]) for a in range(d)),
+                      tuple(d - 1 - a for a in range(d))) for i in range(q)]
+    th_x = np.empty(shape)
+    J_x = np.empty((d,) + shape)
+    for idx in np.ndindex(*shape):
+        col = [pv[idx] for pv in pulled]
+        th_x[idx] = math.fsum([2.0] + col)
+        for a in range(d):
+            J_x[(a,) + idx] = math.fsum([float(e[i, a]) * col[i] for i in range(q)])
+    u_x = ucoef * J_x / th_x[None]
+    assert np.max(np.abs(th - th_x)) <= 4 * np.spacing(2.0)
+    assert np.max(np.abs(u - u_x)) <= 1e-14 * np.max(np.abs(u_x))
+    gcoef = -p["s1"] / (p["cs2"] / p["c"] ** 2 * dx)  # grad theta = -s1 J / (sigma dx), Sec. III.C
+    assert np.max(np.abs(g - gcoef * J_x)) <= 1e-14 * np.max(np.abs(gcoef * J_x))
+    s.close()
