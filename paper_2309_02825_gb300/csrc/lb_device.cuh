@@ -147,6 +147,51 @@ __device__ __forceinline__ double i64_to_f64_rn(long long v)
     return u64_bits_to_f64(a, v < 0 ? 0x8000000000000000ull : 0ull);
 }
 
+// Exact sums of floats on the integer pipes (GB300 issues FP64 at 1/64 of its
+// integer rate).  A float is m 2^(e - 150) with a 24-bit m (e its biased
+// exponent, read as 1 for subnormals).  Aligned to the largest exponent E of
+// the values summed, with m at bit PB, it is the integer m 2^(PB + e - E);
+// f32_align_bit<N>() leaves room for N such values below 2^62, and only bits
+// below 2^-(PB + 23) of the largest value are dropped (at least 2^-55; FP64
+// addition rounds at 2^-53).  A sum is converted to FP64 once and scaled by
+// f32_scale<PB>(E) = 2^(E - 150 - PB).
+template <int N> __host__ __device__ constexpr int f32_align_bit()
+{
+    return 62 - 24 - (N <= 4 ? 2 : N <= 16 ? 4 : N <= 32 ? 5 : 6);
+}
+__device__ __forceinline__ unsigned f32_exp(float v)
+{
+    const unsigned e = (__float_as_uint(v) >> 23) & 0xffu;
+    return e ? e : 1u;
+}
+template <int PB> __device__ __forceinline__ long long f32_align(float v, unsigned emax)
+{
+    const unsigned b = __float_as_uint(v);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | (e ? 0x800000u : 0u)) << PB;
+    const unsigned sh = emax - (e ? e : 1u);
+    const long long mag = (long long)(sh < 64u ? (m >> sh) : 0ull);
+    return (b >> 31) ? -mag : mag;
+}
+template <int PB> __device__ __forceinline__ double f32_scale(unsigned emax)
+{
+    return __longlong_as_double((long long)(emax + 1023u - 150u - PB) << 52);  // normal for every emax <= 254
+}
+
+// Sum of N floats rounded once to FP64 (NaN if any is not finite).
+template <int N> __device__ __forceinline__ double sum_f32_int(const float (&v)[N])
+{
+    constexpr int PB = f32_align_bit<N>();
+    unsigned emax = 1;
+#pragma unroll
+    for (int i = 0; i < N; ++i) emax = max(emax, f32_exp(v[i]));
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) s += f32_align<PB>(v[i], emax);
+    if (emax == 0xffu) return __longlong_as_double(0x7ff8000000000000ll);
+    return i64_to_f64_rn(s) * f32_scale<PB>(emax);
+}
+
 __device__ __forceinline__ double i128_to_f64_rn(__int128 v)
 {
     const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;

@@ -127,6 +127,37 @@ __global__ void init_kernel(T *__restrict__ dst, Geom g, InitK K, const double *
             rest += v;
         });
         val[0] = t - rest;
+    } else if constexpr (std::is_same<T, float>::value) {
+        // FP32 shifted storage: f_i - w_i theta_ref formed from theta0 - theta_ref
+        // and the gradient terms, each shared term computed once (the float
+        // rounding of the stored value dominates; FP64 issues at 1/64 of the
+        // FP32 rate on this part, so the FP64 operations per node are kept few)
+        const double dth = th - K.theta_ref;
+        const double b0 = K.w0 * dth, b1 = K.w1 * dth, bd = K.wd * dth;
+        double ga[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) ga[a] = K.iax * gr[a];
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int ex = L::E[i][0], ey = L::E[i][1], ez = L::E[i][2], ew = L::E[i][3];
+            constexpr int nz = (ex != 0) + (ey != 0) + (ez != 0) + (ew != 0);
+            double v;
+            if constexpr (nz == 0) {
+                v = b0;
+            } else if constexpr (nz == 1) {
+                constexpr int a = (ex != 0) ? 0 : ((ey != 0) ? 1 : ((ez != 0) ? 2 : 3));
+                constexpr int sgn = (ex != 0) ? ex : ((ey != 0) ? ey : ((ez != 0) ? ez : ew));
+                v = sgn > 0 ? b1 - ga[a] : b1 + ga[a];
+            } else {
+                double edg = 0.0;
+                if constexpr (ex != 0) edg += (double)ex * gr[0];
+                if constexpr (ey != 0) edg += (double)ey * gr[1];
+                if constexpr (ez != 0) edg += (double)ez * gr[2];
+                if constexpr (ew != 0) edg += (double)ew * gr[3];
+                v = fma(-K.idg, edg, bd);
+            }
+            val[i] = (T)v;
+        });
     } else {
         static_for<0, Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
@@ -341,6 +372,13 @@ __global__ void __launch_bounds__(kRedThreads) sum_state_kernel(const T *__restr
                 if (x0 + j * 32 * V < g.N0) ld_vec(rowp + x0 + j * 32 * V, a[j]);
 #pragma unroll
             for (int j = 0; j < U; ++j) {
+                if constexpr (std::is_same<T, float>::value) {
+                    // a whole vector of floats: one integer-pipe sum and one FP64 addition
+                    if (!g.mirror && x0 + j * 32 * V + V <= g.N0) {
+                        acc += sum_f32_int(a[j]);
+                        continue;
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < V; ++k) {
                     const int x = x0 + j * 32 * V + k;

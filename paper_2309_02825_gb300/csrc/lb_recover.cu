@@ -141,31 +141,16 @@ __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ sr
     });
     double thm, Jd[4];  // theta - theta_ref and J in storage units
     if constexpr (std::is_same<T, float>::value) {
-        // FP32 shifted storage: sums on the integer pipes instead of FP64
-        // additions (GB300 issues FP64 at 1/64 of its integer rate).  Each
-        // float is m 2^(e - 150) with a 24-bit m (e the biased exponent, 1 for
-        // subnormals); aligned to the node's largest exponent E with m placed at
-        // bit PB it is the integer m 2^(PB + e - E).  PB leaves room for the
-        // sum of Q such values below 2^62, and only bits below 2^-(PB + 23) of
-        // the largest value are dropped (at least 2^-55; FP64 addition rounds
-        // at 2^-53).  The sums are converted to FP64 once each and scaled by
-        // 2^(E - 150 - PB).
-        constexpr int PB = 62 - 24 - (L::Q <= 4 ? 2 : L::Q <= 16 ? 4 : L::Q <= 32 ? 5 : 6);
+        // FP32 shifted storage: theta and J summed on the integer pipes
+        // (f32_align in lb_device.cuh), each rounded once to FP64
+        constexpr int PB = f32_align_bit<L::Q>();
         unsigned emax = 1;
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-            const unsigned e = (__float_as_uint(vals[i]) >> 23) & 0xffu;
-            emax = e > emax ? e : emax;
-        }
+        for (int i = 0; i < L::Q; ++i) emax = max(emax, f32_exp(vals[i]));
         long long thi = 0, Ji[4] = {0, 0, 0, 0};
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            const unsigned b = __float_as_uint(vals[i]);
-            const unsigned e = (b >> 23) & 0xffu;
-            const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | (e ? 0x800000u : 0u)) << PB;
-            const unsigned sh = emax - (e ? e : 1u);
-            const long long mag = (long long)(sh < 64u ? (m >> sh) : 0ull);
-            const long long fv = (b >> 31) ? -mag : mag;
+            const long long fv = f32_align<PB>(vals[i], emax);
             thi += fv;
             static_for<0, L::D>([&](auto Ad) {
                 constexpr int a = decltype(Ad)::value;
@@ -174,7 +159,7 @@ __global__ void __launch_bounds__(kTile) recover_kernel(const T *__restrict__ sr
                 if constexpr (ev == -1) Ji[a] -= fv;
             });
         });
-        const double sc = __longlong_as_double((long long)(emax + 1023u - 150u - PB) << 52);  // 2^(E - 150 - PB), normal
+        const double sc = f32_scale<PB>(emax);
         thm = emax == 0xffu ? __longlong_as_double(0x7ff8000000000000ll) : i64_to_f64_rn(thi) * sc;
 #pragma unroll
         for (int a = 0; a < L::D; ++a) Jd[a] = i64_to_f64_rn(Ji[a]) * sc;
