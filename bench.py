@@ -1176,6 +1176,9 @@ def main():
                      "error": v["error"], "sweep_ms": v["sweep_ms"], "blocking": v["blocking"]}
             if "roofline_fp64_pipe" in v:
                 entry["roofline_fp64_pipe"] = v["roofline_fp64_pipe"]
+            if other == "fp64":
+                entry["note"] = ("native FP64 arithmetic, bound by the FP64 pipe (1/64 of the FP32 rate on this part); "
+                                 "the FP64-accurate result at the HBM rate and beyond is the 64-bit fixed-point line")
             variants.append(entry)
     batched = None
     if not args.no_batched:
