@@ -48,11 +48,13 @@ typedef struct lb_adj lb_adj;
  *   want_nu  nonzero to also compute dL/dnu (needs the paper's relaxation
  *            set; keeps checkpoints and recomputes segments); zero computes
  *            dL/dtheta0 only and keeps no forward states.
- * Allocates ceil(T/C) + 2C state copies (want_nu; ceil(T/C) + C when there
- * is one segment): the checkpoints and two segment buffers, so that the
- * recomputation of one segment runs beside the reverse steps of the next;
- * and two adjoint fields (8 bytes per value, 4 for LB_FP32_SHIFTED).  The
- * context must outlive the workspace.
+ * Allocates ceil(T/C) + 2C state copies (want_nu): the checkpoints and two
+ * segment buffers, so that the recomputation of one segment runs beside the
+ * reverse steps of the next; the second segment buffer is left out (and
+ * segments recomputed one at a time) when there is one segment or the device
+ * has no room for it, which lb_adjoint_info's byte count shows.  Also two
+ * adjoint fields (8 bytes per value, 4 for LB_FP32_SHIFTED).  The context
+ * must outlive the workspace.
  * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA.
  */
 lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_adj **out);

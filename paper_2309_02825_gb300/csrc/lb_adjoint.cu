@@ -1146,16 +1146,14 @@ lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_a
     const size_t sbytes = a->state_bytes + lbk::kSlackElems * ctx->elem;  // allocation incl. slack
     if (a->want_nu) {
         a->nck = (T + C - 1) / C;
-        a->nseg_buf = a->nck >= 2 ? 2 : 1;
+        a->nseg_buf = 1;  // a second segment buffer is added below when the device has room for it
         a->ck.assign(a->nck, nullptr);
         for (auto &p : a->ck)
             if (e == cudaSuccess) e = cudaMalloc(&p, sbytes);
-        for (int b = 0; b < a->nseg_buf; ++b) {
-            a->seg[b].assign(C, nullptr);
-            for (auto &p : a->seg[b])
-                if (e == cudaSuccess) e = cudaMalloc(&p, sbytes);
-        }
-        a->bytes += (a->nck + a->nseg_buf * C) * sbytes;
+        a->seg[0].assign(C, nullptr);
+        for (auto &p : a->seg[0])
+            if (e == cudaSuccess) e = cudaMalloc(&p, sbytes);
+        a->bytes += (a->nck + C) * sbytes;
     }
     for (auto &p : a->phi)
         if (e == cudaSuccess) e = cudaMalloc(&p, pbytes);
@@ -1171,6 +1169,26 @@ lb_status lb_adjoint_create(lb_ctx *ctx, int64_t T, int64_t C, int want_nu, lb_a
     if (e != cudaSuccess) {
         free_adj(a);
         return e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA;
+    }
+    if (a->want_nu && a->nck >= 2) {
+        // optional: the buffer the next segment is recomputed into while the
+        // current one is reversed; without room for it segments are recomputed
+        // one at a time, the same launches in the same order within each
+        std::vector<void *> s2(C, nullptr);
+        for (auto &p : s2)
+            if (e == cudaSuccess) e = cudaMalloc(&p, sbytes);
+        if (e == cudaSuccess) {
+            a->seg[1] = std::move(s2);
+            a->nseg_buf = 2;
+            a->bytes += C * sbytes;
+        } else {
+            for (void *p : s2) cudaFree(p);
+            if (e != cudaErrorMemoryAllocation) {
+                free_adj(a);
+                return LB_ECUDA;
+            }
+            cudaGetLastError();  // an allocation failure leaves no sticky error
+        }
     }
     *out = a;
     return LB_OK;
