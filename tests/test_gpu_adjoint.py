@@ -76,9 +76,10 @@ def test_adjoint_checkpoint_interval_does_not_change_the_gradient():
 
 @pytest.mark.parametrize("precision", ["fp64", "fx64", "fp32s"])
 def test_recorded_segments_match_single_steps(precision):
-    """Whole checkpoint segments run as recorded graphs (C forward sweeps; C - 1
-    recompute sweeps and C reverse steps); one reverse step per call, or calls
-    that split segments, launch the same kernels one by one.  The gradient and
+    """Whole checkpoint segments run as recorded graphs (C forward sweeps; C
+    reverse steps with the previous segment's C - 1 recompute sweeps on a
+    second branch); one reverse step per call, or calls that split segments,
+    recompute and reverse one segment at a time with single launches.  The gradient and
     dL/dnu agree bit for bit, also on a second forward and seed of the same
     workspace (graphs reused or re-recorded)."""
     d, N, T = 2, (70, 45), 23  # C = 5: four whole segments and a short last one
