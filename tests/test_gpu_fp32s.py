@@ -140,4 +140,10 @@ def test_fp32s_recovery_sums_match_exact_arithmetic(d, N):
     assert np.max(np.abs(u - u_x)) <= 1e-14 * np.max(np.abs(u_x))
     gcoef = -p["s1"] / (p["cs2"] / p["c"] ** 2 * dx)  # grad theta = -s1 J / (sigma dx), Sec. III.C
     assert np.max(np.abs(g - gcoef * J_x)) <= 1e-14 * np.max(np.abs(gcoef * J_x))
+    # the state sum (Eq. (conseved-moment)): theta_ref per node plus every stored value, the floats of each
+    # 16-byte vector summed on the integer pipes and the vector sums added in FP64
+    nodes = int(np.prod(shape))
+    total = s.sum_theta()
+    exact = math.fsum([2.0 * nodes] + [float(v) for v in vals.ravel()])
+    assert abs(total - exact) <= 1e-14 * (2.0 * nodes + float(np.sum(np.abs(vals.astype(np.float64)))))
     s.close()
