@@ -85,15 +85,16 @@ lb_status lb_slab_set_theta0(lb_slab *s, const double *theta0, const double *gra
  * the velocities with a +1 component on the slowest axis from the last owned
  * layer, send_down (to part p-1) those with -1 from the first owned layer;
  * each buffer holds info[2] values (device, storage type of the precision,
- * 16-byte aligned).  Asynchronous.  Errors: LB_ESTATE (no state), LB_EINVAL,
- * LB_ECUDA.
+ * 16-byte aligned; LB_EINVAL otherwise).  One launch moves both directions.
+ * Asynchronous.  Errors: LB_ESTATE (no state), LB_EINVAL, LB_ECUDA.
  */
 lb_status lb_slab_pack(lb_slab *s, void *send_down, void *send_up);
 
 /*
  * Unpack what the neighbours sent: recv_down (part p-1's send_up) into the
- * lower ghost layer, recv_up (part p+1's send_down) into the upper one.
- * Asynchronous.  Errors: LB_ESTATE, LB_EINVAL, LB_ECUDA.
+ * lower ghost layer, recv_up (part p+1's send_down) into the upper one
+ * (16-byte aligned buffers, one launch).  Asynchronous.  Errors: LB_ESTATE,
+ * LB_EINVAL, LB_ECUDA.
  */
 lb_status lb_slab_unpack(lb_slab *s, const void *recv_down, const void *recv_up);
 

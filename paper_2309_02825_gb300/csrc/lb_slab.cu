@@ -2,10 +2,13 @@
 // ordinary context over the slab's layers plus one ghost layer on each side,
 // and the packing of the populations that cross the cuts.  The sweep, the
 // recovery and the sums are the single-grid kernels (the recovery and the
-// sum restricted to the owned rows); packing and unpacking are device copies
-// of whole layers, one per crossing population.
+// sum restricted to the owned rows); packing and unpacking move the crossing
+// populations' layers of both directions in one launch each.
 #include <math.h>
 
+#include <stdint.h>
+
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -139,30 +142,71 @@ lb_status lb_slab_set_theta0(lb_slab *s, const double *theta0, const double *gra
     return st;
 }
 
-// Copy the listed populations' layer `layer` of the current state to (pack)
-// or from (unpack) consecutive slots of a buffer.
-static cudaError_t copy_layers(lb_slab *s, const std::vector<int> &pops, int64_t layer, void *buf, bool pack)
+// One direction of an exchange: the listed populations' layer of the state
+// and the buffer whose consecutive slots hold them, in 16-byte vectors (a
+// layer's rows are padded to 16 bytes, so every layer and slab starts on a
+// vector boundary; the buffers are 16-byte aligned by contract).
+struct LayerCopy {
+    uint4 *buf;
+    int64_t layer_off;  // vector offset of the layer within a population's slab
+    int npop;
+    int pop[8];
+};
+
+// Both directions of a pack (state -> buffers) or an unpack (buffers ->
+// state) in one launch: thread t moves vector t of the concatenated slots.
+__global__ void slab_copy_kernel(uint4 *__restrict__ state, LayerCopy a, LayerCopy b, int64_t layer_vecs,
+                                 int64_t slab_vecs, int pack)
+{
+    const int64_t na = a.npop * layer_vecs, total = na + b.npop * layer_vecs;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const bool first = t < na;
+        const LayerCopy &lc = first ? a : b;
+        const int64_t u = first ? t : t - na;
+        const int k = (int)(u / layer_vecs);
+        uint4 *st = state + lc.pop[k] * slab_vecs + lc.layer_off + (u - k * layer_vecs);
+        if (pack)
+            lc.buf[u] = *st;
+        else
+            *st = lc.buf[u];
+    }
+}
+
+static LayerCopy layer_copy(const lb_slab *s, const std::vector<int> &pops, int64_t layer, void *buf)
+{
+    LayerCopy lc{};
+    lc.buf = (uint4 *)buf;
+    lc.layer_off = layer * s->layer_elems * (int64_t)s->ctx->elem / 16;
+    lc.npop = (int)pops.size();
+    for (size_t k = 0; k < pops.size(); ++k) lc.pop[k] = pops[k];
+    return lc;
+}
+
+// Move the crossing populations of layers `la` (buffer `ba`, populations
+// `pa`) and `lb` (buffer `bb`, populations `pb`) to (pack) or from the
+// buffers, on the context's stream.
+static cudaError_t copy_layers(lb_slab *s, const std::vector<int> &pa, int64_t la, void *ba, const std::vector<int> &pb,
+                               int64_t lb, void *bb, bool pack)
 {
     lb_ctx *c = s->ctx;
-    const size_t bytes = (size_t)s->layer_elems * c->elem;
-    char *state = (char *)c->f[c->cur];
-    for (size_t k = 0; k < pops.size(); ++k) {
-        char *st = state + ((size_t)pops[k] * c->geom.slab + (size_t)layer * s->layer_elems) * c->elem;
-        char *b = (char *)buf + k * bytes;
-        cudaError_t e = pack ? cudaMemcpyAsync(b, st, bytes, cudaMemcpyDeviceToDevice, c->stream)
-                             : cudaMemcpyAsync(st, b, bytes, cudaMemcpyDeviceToDevice, c->stream);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    const int64_t layer_vecs = s->layer_elems * (int64_t)c->elem / 16, slab_vecs = c->geom.slab * (int64_t)c->elem / 16;
+    const int64_t total = (int64_t)(pa.size() + pb.size()) * layer_vecs;
+    const unsigned nb = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
+    slab_copy_kernel<<<nb, 256, 0, c->stream>>>((uint4 *)c->f[c->cur], layer_copy(s, pa, la, ba),
+                                                layer_copy(s, pb, lb, bb), layer_vecs, slab_vecs, pack ? 1 : 0);
+    return cudaGetLastError();
 }
 
 lb_status lb_slab_pack(lb_slab *s, void *send_down, void *send_up)
 {
     lbk::NvtxRange nvtx_range("lb_slab_pack");
     if (!s || !send_down || !send_up) return LB_EINVAL;
+    if ((((uintptr_t)send_down) | ((uintptr_t)send_up)) & 15u)
+        return sfail(s, LB_EINVAL, "lb_slab_pack: buffers must be 16-byte aligned");
     if (!s->ctx->initialized) return sfail(s, LB_ESTATE, "lb_slab_pack: no state (lb_slab_set_theta0 first)");
-    cudaError_t e = copy_layers(s, s->up, s->nz, send_up, true);  // last owned layer, moving up
-    if (e == cudaSuccess) e = copy_layers(s, s->down, 1, send_down, true);  // first owned layer, moving down
+    // last owned layer moving up, first owned layer moving down
+    cudaError_t e = copy_layers(s, s->up, s->nz, send_up, s->down, 1, send_down, true);
     if (e != cudaSuccess) return scuda(s, e, "lb_slab_pack");
     return LB_OK;
 }
@@ -171,9 +215,12 @@ lb_status lb_slab_unpack(lb_slab *s, const void *recv_down, const void *recv_up)
 {
     lbk::NvtxRange nvtx_range("lb_slab_unpack");
     if (!s || !recv_down || !recv_up) return LB_EINVAL;
+    if ((((uintptr_t)recv_down) | ((uintptr_t)recv_up)) & 15u)
+        return sfail(s, LB_EINVAL, "lb_slab_unpack: buffers must be 16-byte aligned");
     if (!s->ctx->initialized) return sfail(s, LB_ESTATE, "lb_slab_unpack: no state (lb_slab_set_theta0 first)");
-    cudaError_t e = copy_layers(s, s->up, 0, const_cast<void *>(recv_down), false);  // from below: lower ghost
-    if (e == cudaSuccess) e = copy_layers(s, s->down, s->nz + 1, const_cast<void *>(recv_up), false);
+    // from below into the lower ghost layer, from above into the upper one
+    cudaError_t e = copy_layers(s, s->up, 0, const_cast<void *>(recv_down), s->down, s->nz + 1,
+                                const_cast<void *>(recv_up), false);
     if (e != cudaSuccess) return scuda(s, e, "lb_slab_unpack");
     s->halo_fresh = true;
     return LB_OK;
